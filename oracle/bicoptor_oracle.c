@@ -1,0 +1,563 @@
+/*
+ * Bicoptor 2.0 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, step-by-step CPU implementation of what the GPU hot path
+ * computes.  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load it; the product path never does.  It shares no code with the
+ * CUDA sources.
+ *
+ * Paper: "Bicoptor 2.0: Addressing Challenges in Probabilistic Truncation for
+ * Enhanced Privacy-Preserving Machine Learning" (arXiv 2309.04909).
+ *
+ * Every ring value is held in a uint64_t and reduced explicitly; every Z_p
+ * value in a uint32_t (p < 2^32).  There is no floating point on the protocol
+ * path; the fixed-point encoder is the only place a double appears.
+ *
+ * Readings of the paper that this file takes (the paper is silent or
+ * ambiguous there) are marked "READING".  The pseudorandom layout (Philox
+ * counters, how words become ring/Z_p elements, the Fisher-Yates rule) is not
+ * in the paper at all; it is this project's fixed convention and is described
+ * next to orc_stream_word below.
+ *
+ * Pins (tests/test_oracle_pins.py): the paper's worked 8-bit truncation
+ * examples (Sec. 1, Sec. 5.1), Table "sign determination" rows, the exact
+ * SecureML failure law derived from Cor. 2, exhaustive zero-preservation of
+ * Alg. modswitch, brute force of Alg. drelu at l=8 and l=10 against the
+ * closed form of Thm. "newtrc2" and the plaintext sign, the Beaver identity of
+ * Alg. relu, and Philox-4x32-10 against an independent library implementation.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------------- */
+/* Ring Z_{2^l}                                                              */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t ring_mask(int ell) { return ell >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << ell) - 1); }
+static uint64_t rmod(uint64_t a, int ell) { return a & ring_mask(ell); }
+static uint64_t rneg(uint64_t a, int ell) { return rmod((uint64_t)0 - a, ell); }
+
+/* Sec. 2.3: cut(alpha, k1, k2) keeps bits k1 .. l-k2-1 of alpha.
+ * READING: the bits are moved down to position 0 (cut is a right shift): the
+ * worked examples of Sec. 1 and cut(2^l, k) = 2^(l-k) in Sec. 5.1 need it,
+ * although the displayed sum keeps the weights 2^i.  Written bit by bit,
+ * exactly as the definition reads. */
+uint64_t orc_cut(uint64_t alpha, int ell, int k1, int k2)
+{
+    uint64_t out = 0;
+    for (int i = k1; i <= ell - k2 - 1; i++) {
+        uint64_t bit = (alpha >> i) & 1u;
+        out |= bit << (i - k1);
+    }
+    return out;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC 2011): 10 rounds of the 4x32 S-box with the          */
+/* published multipliers and Weyl key increments.                            */
+/* ------------------------------------------------------------------------- */
+
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * x0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * x2;
+        uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod1;
+        uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pre-shared seeds (Sec. 2.1): seed01, seed02, seed12.  The simulation      */
+/* derives every pair's stream from one 64-bit seed, keyed by a pair tag.    */
+/*                                                                           */
+/* Layout (this project's convention; the paper does not specify a PRG):     */
+/*   key     = (lo32(seed), hi32(seed))                                      */
+/*   counter = (lo32(elem), tensor_id, block,                                */
+/*              pair << 24 | purpose << 16 | (elem >> 32) & 0xffff)          */
+/* Word j of a stream is word j % 4 of block j / 4.                          */
+/* ------------------------------------------------------------------------- */
+
+enum { PAIR_01 = 0x01, PAIR_02 = 0x02, PAIR_12 = 0x12, PAIR_DEALER = 0xDE };
+enum {
+    PUR_SHARE = 1,      /* dealer's R for the 2-of-2 sharing            */
+    PUR_PERM = 2,       /* seed01: flip bit t and the shuffle           */
+    PUR_MASK = 3,       /* seed01: r_k, z_k of message slot k           */
+    PUR_REPLY = 4,      /* seed02: P0's share of DReLU'                 */
+    PUR_RELU_TRIPLE = 5,/* seed02: a0,b0,c0 / seed12: a1,b1 (ReLU)      */
+    PUR_MUL_TRIPLE = 6  /* seed02: a0,b0,c0 / seed12: a1,b1 (product)   */
+};
+
+uint32_t orc_stream_word(uint64_t seed, int pair, int purpose, uint32_t tensor_id,
+                         uint64_t elem, uint64_t j)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)elem, tensor_id, (uint32_t)(j / 4),
+                       ((uint32_t)pair << 24) | ((uint32_t)purpose << 16) |
+                           (uint32_t)((elem >> 32) & 0xffffu)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[j % 4];
+}
+
+/* Ring element number j of a stream: one word for l <= 32, two words (low
+ * word first) for l > 32, reduced mod 2^l. */
+static uint64_t stream_ring(uint64_t seed, int pair, int purpose, uint32_t tid,
+                            uint64_t elem, uint64_t j, int ell)
+{
+    if (ell <= 32)
+        return rmod(orc_stream_word(seed, pair, purpose, tid, elem, j), ell);
+    uint64_t lo = orc_stream_word(seed, pair, purpose, tid, elem, 2 * j);
+    uint64_t hi = orc_stream_word(seed, pair, purpose, tid, elem, 2 * j + 1);
+    return rmod(lo | (hi << 32), ell);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Prime for the modulo switch.                                              */
+/* READING: "log2 p = l'+1" (Sec. 5.3, Table notation) with the correctness  */
+/* argument needing p > 2^l'; the oracle takes the smallest prime above      */
+/* 2^lx, found by trial division.                                            */
+/* ------------------------------------------------------------------------- */
+
+static int is_prime_u64(uint64_t q)
+{
+    if (q < 2) return 0;
+    for (uint64_t d = 2; d * d <= q; d++)
+        if (q % d == 0) return 0;
+    return 1;
+}
+
+uint32_t orc_prime_above(int lx)
+{
+    uint64_t q = ((uint64_t)1 << lx) + 1;
+    while (!is_prime_u64(q)) q++;
+    return (uint32_t)q;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fixed-point encoding (Sec. 2.2): x -> round(x * 2^f) mod 2^l, with        */
+/* l_x = l_x^int + l_x^frac.  READING: round half to even (the paper does    */
+/* not say); nearbyint() in the default rounding mode does exactly that.     */
+/* ------------------------------------------------------------------------- */
+
+void orc_encode(const double *x, size_t n, int f, int ell, uint64_t *out)
+{
+    for (size_t i = 0; i < n; i++) {
+        double scaled = nearbyint(ldexp(x[i], f));
+        int64_t v = (int64_t)scaled;
+        out[i] = rmod((uint64_t)v, ell);
+    }
+}
+
+/* Signed value of a ring element: x in [0, 2^(l-1)) is positive. */
+void orc_to_signed(const uint64_t *v, size_t n, int ell, int64_t *out)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t a = rmod(v[i], ell);
+        if (ell < 64 && (a >> (ell - 1)))
+            out[i] = (int64_t)a - (int64_t)((uint64_t)1 << ell);
+        else
+            out[i] = (int64_t)a;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* 2-of-2 additive sharing (Sec. 2.2): [x]_0 = x + R, [x]_1 = -R (mod 2^l).  */
+/* ------------------------------------------------------------------------- */
+
+void orc_share_with_r(int ell, uint64_t x, uint64_t r, uint64_t *s0, uint64_t *s1)
+{
+    *s0 = rmod(x + r, ell);
+    *s1 = rneg(r, ell);
+}
+
+static uint64_t elem_index(const uint64_t *idx, size_t i) { return idx ? idx[i] : (uint64_t)i; }
+
+void orc_share(int ell, const uint64_t *x, const uint64_t *idx, size_t n, uint64_t seed,
+               uint32_t tid, uint64_t *s0, uint64_t *s1)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t R = stream_ring(seed, PAIR_DEALER, PUR_SHARE, tid, elem_index(idx, i), 0, ell);
+        orc_share_with_r(ell, x[i], R, &s0[i], &s1[i]);
+    }
+}
+
+void orc_reconstruct(int ell, const uint64_t *s0, const uint64_t *s1, size_t n, uint64_t *x)
+{
+    for (size_t i = 0; i < n; i++) x[i] = rmod(s0[i] + s1[i], ell);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. smltrc (SecureML probabilistic truncation), per party.               */
+/*   P0: cut([x]_0, k) mod 2^l;  P1: 2^l - cut(2^l - [x]_1, k) mod 2^l.      */
+/* READING: 2^l - [x]_1 is reduced mod 2^l before the cut (so [x]_1 = 0      */
+/* gives 0).                                                                  */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t smltrc_p0(uint64_t s0, int ell, int k) { return rmod(orc_cut(s0, ell, k, 0), ell); }
+static uint64_t smltrc_p1(uint64_t s1, int ell, int k)
+{
+    uint64_t a = rneg(s1, ell);                 /* 2^l - [x]_1 mod 2^l */
+    return rneg(orc_cut(a, ell, k, 0), ell);    /* 2^l - cut(., k) mod 2^l */
+}
+
+void orc_trunc_prob(int ell, int k, const uint64_t *s0, const uint64_t *s1, size_t n,
+                    uint64_t *o0, uint64_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        o0[i] = smltrc_p0(s0[i], ell, k);
+        o1[i] = smltrc_p1(s1[i], ell, k);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. newtrc2 (deterministic truncation keeping bits k1 .. l-k2-1), per    */
+/* party, outputs in Z_{2^(l-k1-k2)}.  Alg. newtrc is the case k2 = 0.       */
+/* READING: k1 counts the low bits dropped and k2 the high bits dropped; the */
+/* worked example of Sec. 5.1 (k1 = 4, k2 = 1 -> 100) fixes this order.      */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t newtrc_p0(uint64_t s0, int ell, int k1, int k2)
+{
+    return rmod(orc_cut(s0, ell, k1, k2), ell - k1 - k2);
+}
+static uint64_t newtrc_p1(uint64_t s1, int ell, int k1, int k2)
+{
+    uint64_t a = rneg(s1, ell);                          /* 2^l - [x]_1 mod 2^l */
+    return rneg(orc_cut(a, ell, k1, k2), ell - k1 - k2); /* 2^l - cut(.) mod 2^(l-k1-k2) */
+}
+
+void orc_trunc_det(int ell, int k1, int k2, const uint64_t *s0, const uint64_t *s1, size_t n,
+                   uint64_t *o0, uint64_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        o0[i] = newtrc_p0(s0[i], ell, k1, k2);
+        o1[i] = newtrc_p1(s1[i], ell, k1, k2);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. modswitch: shares in Z_{2^l'} -> shares in Z_p with zero <-> zero.   */
+/*   P0: 2^l' mod p if [x]_0 = 0, else [x]_0 mod p;                          */
+/*   P1: p + [x]_1 - 2^l' mod p.                                             */
+/* ------------------------------------------------------------------------- */
+
+static uint32_t modswitch_p0(uint64_t a, int lp, uint32_t p)
+{
+    uint64_t pow2 = (uint64_t)1 << lp;
+    if (a == 0) return (uint32_t)(pow2 % p);
+    return (uint32_t)(a % p);
+}
+static uint32_t modswitch_p1(uint64_t b, int lp, uint32_t p)
+{
+    uint64_t pow2 = (uint64_t)1 << lp;
+    /* p + b - 2^l' is in (p - 2^l', p + 2^l'), never negative since b >= 0
+       and p > 2^l'. */
+    return (uint32_t)(((uint64_t)p + b - pow2) % p);
+}
+
+void orc_mod_switch(int lp, uint32_t p, const uint64_t *s0, const uint64_t *s1, size_t n,
+                    uint32_t *o0, uint32_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        o0[i] = modswitch_p0(rmod(s0[i], lp), lp, p);
+        o1[i] = modswitch_p1(rmod(s1[i], lp), lp, p);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Beaver multiplication (Table notation, Sec. 2.3; Alg. relu pre-          */
+/* processing): the triple comes from the pre-shared seeds, P2 completes     */
+/* [c]_1 = (a0 + a1)(b0 + b1) - [c]_0 and sends it to P1.  d = x - a and     */
+/* e = y - b are opened; [xy] = de + d[b] + e[a] + [c], de added by P0.      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { uint64_t a0, b0, c0, a1, b1, c1; } triple_t;
+
+static triple_t draw_triple(uint64_t seed, int purpose, uint32_t tid, uint64_t elem, int ell)
+{
+    triple_t T;
+    T.a0 = stream_ring(seed, PAIR_02, purpose, tid, elem, 0, ell);
+    T.b0 = stream_ring(seed, PAIR_02, purpose, tid, elem, 1, ell);
+    T.c0 = stream_ring(seed, PAIR_02, purpose, tid, elem, 2, ell);
+    T.a1 = stream_ring(seed, PAIR_12, purpose, tid, elem, 0, ell);
+    T.b1 = stream_ring(seed, PAIR_12, purpose, tid, elem, 1, ell);
+    /* P2 knows both halves and completes the triple. */
+    T.c1 = rmod((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0, ell);
+    return T;
+}
+
+void orc_mul_beaver(int ell, const uint64_t *x0, const uint64_t *x1, const uint64_t *y0,
+                    const uint64_t *y1, const uint64_t *idx, size_t n, uint64_t seed,
+                    uint32_t tid, uint64_t *o0, uint64_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        triple_t T = draw_triple(seed, PUR_MUL_TRIPLE, tid, elem_index(idx, i), ell);
+        /* openings: each party sends its share of x - a and of y - b */
+        uint64_t d = rmod((x0[i] - T.a0) + (x1[i] - T.a1), ell);
+        uint64_t e = rmod((y0[i] - T.b0) + (y1[i] - T.b1), ell);
+        o0[i] = rmod(d * e + d * T.b0 + e * T.a0 + T.c0, ell);
+        o1[i] = rmod(d * T.b1 + e * T.a1 + T.c1, ell);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. drelu (UBL Bicoptor 2.0 DReLU), steps 1-9, for one element, with     */
+/* the randomness that P0 and P1 draw from seed01 passed in:                 */
+/*   t          flip bit (step 1)                                            */
+/*   fy[1..lx]  32-bit words for the shuffle (step 6)                        */
+/*   r[k],z[k]  mask in Z_p^* and reshare value in Z_p of message slot k     */
+/* Writes P0's and P1's messages to P2 and P2's bit DReLU'.                  */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { int ell, lx, c; uint32_t p; } orc_params;
+
+#define MAXL 64
+
+int orc_drelu_core(const orc_params *P, uint64_t s0, uint64_t s1, int t, const uint32_t *fy,
+                   const uint32_t *r, const uint32_t *z, uint32_t *msg0, uint32_t *msg1)
+{
+    const int ell = P->ell, lx = P->lx, c = P->c;
+    const uint32_t p = P->p;
+    const int L = lx + 1;
+    uint64_t u0[MAXL], u1[MAXL], v0[MAXL], v1[MAXL];
+    uint32_t m0[MAXL], m1[MAXL], sh0[MAXL], sh1[MAXL], w[MAXL];
+    int perm[MAXL];
+
+    /* Steps 1-2: both parties flip their share by (-1)^t. */
+    if (t) { s0 = rneg(s0, ell); s1 = rneg(s1, ell); }
+
+    /* Step 3: [u_i] = [trc(x, i, l - lx - i)] mod 2^lx for i in [0, lx], with
+       the window moved up by the key-bit offset c (Sec. 6.1):
+       k1 = c + i, k2 = l - lx - c - i. */
+    for (int i = 0; i <= lx; i++) {
+        int k1 = c + i, k2 = ell - lx - c - i;
+        u0[i] = newtrc_p0(s0, ell, k1, k2);
+        u1[i] = newtrc_p1(s1, ell, k1, k2);
+    }
+
+    /* Step 4: [v_i] = [u_i] + [u_(i+1)] - 1, [v_lx] = [u_lx] - 1 (mod 2^lx).
+       READING: the public constant -1 is applied by P0 alone. */
+    for (int i = 0; i < lx; i++) {
+        v0[i] = rmod(u0[i] + u0[i + 1] - 1, lx);
+        v1[i] = rmod(u1[i] + u1[i + 1], lx);
+    }
+    v0[lx] = rmod(u0[lx] - 1, lx);
+    v1[lx] = rmod(u1[lx], lx);
+
+    /* Step 5: Alg. modswitch, Z_{2^lx} -> Z_p. */
+    for (int i = 0; i <= lx; i++) {
+        m0[i] = modswitch_p0(v0[i], lx, p);
+        m1[i] = modswitch_p1(v1[i], lx, p);
+    }
+
+    /* Step 6: shuffle with seed01.  READING: a Fisher-Yates shuffle of the
+       slots 0..lx starting from the identity; for j = lx down to 1 the swap
+       partner is floor(W * (j+1) / 2^32) with W = fy[lx - j + 1].  Message
+       slot k carries the value at perm[k]. */
+    for (int k = 0; k < L; k++) perm[k] = k;
+    for (int j = lx; j >= 1; j--) {
+        uint32_t W = fy[lx - j + 1];
+        int partner = (int)(((uint64_t)W * (uint64_t)(j + 1)) >> 32);
+        int tmp = perm[j]; perm[j] = perm[partner]; perm[partner] = tmp;
+    }
+    for (int k = 0; k < L; k++) { sh0[k] = m0[perm[k]]; sh1[k] = m1[perm[k]]; }
+
+    /* Step 7: mask with r_k in Z_p^*, w_k = v_k * r_k mod p. */
+    for (int k = 0; k < L; k++) {
+        sh0[k] = (uint32_t)(((uint64_t)sh0[k] * r[k]) % p);
+        sh1[k] = (uint32_t)(((uint64_t)sh1[k] * r[k]) % p);
+    }
+
+    /* Step 8: reshare with z_k (READING: P0 adds, P1 subtracts) and send. */
+    for (int k = 0; k < L; k++) {
+        msg0[k] = (uint32_t)(((uint64_t)sh0[k] + z[k]) % p);
+        msg1[k] = (uint32_t)(((uint64_t)sh1[k] + p - z[k]) % p);
+    }
+
+    /* Step 9: P2 reconstructs every w_k and sets DReLU' = 1 if one is 0. */
+    int dprime = 0;
+    for (int k = 0; k < L; k++) {
+        w[k] = (uint32_t)(((uint64_t)msg0[k] + msg1[k]) % p);
+        if (w[k] == 0) dprime = 1;
+    }
+    return dprime;
+}
+
+/* The seed01 draws of one element: t, the shuffle words, and (r_k, z_k).
+ * READING: r_k = 1 + floor(W64 * (p-1) / 2^64), z_k = floor(W64' * p / 2^64)
+ * from two 64-bit words of the slot's mask block (words 4k..4k+3, low word
+ * first), which keeps every draw within 2^-(64 - log2 p) of uniform. */
+static void draw_seed01(const orc_params *P, uint64_t seed, uint32_t tid, uint64_t elem,
+                        int *t, uint32_t *fy, uint32_t *r, uint32_t *z)
+{
+    const int L = P->lx + 1;
+    *t = (int)(orc_stream_word(seed, PAIR_01, PUR_PERM, tid, elem, 0) & 1u);
+    for (int j = 1; j < L; j++) fy[j] = orc_stream_word(seed, PAIR_01, PUR_PERM, tid, elem, j);
+    for (int k = 0; k < L; k++) {
+        uint64_t wr = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k) |
+                      ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 1) << 32);
+        uint64_t wz = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 2) |
+                      ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 3) << 32);
+        r[k] = 1u + (uint32_t)(((u128)wr * (u128)(P->p - 1u)) >> 64);
+        z[k] = (uint32_t)(((u128)wz * (u128)P->p) >> 64);
+    }
+}
+
+/* Parameter checks shared by DReLU and ReLU: the window needs c + 2 lx <= l
+ * (k2 >= 0 at i = lx), p must lie in (2^lx, 2^(lx+1)). */
+static int check_params(const orc_params *P)
+{
+    if (P->ell < 2 || P->ell > 64) return -1;
+    if (P->lx < 1 || P->lx > 31 || P->lx + 1 > MAXL) return -1;
+    if (P->c < 0 || P->c + 2 * P->lx > P->ell) return -1;
+    if ((uint64_t)P->p <= ((uint64_t)1 << P->lx) || (uint64_t)P->p >= ((uint64_t)1 << (P->lx + 1)))
+        return -1;
+    if (!is_prime_u64(P->p)) return -1;
+    return 0;
+}
+
+/* Audit view of one call: what each party sent (NULL = not wanted). */
+typedef struct {
+    uint32_t *w0;        /* P0 -> P2, n * (lx+1) values in Z_p              */
+    uint32_t *w1;        /* P1 -> P2, n * (lx+1) values in Z_p              */
+    uint64_t *reply;     /* P2 -> P1: [DReLU']_1 (DReLU); P2 -> P0,P1: e (ReLU) */
+    uint64_t *open0;     /* P0 -> P1: [x]_0 - [a]_0 (ReLU)                  */
+    uint64_t *open1;     /* P1 -> P0: [x]_1 - [a]_1 (ReLU)                  */
+    uint64_t *pre_c1;    /* P2 -> P1 preprocessing: [c]_1 (ReLU)             */
+    uint8_t *t;          /* the flip bit (seed01)                           */
+    uint8_t *dprime;     /* P2's DReLU'                                     */
+} orc_audit;
+
+/* Steps 10-11 of Alg. drelu: P2 returns DReLU' as shares in Z_{2^l};
+ * READING: [DReLU']_0 = d0 is drawn from seed02 by P0 and P2 alike, so only
+ * [DReLU']_1 = DReLU' - d0 travels (to P1).  Unflip:
+ * [DReLU]_0 = t + (1-2t)[DReLU']_0, [DReLU]_1 = (1-2t)[DReLU']_1; the public
+ * t is added by P0 alone. */
+int orc_drelu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const uint64_t *idx,
+              size_t n, uint64_t seed, uint32_t tid, uint64_t *o0, uint64_t *o1,
+              const orc_audit *audit, int threads)
+{
+    if (check_params(P)) return -1;
+    const int ell = P->ell, L = P->lx + 1;
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (long long ii = 0; ii < (long long)n; ii++) {
+        size_t i = (size_t)ii;
+        uint64_t elem = elem_index(idx, i);
+        int t;
+        uint32_t fy[MAXL], r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
+        draw_seed01(P, seed, tid, elem, &t, fy, r, z);
+        int dprime = orc_drelu_core(P, s0[i], s1[i], t, fy, r, z, msg0, msg1);
+        uint64_t d0 = stream_ring(seed, PAIR_02, PUR_REPLY, tid, elem, 0, ell);
+        uint64_t d1 = rmod((uint64_t)dprime - d0, ell);
+        uint64_t one_m2t = rmod((uint64_t)1 - 2 * (uint64_t)t, ell);
+        o0[i] = rmod((uint64_t)t + one_m2t * d0, ell);
+        o1[i] = rmod(one_m2t * d1, ell);
+        if (audit) {
+            if (audit->w0) memcpy(audit->w0 + i * L, msg0, sizeof(uint32_t) * L);
+            if (audit->w1) memcpy(audit->w1 + i * L, msg1, sizeof(uint32_t) * L);
+            if (audit->reply) audit->reply[i] = d1;
+            if (audit->t) audit->t[i] = (uint8_t)t;
+            if (audit->dprime) audit->dprime[i] = (uint8_t)dprime;
+        }
+    }
+    return 0;
+}
+
+/* Alg. relu (UBL Bicoptor 2.0 ReLU).  P2 answers e = DReLU' - b instead of
+ * shares of DReLU'; P0 and P1 open d = x - a and finish
+ * [ReLU] = t[x] + (1-2t)(de + d[b] + e[a] + [c]), de added by P0 alone.
+ * READING: x here is the input before the flip of step 2. */
+int orc_relu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const uint64_t *idx,
+             size_t n, uint64_t seed, uint32_t tid, uint64_t *o0, uint64_t *o1,
+             const orc_audit *audit, int threads)
+{
+    if (check_params(P)) return -1;
+    const int ell = P->ell, L = P->lx + 1;
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (long long ii = 0; ii < (long long)n; ii++) {
+        size_t i = (size_t)ii;
+        uint64_t elem = elem_index(idx, i);
+        /* preprocessing: the triple */
+        triple_t T = draw_triple(seed, PUR_RELU_TRIPLE, tid, elem, ell);
+        /* P0, P1 run Alg. drelu up to step 8; P2 runs step 9 */
+        int t;
+        uint32_t fy[MAXL], r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
+        draw_seed01(P, seed, tid, elem, &t, fy, r, z);
+        int dprime = orc_drelu_core(P, s0[i], s1[i], t, fy, r, z, msg0, msg1);
+        /* P2 responds e = DReLU' - b */
+        uint64_t e = rmod((uint64_t)dprime - (T.b0 + T.b1), ell);
+        /* P0 and P1 open d = x - a */
+        uint64_t open0 = rmod(s0[i] - T.a0, ell), open1 = rmod(s1[i] - T.a1, ell);
+        uint64_t d = rmod(open0 + open1, ell);
+        uint64_t xd0 = rmod(d * e + d * T.b0 + e * T.a0 + T.c0, ell);
+        uint64_t xd1 = rmod(d * T.b1 + e * T.a1 + T.c1, ell);
+        uint64_t one_m2t = rmod((uint64_t)1 - 2 * (uint64_t)t, ell);
+        o0[i] = rmod((uint64_t)t * s0[i] + one_m2t * xd0, ell);
+        o1[i] = rmod((uint64_t)t * s1[i] + one_m2t * xd1, ell);
+        if (audit) {
+            if (audit->w0) memcpy(audit->w0 + i * L, msg0, sizeof(uint32_t) * L);
+            if (audit->w1) memcpy(audit->w1 + i * L, msg1, sizeof(uint32_t) * L);
+            if (audit->reply) audit->reply[i] = e;
+            if (audit->open0) audit->open0[i] = open0;
+            if (audit->open1) audit->open1[i] = open1;
+            if (audit->pre_c1) audit->pre_c1[i] = T.c1;
+            if (audit->t) audit->t[i] = (uint8_t)t;
+            if (audit->dprime) audit->dprime[i] = (uint8_t)dprime;
+        }
+    }
+    return 0;
+}
+
+/* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Steps 1-9 of Alg. drelu over many elements with explicit randomness
+ * (row i uses t[i], fy[i*L ..], r[i*L ..], z[i*L ..]); used by the brute-force
+ * pins, which sweep t and the shares directly. */
+int orc_drelu_core_many(const orc_params *P, const uint64_t *s0, const uint64_t *s1,
+                        const uint8_t *t, const uint32_t *fy, const uint32_t *r,
+                        const uint32_t *z, size_t n, uint8_t *dprime)
+{
+    if (check_params(P)) return -1;
+    const int L = P->lx + 1;
+    uint32_t msg0[MAXL], msg1[MAXL];
+    for (size_t i = 0; i < n; i++)
+        dprime[i] = (uint8_t)orc_drelu_core(P, s0[i], s1[i], t[i], fy + i * L, r + i * L,
+                                            z + i * L, msg0, msg1);
+    return 0;
+}

@@ -1,0 +1,404 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms derived from its theorems, exhaustive enumeration,
+the plaintext it should compute, or an independent library implementation.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def _mask(ell):
+    return (1 << ell) - 1
+
+
+# --------------------------------------------------------------------------
+# Worked examples (Sec. 1 and Sec. 5.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", _rows("worked_examples.txt"), ids=lambda r: r[0])
+def test_worked_truncation_examples(row):
+    name, ell, k1, k2, alg, x, R, sh0, sh1, res, res_bits = row
+    ell, k1, k2, res_bits = int(ell), int(k1), int(k2), int(res_bits)
+    x, R, sh0, sh1, res = (int(v, 2) for v in (x, R, sh0, sh1, res))
+    # the paper's sharing [x]_0 = x + R, [x]_1 = -R reproduces its printed shares
+    assert O.share_with_r(ell, x, R) == (sh0, sh1)
+    if alg == "smltrc":
+        o0, o1 = O.trunc_prob(ell, k1, [sh0], [sh1])
+        assert int(O.reconstruct(ell, o0, o1)[0]) == res
+    else:
+        o0, o1 = O.trunc_det(ell, k1, k2, [sh0], [sh1])
+        assert ell - k1 - k2 == res_bits
+        assert int(O.reconstruct(res_bits, o0, o1)[0]) == res
+
+
+def test_cut_definition_small():
+    # cut keeps bits k1..l-k2-1 and moves them to position 0 (Sec. 2.3)
+    assert O.cut(0b01001011, 8, 4) == 0b0100
+    assert O.cut(0b01001011, 8, 4, 1) == 0b100
+    assert O.cut(0b11110101, 8, 4) == 0b1111
+    for a in range(256):
+        for k1 in range(8):
+            for k2 in range(8 - k1):
+                assert O.cut(a, 8, k1, k2) == (a >> k1) % (1 << (8 - k1 - k2))
+
+
+def test_sign_table_rows():
+    """Table 'sign determination' (Sec. 5.2), l=64, lx=7, x=+-22: the paper's
+    value of each row is reachable for some R, and every R gives that row's
+    floor(x / 2^k) or floor(x / 2^k) + 1 in Z_{2^7} (Thm. newtrc2)."""
+    ell, lx = 64, 7
+    rng = np.random.default_rng(5)
+    R = rng.integers(0, 2**63, size=4000, dtype=np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=4000, dtype=np.uint64)
+    # also R whose low bits are all ones / zeros so both carries occur
+    R = np.concatenate([R, np.arange(0, 256, dtype=np.uint64),
+                        np.uint64(2**64 - 1) - np.arange(0, 256, dtype=np.uint64)])
+    for row in _rows("sign_table.txt"):
+        k = int(row[0])
+        for x, printed, e0 in ((22, int(row[1], 2), int(row[2])),
+                               (-22, int(row[3], 2), int(row[4]))):
+            xs = np.full(R.size, x % 2**64, dtype=np.uint64)
+            s0 = xs + R
+            s1 = np.uint64(0) - R
+            o0, o1 = O.trunc_det(ell, k, ell - lx - k, s0, s1)
+            got = set(O.reconstruct(lx, o0, o1).tolist())
+            base = (x >> k) % 2**lx          # floor(x / 2^k) mod 2^7
+            assert got <= {base, (base + 1) % 2**lx}
+            assert printed in got
+            # printed e0 is the deviation from cut(xi, k) with the sign of x
+            xi = abs(x)
+            expect = (xi >> k) + e0 if x > 0 else -(xi >> k) + e0
+            assert printed == expect % 2**lx
+
+
+# --------------------------------------------------------------------------
+# SecureML truncation: exact failure law (Cor. 2) and the deterministic one
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_smltrc_failure_law_exhaustive_l8(k):
+    """Per Cor. 2, e1 occurs iff x + R mod 2^l < x (positive x) or
+    x < x + R mod 2^l (negative x): for uniform R that is exactly |x| of the
+    2^l values.  Failure = more than one away from floor(x / 2^k).  Alg.
+    newtrc never fails: it gives floor(x/2^k) or floor(x/2^k)+1 mod 2^(l-k)."""
+    ell, m = 8, 255
+    R = np.arange(256, dtype=np.uint64)
+    for x in range(-100, 101):
+        xs = np.full(256, x & m, dtype=np.uint64)
+        s0 = (xs + R) & np.uint64(m)
+        s1 = (np.uint64(0) - R) & np.uint64(m)
+        o0, o1 = O.trunc_prob(ell, k, s0, s1)
+        res = O.to_signed(O.reconstruct(ell, o0, o1), ell)
+        want = x >> k
+        assert int((np.abs(res - want) > 1).sum()) == abs(x)
+        d0, d1 = O.trunc_det(ell, k, 0, s0, s1)
+        rd = set(O.reconstruct(ell - k, d0, d1).tolist())
+        assert rd <= {want % 2**(ell - k), (want + 1) % 2**(ell - k)}
+
+
+def test_trunc_det_closed_form_l64():
+    """Thm. newtrc2 made exact: the reconstructed output of Alg. newtrc2 is
+    ((x >> k1) + carry) mod 2^(l-k1-k2), carry = [x mod 2^k1 + R mod 2^k1 >= 2^k1]
+    for the sharing [x]_0 = x + R, [x]_1 = -R."""
+    rng = np.random.default_rng(11)
+    n = 20000
+    x = rng.integers(0, 2**64, size=n, dtype=np.uint64)
+    R = rng.integers(0, 2**64, size=n, dtype=np.uint64)
+    s0, s1 = x + R, np.uint64(0) - R
+    for k1, k2 in ((16, 0), (16, 16), (3, 40), (0, 8), (31, 1)):
+        o0, o1 = O.trunc_det(64, k1, k2, s0, s1)
+        got = O.reconstruct(64 - k1 - k2, o0, o1)
+        low = np.uint64((1 << k1) - 1)
+        carry = ((x & low).astype(object) + (R & low).astype(object)) >= (1 << k1)
+        want = ((x >> np.uint64(k1)).astype(object) + carry.astype(object)) % (1 << (64 - k1 - k2))
+        assert (got.astype(object) == want).all()
+
+
+def test_smltrc_failure_rate_l64_statistical():
+    """At l = 64 the expected number of e1 failures is sum |x_i| / 2^64
+    (exact per-element law); observed within 5 sigma.  Inputs: |x| < 2^56."""
+    from paper_2309_04909_gb300 import workloads as W
+    n = 1 << 19
+    xs = W.magnitude_bounded_ints(n, 56, seed=1)
+    x = xs.astype(np.uint64)
+    s0, s1 = O.share(64, x, seed=0x1234, tid=9)
+    k = 16
+    o0, o1 = O.trunc_prob(64, k, s0, s1)
+    res = O.to_signed(O.reconstruct(64, o0, o1), 64)
+    want = xs >> k
+    fails = int((np.abs(res.astype(object) - want.astype(object)) > 1).sum())
+    pvec = np.abs(xs).astype(np.float64) / 2.0**64
+    mu, var = pvec.sum(), (pvec * (1 - pvec)).sum()
+    assert abs(fails - mu) < 5 * math.sqrt(var) + 1, (fails, mu)
+    d0, d1 = O.trunc_det(64, k, 0, s0, s1)
+    rd = O.reconstruct(48, d0, d1).astype(object)
+    w = (want.astype(object)) % (1 << 48)
+    assert (((rd - w) % (1 << 48)) <= 1).all()
+
+
+# --------------------------------------------------------------------------
+# Alg. modswitch: zero <-> zero, exhaustively
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lp", [1, 2, 3, 5, 8, 10])
+def test_modswitch_zero_preservation_exhaustive(lp):
+    a, b = np.meshgrid(np.arange(1 << lp, dtype=np.uint64), np.arange(1 << lp, dtype=np.uint64))
+    a, b = a.ravel(), b.ravel()
+    zero_in = ((a + b) & np.uint64((1 << lp) - 1)) == 0
+    primes = [q for q in range((1 << lp) + 1, 1 << (lp + 1)) if all(q % d for d in range(2, q))][:3]
+    assert primes[0] == O.prime_above(lp)
+    for p in primes:
+        o0, o1 = O.mod_switch(lp, p, a, b)
+        assert (o0 < p).all() and (o1 < p).all()
+        zero_out = ((o0.astype(np.uint64) + o1.astype(np.uint64)) % np.uint64(p)) == 0
+        assert (zero_in == zero_out).all()
+
+
+def test_prime_above():
+    for lx in (2, 3, 4, 5, 7, 9, 14, 24):
+        p = O.prime_above(lx)
+        assert 2**lx < p < 2**(lx + 1)
+        assert all(p % d for d in range(2, int(p ** 0.5) + 1))
+        assert all(any(q % d == 0 for d in range(2, int(q ** 0.5) + 1))
+                   for q in range(2**lx + 1, p))
+
+
+# --------------------------------------------------------------------------
+# Alg. drelu: brute force against the closed form and the plaintext sign
+# --------------------------------------------------------------------------
+
+def _closed_form_dprime(ell, lx, c, fs0, fs1):
+    """DReLU' from Thm. newtrc2's exact form: reconstructed
+    u_i = ((x' >> (c+i)) + carry_(c+i)) mod 2^lx with x' = fs0 + fs1 and
+    R' = -fs1, v_i = u_i + u_(i+1) - 1 (v_lx = u_lx - 1); DReLU' = 1 iff some
+    v_i = 0.  Masking by r != 0 in Z_p, shuffling and resharing keep the
+    zero set (Alg. drelu steps 5-9)."""
+    m, mx = (1 << ell) - 1, (1 << lx) - 1
+    xp = (fs0.astype(object) + fs1.astype(object)) & m
+    Rp = (-fs1.astype(object)) & m
+    us = []
+    for i in range(lx + 1):
+        k1 = c + i
+        carry = ((xp % (1 << k1)) + (Rp % (1 << k1))) >= (1 << k1)
+        us.append(((xp >> k1) + carry.astype(object)) & mx)
+    d = np.zeros(fs0.size, dtype=bool)
+    for i in range(lx + 1):
+        nxt = us[i + 1] if i < lx else 0
+        d |= ((us[i] + nxt - 1) & mx) == 0
+    return d
+
+
+def _c0_exceptions(lx):
+    """Magnitudes where, at c = 0, the mod-2^lx wrap of v_0 can vanish for a
+    negative flipped input: xi + ceil(xi/2) in {2^lx - 1, 2^lx} (for lx = 2
+    the wrap of v_1 adds xi = 3)."""
+    out = set()
+    for T in ((1 << lx) - 1, 1 << lx):
+        for xi in range(max(1, 2 * T // 3 - 2), 2 * T // 3 + 3):
+            if xi < (1 << lx) and xi + (xi + 1) // 2 == T:
+                out.add(xi)
+    if lx == 2:
+        out.add(3)
+    return out
+
+
+def _predicted_miss(xi, lx, c):
+    """Sign misses allowed on the domain: at c = 0 exactly the magnitudes
+    above; at c > 0 also |x| < 2^c (the window skips those bits) and a band
+    of half-width 2^c around each xi* 2^c."""
+    if xi < (1 << c):
+        return True
+    return any(abs(xi - e * (1 << c)) < (1 << c) for e in _c0_exceptions(lx))
+
+
+BRUTE = [(8, 2, 0), (8, 3, 0), (8, 4, 0), (8, 3, 1), (8, 2, 2), (10, 5, 0), (10, 4, 1), (10, 4, 2)]
+
+
+@pytest.mark.parametrize("ell,lx,c", BRUTE)
+def test_drelu_bruteforce(ell, lx, c):
+    """Every x in Z_{2^l}, every R in Z_{2^l}, t in {0, 1}."""
+    P = O.params(ell, lx, c)
+    L, p, m = lx + 1, P.p, (1 << ell) - 1
+    X, RR, T = np.meshgrid(np.arange(1 << ell, dtype=np.uint64), np.arange(1 << ell, dtype=np.uint64),
+                           np.array([0, 1], dtype=np.uint64), indexing="ij")
+    X, RR, T = X.ravel(), RR.ravel(), T.ravel()
+    s0 = (X + RR) & np.uint64(m)
+    s1 = (np.uint64(0) - RR) & np.uint64(m)
+    n = X.size
+    rng = np.random.default_rng(ell * 100 + lx * 10 + c)
+    fy = rng.integers(0, 2**32, size=(n, L), dtype=np.uint64).astype(np.uint32)
+    r = rng.integers(1, p, size=(n, L)).astype(np.uint32)
+    z = rng.integers(0, p, size=(n, L)).astype(np.uint32)
+    d = O.drelu_core_many(P, s0, s1, T.astype(np.uint8), fy, r, z).astype(bool)
+    neg = lambda a: (np.uint64(0) - a) & np.uint64(m)
+    fs0 = np.where(T == 1, neg(s0), s0)
+    fs1 = np.where(T == 1, neg(s1), s1)
+    assert (d == _closed_form_dprime(ell, lx, c, fs0, fs1)).all()
+    # plaintext sign: DReLU = DReLU' xor t equals [x >= 0] on the domain
+    # |x| < 2^(lx+c), x != 0 (DReLU(0) is irrelevant for ReLU, Sec. 5.4),
+    # except on the exception set of the wrap of v_0.
+    xs = X.astype(np.int64)
+    xs = np.where(xs >= 1 << (ell - 1), xs - (1 << ell), xs)
+    got = d.astype(np.int64) ^ T.astype(np.int64)
+    dom = (np.abs(xs) < (1 << (lx + c))) & (xs != 0)
+    bad = dom & (got != (xs >= 0))
+    mags = set(np.abs(xs[bad]).tolist())
+    if c == 0 and lx >= 3:
+        assert mags == _c0_exceptions(lx)
+    else:
+        assert all(_predicted_miss(xi, lx, c) for xi in mags)
+    if lx >= 3:
+        assert bad.sum() <= 0.25 * dom.sum()
+
+
+def test_drelu_exception_l64():
+    """The c = 0 exception magnitude at l = 64, lx = 24: xi* = 11,184,810
+    (xi + ceil(xi/2) = 2^24 - 1) fails for about half of the (R, t) draws,
+    xi* + 1 never does, and random in-range inputs give the exact sign."""
+    P = O.params(64, 24, 0)
+    n = 600
+    for xi, expect_fail in ((11184810, True), (11184811, False)):
+        for sgn in (1, -1):
+            x = np.full(n, (sgn * xi) % 2**64, dtype=np.uint64)
+            s0, s1 = O.share(64, x, seed=77, tid=sgn + 5)
+            o0, o1 = O.drelu(P, s0, s1, seed=99, tid=sgn + 5)
+            got = O.reconstruct(64, o0, o1)
+            fails = int((got != (1 if sgn > 0 else 0)).sum())
+            if expect_fail:
+                assert 0.3 * n < fails < 0.7 * n
+            else:
+                assert fails == 0
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(4000, 23, seed=3)
+    xs = xs[np.abs(xs) != 11184810]
+    xs = xs[xs != 0]
+    s0, s1 = O.share(64, xs.astype(np.uint64), seed=1, tid=2)
+    o0, o1 = O.drelu(P, s0, s1, seed=3, tid=2)
+    assert (O.reconstruct(64, o0, o1) == (xs >= 0)).all()
+
+
+def test_relu_beaver_identity():
+    """Alg. relu: reconstruct(ReLU shares) = x * (DReLU' xor t) mod 2^l
+    exactly (Beaver identity), and equals max(x, 0) on in-domain inputs."""
+    from paper_2309_04909_gb300 import workloads as W
+    for ell, lx, c, bits in ((64, 24, 0, 23), (32, 9, 14, 22), (32, 14, 4, 17), (16, 5, 2, 6)):
+        P = O.params(ell, lx, c)
+        xs = W.magnitude_bounded_ints(3000, bits, seed=ell + lx)
+        x = xs.astype(np.uint64) & np.uint64(_mask(ell))
+        s0, s1 = O.share(ell, x, seed=5, tid=1)
+        o0, o1, aud = O.relu(P, s0, s1, seed=6, tid=1, audit=True)
+        rec = O.reconstruct(ell, o0, o1)
+        b = aud["dprime"].astype(np.uint64) ^ aud["t"].astype(np.uint64)
+        want = (x.astype(object) * b.astype(object)) % (1 << ell)
+        assert (rec.astype(object) == want).all()
+        signed = O.to_signed(rec, ell)
+        miss = np.abs(xs[signed != np.maximum(xs, 0)])
+        # every miss lies in the predicted exception set of the sign test
+        assert all(_predicted_miss(int(xi), lx, c) for xi in miss)
+        assert miss.size < 0.08 * xs.size
+
+
+def test_drelu_output_shares_and_messages():
+    """Alg. drelu steps 10-11: reconstructed output is DReLU' xor t; the
+    messages P2 receives reconstruct to a zero exactly when DReLU' = 1; every
+    message lies in Z_p."""
+    P = O.params(64, 24, 0)
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(2000, 20, seed=8)
+    s0, s1 = O.share(64, xs.astype(np.uint64), seed=3, tid=4)
+    o0, o1, aud = O.drelu(P, s0, s1, seed=3, tid=4, audit=True)
+    rec = O.reconstruct(64, o0, o1)
+    assert (rec == (aud["dprime"] ^ aud["t"])).all()
+    w = (aud["w0"].astype(np.uint64) + aud["w1"].astype(np.uint64)) % np.uint64(P.p)
+    assert ((w == 0).any(axis=1) == aud["dprime"].astype(bool)).all()
+    assert (aud["w0"] < P.p).all() and (aud["w1"] < P.p).all()
+    # step 10: P2's reply [DReLU']_1 and P0's seed02 share [DReLU']_0 add up to
+    # DReLU'; step 11 unflips: o0 = t + (1-2t) d0, o1 = (1-2t) d1
+    t = aud["t"].astype(object)
+    sgn = [1 - 2 * v for v in t]
+    d1 = aud["reply"].astype(object)
+    d0 = [((int(a) - int(tt)) * s) % 2**64 for a, tt, s in zip(o0, t, sgn)]
+    assert all((a + int(b)) % 2**64 == int(dp) for a, b, dp in zip(d0, d1, aud["dprime"]))
+    assert all(int(b) == (int(d) * s) % 2**64 for b, d, s in zip(o1, d1, sgn))
+
+
+def test_beaver_mul_exact():
+    from paper_2309_04909_gb300 import workloads as W
+    for ell in (64, 32, 8):
+        x = W.magnitude_bounded_ints(5000, min(ell - 2, 40), seed=ell).astype(np.uint64)
+        y = W.magnitude_bounded_ints(5000, min(ell - 2, 40), seed=ell + 1).astype(np.uint64)
+        mk = np.uint64(_mask(ell))
+        x &= mk
+        y &= mk
+        x0, x1 = O.share(ell, x, seed=21, tid=1)
+        y0, y1 = O.share(ell, y, seed=21, tid=2)
+        o0, o1 = O.mul_beaver(ell, x0, x1, y0, y1, seed=22, tid=3)
+        want = (x.astype(object) * y.astype(object)) % (1 << ell)
+        assert (O.reconstruct(ell, o0, o1).astype(object) == want).all()
+
+
+def test_share_reconstruct_and_uniformity():
+    x = np.arange(1000, dtype=np.uint64)
+    for ell in (8, 32, 64):
+        xm = x & np.uint64(_mask(ell))
+        s0, s1 = O.share(ell, xm, seed=3, tid=7)
+        assert (O.reconstruct(ell, s0, s1) == xm).all()
+        assert (s0 <= np.uint64(_mask(ell))).all() and (s1 <= np.uint64(_mask(ell))).all()
+    # [x]_1 = -R is uniform: byte histogram of 2^16 shares is flat (chi^2)
+    s0, s1 = O.share(64, np.zeros(1 << 16, np.uint64), seed=4, tid=1)
+    hist = np.bincount((s1 & np.uint64(255)).astype(np.int64), minlength=256)
+    chi2 = ((hist - 256.0) ** 2 / 256.0).sum()
+    assert chi2 < 400  # 255 dof; p ~ 1e-8
+
+
+def test_encode_round_half_even():
+    f = 4
+    x = np.array([0.0, 1.0, -1.0, 0.5 / 16, 1.5 / 16, 2.5 / 16, -0.5 / 16, -1.5 / 16, 3.03125])
+    got = O.to_signed(O.encode(x, f, 32), 32)
+    assert got.tolist() == [0, 16, -16, 0, 2, 2, 0, -2, 48]
+    assert O.encode(np.array([-1.0]), 16, 64)[0] == np.uint64(2**64 - 2**16)
+
+
+# --------------------------------------------------------------------------
+# Philox-4x32-10 against an independent library implementation
+# --------------------------------------------------------------------------
+
+def test_philox_matches_library_implementation():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(2)
+    rows = rng.integers(0, 2**32, size=(200, 6), dtype=np.uint64).tolist()
+    rows += [[0] * 6, [2**32 - 1] * 6, [1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0]]
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    proc = subprocess.run([sys.executable, os.path.join(HERE, "philox_library_ref.py")],
+                          input=json.dumps(rows), capture_output=True, text=True, env=env,
+                          timeout=600)
+    assert proc.returncode == 0, proc.stderr[-2000:]
+    ref = json.loads(proc.stdout)
+    for row, want in zip(rows, ref):
+        assert O.philox(row[:4], row[4:]) == want
+
+
+def test_stream_layout():
+    # word j of a stream is word j % 4 of block j / 4 of the documented counter
+    seed, pair, pur, tid, elem = 0x0123456789ABCDEF, O.PAIR_01, O.PUR_MASK, 7, (5 << 32) | 9
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(9):
+        ctr = [elem & 0xFFFFFFFF, tid, j // 4, (pair << 24) | (pur << 16) | (elem >> 32)]
+        assert O.stream_word(seed, pair, pur, tid, elem, j) == O.philox(ctr, key)[j % 4]
