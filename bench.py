@@ -1,0 +1,387 @@
+"""Benchmark of the Bicoptor 2.0 hot path on GB300.
+
+Default workload (one "step" = every row of the hot path over one batch):
+  Z_{2^64}, f = 16: Beaver product of two share tensors of N = 2^22 Gaussian
+  (sigma = 4) reals -> SecureML and deterministic truncation by 16 bits ->
+  ReLU (lx = 24 key bits, c = 0) of the probabilistically truncated product.
+  Three parties simulated on one GPU; inputs resident in HBM.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ReLU elems/s on 1 GB300 (3 parties sim.), % roofline, batched vs plain; p99 ms"
+WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
+            "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated product")
+N_DEFAULT = 1 << 22
+RING, FRAC, K_TRUNC, LX, KEY_OFF = 64, 16, 16, 24, 0
+SEED = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu extras")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_inputs(n: int, seed: int = SEED):
+    from paper_2309_04909_gb300 import workloads as W
+    X = W.gaussian_reals(n, 4.0, seed=seed, stream=0)
+    Y = W.gaussian_reals(n, 4.0, seed=seed, stream=1)
+    xi = np.rint(np.ldexp(X, FRAC)).astype(np.int64)
+    yi = np.rint(np.ldexp(Y, FRAC)).astype(np.int64)
+    return xi, yi
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_chain(xi, yi, seed, threads):
+    """The oracle's run of one step over a sample (first elements)."""
+    import oracle as O
+    n = xi.size
+    idx = np.arange(n, dtype=np.uint64)
+    x0, x1 = O.share(RING, xi.astype(np.uint64), seed, 1, idx=idx)
+    y0, y1 = O.share(RING, yi.astype(np.uint64), seed, 2, idx=idx)
+    p0, p1 = O.mul_beaver(RING, x0, x1, y0, y1, seed, 3, idx=idx)
+    t0, t1 = O.trunc_prob(RING, K_TRUNC, p0, p1)
+    O.trunc_det(RING, K_TRUNC, 0, p0, p1)
+    O.relu(O.params(RING, LX, KEY_OFF), t0, t1, seed, 4, idx=idx, threads=threads)
+
+
+def cpu_rate(n_target_s: float, xi, yi, threads):
+    """Time the oracle on a sample sized for about n_target_s seconds."""
+    m = 2048
+    t0 = time.perf_counter()
+    oracle_chain(xi[:m], yi[:m], 77, threads)
+    dt = time.perf_counter() - t0
+    per = dt / m
+    m2 = int(min(xi.size, max(m, n_target_s / per)))
+    t0 = time.perf_counter()
+    oracle_chain(xi[:m2], yi[:m2], 77, threads)
+    dt = time.perf_counter() - t0
+    return m2 / dt, m2, dt
+
+
+def run_reference(args):
+    import oracle as O
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = O.max_threads()
+    xi, yi = workload_inputs(min(args.n, 1 << 20))
+    # calibrate: elements per step so that warmup + steps take ~2 minutes
+    m = 1024
+    t0 = time.perf_counter()
+    oracle_chain(xi[:m], yi[:m], 5, threads)
+    per = (time.perf_counter() - t0) / m
+    total_steps = max(1, args.steps + args.warmup)
+    m_step = int(max(256, min(xi.size, 120.0 / (per * total_steps))))
+    for w in range(args.warmup):
+        oracle_chain(xi[:m_step], yi[:m_step], 1000 + w, threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle_chain(xi[:m_step], yi[:m_step], 2000 + s, threads)
+    dt = time.perf_counter() - t0
+    value = m_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elems/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "sample_per_step": m_step},
+        "cpu_baseline": {"value": value, "unit": "elems/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {m_step} elements of the workload per step"},
+        "e2e": {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2309_04909_gb300 import Context, Params, costmodel
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    n = args.n
+    xi, yi = workload_inputs(n, seed=SEED + rank)   # each rank its own batch (replicas)
+    ctx = Context(0xB1C0_2309_0490_9000 + rank, device=local)
+    x0, x1 = ctx.share(RING, torch.from_numpy(xi).to(dev), tensor_id=1)
+    y0, y1 = ctx.share(RING, torch.from_numpy(yi).to(dev), tensor_id=2)
+    prm = Params(RING, LX, KEY_OFF)
+    buf = ctx.linear_relu_buffers(RING, K_TRUNC, n)
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        ctx.mul_beaver(RING, x0, x1, y0, y1, 3, out=(buf["prod0"], buf["prod1"]))
+        ctx.trunc_prob(RING, K_TRUNC, buf["prod0"], buf["prod1"], out=(buf["trc0"], buf["trc1"]))
+        ctx.trunc_det(RING, K_TRUNC, 0, buf["prod0"], buf["prod1"], out=(buf["det0"], buf["det1"]))
+        if ev is not None:
+            ev[1].record()
+        ctx.relu(prm, buf["trc0"], buf["trc1"], 4, out=(buf["relu0"], buf["relu1"]))
+        if ev is not None:
+            ev[2].record()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record()
+    for s in range(args.steps):
+        step(evs[s])
+    end.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop() if clocks else None
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    relu_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    relu_avg = sum(relu_ms) / len(relu_ms)
+    value = n * args.steps * world / (total_ms / 1e3)
+    ops = costmodel.int_ops_per_element(LX, RING, relu=True)
+    peak = costmodel.int_issue_peak_ops()
+    achieved = ops * n / (relu_avg / 1e3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "ring_bits": RING, "frac_bits": FRAC,
+                   "trunc_bits": K_TRUNC, "lx": LX, "key_off": KEY_OFF, "p": 16777259,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set 384 MB per step > 129 MB L2; no flush"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "Tops/s (int32)", "frac": achieved / peak, "traffic": None,
+                     "kernel": "relu_kernel<uint64_t,24,ReLU>",
+                     "ops_per_element": ops, "kernel_ms": relu_avg,
+                     "peak_basis": "152 SM x 4 issue/clk x 32 lanes x 2070 MHz"},
+        "gpu_launches": 4 * args.steps,
+        "clocks": ck,
+        "step_breakdown_ms": {"product_and_truncations": sum(pre_ms) / len(pre_ms),
+                              "relu": relu_avg},
+    }
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), dev)
+        line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
+        if world == 1:
+            rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
+            line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
+                                    "kind": "oracle",
+                                    "sample": f"first {m2} elements of the workload, full step "
+                                              f"(share, product, both truncations, ReLU), {dt:.1f} s"}
+        line["batched_vs_plain"] = vgg16_batched_vs_plain(ctx, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _threads():
+    import oracle as O
+    return O.max_threads()
+
+
+def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, dev):
+    """The same step through the host-buffer entry point: pinned host inputs,
+    copies in, compute, copies out, inside the timed region."""
+    import torch
+    hx = [t.cpu().pin_memory() for t in (x0, x1, y0, y1)]
+    out = {k: torch.empty(n, dtype=torch.int64).pin_memory() for k in ("relu0", "relu1")}
+    out["det0"] = torch.empty(n, dtype=torch.int64).pin_memory()
+    out["det1"] = torch.empty(n, dtype=torch.int64).pin_memory()
+    ctx.reserve(1 << 20)
+    for _ in range(3):
+        ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
+            "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
+            "api": "bc_linear_relu_host (chunks of 2^20, two streams)"}
+
+
+def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):
+    """Probabilistic vs deterministic truncation failures against the
+    plaintext, with the closed form sum |x| / 2^l, on the product and on a
+    stress sweep of large-magnitude inputs."""
+    import torch
+    from paper_2309_04909_gb300 import workloads as W
+    out = {}
+    prod = torch.from_numpy(xi * yi).to(dev)        # |x y| < 2^63 for these inputs
+    pf = ctx.count_trunc_failures(RING, K_TRUNC, prod, buf["trc0"], buf["trc1"])
+    df = ctx.count_trunc_failures(RING - K_TRUNC, K_TRUNC, prod, buf["det0"], buf["det1"])
+    expect = float(np.abs(xi.astype(np.float64) * yi.astype(np.float64)).sum() / 2.0**64)
+    out["product"] = {"prob": pf, "det": df, "prob_expected": expect}
+    sweep = {}
+    n = 1 << 22
+    for bits in (48, 56, 60, 62):
+        x = W.magnitude_bounded_ints(n, bits, seed=bits)
+        xg = torch.from_numpy(x).to(dev)
+        s0, s1 = ctx.share(RING, xg, tensor_id=7000 + bits)
+        p0, p1 = ctx.trunc_prob(RING, K_TRUNC, s0, s1)
+        d0, d1 = ctx.trunc_det(RING, K_TRUNC, 0, s0, s1)
+        sweep[str(bits)] = {
+            "prob": ctx.count_trunc_failures(RING, K_TRUNC, xg, p0, p1),
+            "det": ctx.count_trunc_failures(RING - K_TRUNC, K_TRUNC, xg, d0, d1),
+            "prob_expected": float(np.abs(x.astype(np.float64)).sum() / 2.0**64)}
+    out["stress_sweep_mag_bits"] = sweep
+    return out
+
+
+def vgg16_batched_vs_plain(ctx, dev, batch=128):
+    """Config-3 shape: the 13 ReLU tensors of a VGG-16 on 32x32 inputs for
+    `batch` images (1,664 tensors, 35,389,440 elements at batch 128), l = 64,
+    f = 16, per-layer sigma in [0.5, 8].  Plain = one launch per tensor
+    (eager, and replayed from a CUDA graph); batched = one persistent launch
+    over the tile queue (autotuned tile / CTAs per SM), eager and graph."""
+    import torch
+    from paper_2309_04909_gb300 import Params, workloads as W
+    from paper_2309_04909_gb300.batch import ReluBatch, autotune, time_ms
+    ts = W.vgg16_batch(batch, seed=2)
+    allx = np.concatenate([np.rint(np.ldexp(r, 16)).astype(np.int64) for r in ts.reals])
+    total = allx.size
+    s0, s1 = ctx.share(64, torch.from_numpy(allx).to(dev), tensor_id=11)
+    o0 = torch.empty(total, dtype=torch.int64, device=dev)
+    o1 = torch.empty(total, dtype=torch.int64, device=dev)
+    q0 = torch.empty_like(o0)
+    q1 = torch.empty_like(o1)
+    prm = Params(64, 24, 0)
+    items, plain_items, off = [], [], 0
+    for t, sz in enumerate(ts.sizes):
+        sl = slice(off, off + sz)
+        items.append((prm, s0[sl], s1[sl], o0[sl], o1[sl], 20000 + t))
+        plain_items.append((prm, s0[sl], s1[sl], q0[sl], q1[sl], 20000 + t))
+        off += sz
+
+    def plain():
+        for it in plain_items:
+            ctx.relu(it[0], it[1], it[2], it[5], out=(it[3], it[4]))
+
+    plain_ms = time_ms(plain, reps=3, warmup=1)
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        plain()
+    plain_graph_ms = time_ms(g.replay, reps=5, warmup=1)
+    best = autotune(ctx, items, reps=2, use_cache=False)
+    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"])
+    batched_ms = time_ms(b.run, reps=5, warmup=1)
+    b.capture()
+    batched_graph_ms = time_ms(b.run, reps=5, warmup=1)
+    identical = bool(torch.equal(o0, q0) and torch.equal(o1, q1))
+    return {"workload": f"VGG-16 32x32 ReLU set, batch {batch}: {len(ts.sizes)} tensors, "
+                        f"{total} elements, l=64 f=16 lx=24",
+            "plain_eager_ms": plain_ms, "plain_graph_ms": plain_graph_ms,
+            "batched_ms": batched_ms, "batched_graph_ms": batched_graph_ms,
+            "speedup_vs_plain_eager": plain_ms / batched_graph_ms,
+            "speedup_vs_plain_graph": plain_graph_ms / batched_graph_ms,
+            "batched_elems_per_s": total / (batched_graph_ms / 1e3),
+            "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+            "status": b.status(), "identical_to_plain": identical}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * bicoptor.h -- C-ABI of the GB300 Bicoptor 2.0 hot path.
+ *
+ * Paper: "Bicoptor 2.0: Addressing Challenges in Probabilistic Truncation for
+ * Enhanced Privacy-Preserving Machine Learning" (arXiv 2309.04909).
+ *
+ * Three parties (P0, P1 holding 2-of-2 additive shares in Z_{2^l}, P2 the
+ * helper; Sec. 2.1 "unbalanced mode") are simulated on one GPU.  Every step of
+ * every party runs in this library's CUDA kernels; the messages the parties
+ * would exchange are kept in registers (or written to audit buffers on
+ * request) and their sizes are counted in bc_comm.
+ *
+ * Conventions for every entry point:
+ *  - Share arrays are DEVICE pointers owned by the caller, except where an
+ *    entry point's name ends in _host.  A ring element of Z_{2^l} is stored in
+ *    a uint32_t lane when l <= 32 and a uint64_t lane when 32 < l <= 64, in
+ *    canonical form (bits >= l are zero).  Inputs that are not canonical give
+ *    undefined (but memory-safe) results.
+ *  - Calls are asynchronous and ordered on the context's stream.  They return
+ *    BC_OK (0) or a negative BC_E* code; on an error nothing is launched.
+ *  - Hot calls allocate nothing: device workspace is reserved by bc_create
+ *    and by bc_reserve.
+ *  - Randomness: every pseudorandom value is Philox-4x32-10 keyed by the
+ *    context seed, with the counter (element index, tensor_id, block,
+ *    pair/purpose tag).  Results therefore depend only on (seed, tensor_id,
+ *    element index, input), never on batch composition or launch shape.
+ */
+#ifndef BICOPTOR_H
+#define BICOPTOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define BC_OK 0
+#define BC_EINVAL (-1)   /* bad argument: sizes, parameters, NULL pointers      */
+#define BC_ENOMEM (-2)   /* device workspace could not be reserved               */
+#define BC_ECUDA (-3)    /* a CUDA call failed (see bc_last_cuda_error)          */
+#define BC_ETIMEOUT (-4) /* a bounded device wait gave up (persistent batch)     */
+#define BC_ECHECK (-5)   /* a device-side consistency check failed               */
+
+typedef struct bc_ctx bc_ctx;
+
+/* Parameters of Alg. drelu / Alg. relu (Sec. 5.4, key bits Sec. 6.1).
+ *   ring_bits  l, 2..64
+ *   lx         key bits, 1..31; the protocol works on lx+1 windows
+ *   key_off    c >= 0, the lowest key bit; the window of step 3 for index i
+ *              keeps bits c+i .. c+i+lx-1, so c + 2*lx <= l is required
+ *   p          prime with 2^lx < p < 2^(lx+1) (Alg. modswitch needs
+ *              log2 p = lx+1); 0 selects the smallest prime above 2^lx      */
+typedef struct {
+  int ring_bits;
+  int lx;
+  int key_off;
+  uint32_t p;
+} bc_drelu_params;
+
+/* Protocol communication counted by the library, in BITS, summed over calls
+ * since bc_create or bc_reset_comm.  A Z_p element counts ceil(log2 p) =
+ * lx+1 bits, a ring element l bits (Table "compare": one-pass cost
+ * (lx+1)*(lx+1) bits per sending party). */
+typedef struct {
+  uint64_t p0_to_p2, p1_to_p2;   /* masked, shuffled, reshared w (Alg. drelu step 8) */
+  uint64_t p2_to_p0, p2_to_p1;   /* DReLU' reply (step 10) / e = DReLU' - b (Alg. relu) */
+  uint64_t p0_to_p1, p1_to_p0;   /* Beaver openings d = x - a (and e for bc_mul_beaver) */
+  uint64_t pre_p2_to_p1;         /* preprocessing: [c]_1 of the Beaver triple           */
+  uint64_t rounds;               /* online communication rounds                        */
+  uint64_t elements;             /* elements processed by interactive protocols        */
+  uint64_t calls;                /* protocol calls                                     */
+} bc_comm;
+
+/* Optional materialised messages of the next DReLU/ReLU calls (device
+ * pointers, NULL = not wanted).  n elements, L = lx+1 slots:
+ *   w0, w1      uint32 [n * L]  P0->P2 and P1->P2 messages, slot-major per element
+ *   reply       lanes  [n]      P2->P1 [DReLU']_1 (drelu) or e (relu)
+ *   open0/open1 lanes  [n]      P0->P1 / P1->P0 share of d = x - a (relu)
+ *   pre_c1      lanes  [n]      P2->P1 preprocessing [c]_1 (relu)
+ *   t, dprime   uint8  [n]      the flip bit and P2's DReLU'              */
+typedef struct {
+  uint32_t *w0, *w1;
+  void *reply, *open0, *open1, *pre_c1;
+  uint8_t *t, *dprime;
+} bc_audit;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on `device` using `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  `seed` keys every pre-shared seed of the
+ * simulation.  *out receives the context; free it with bc_destroy. */
+int bc_create(bc_ctx **out, uint64_t seed, int device, void *cuda_stream);
+int bc_destroy(bc_ctx *ctx);
+int bc_set_stream(bc_ctx *ctx, void *cuda_stream);
+int bc_synchronize(bc_ctx *ctx);
+const char *bc_strerror(int code);
+/* Text of the last CUDA error seen by this context (empty if none). */
+const char *bc_last_cuda_error(bc_ctx *ctx);
+
+/* Smallest prime p with 2^lx < p < 2^(lx+1) (Alg. modswitch); 0 if lx is
+ * outside 1..31. Host-only. */
+uint32_t bc_prime_above(int lx);
+
+/* ---- sharing (Sec. 2.2) ------------------------------------------------- */
+
+/* Dealer: [x]_0 = x + R, [x]_1 = -R mod 2^l for fixed-point plaintexts
+ * x (int64, device, n entries; reduced mod 2^l), R from the dealer stream of
+ * (seed, tensor_id, element index).  Test/dealer utility, not a party's view. */
+int bc_share(bc_ctx *ctx, int ring_bits, const int64_t *x, size_t n, uint32_t tensor_id,
+             void *sh0, void *sh1);
+/* x = [x]_0 + [x]_1 mod 2^l into lanes (device). */
+int bc_reconstruct(bc_ctx *ctx, int ring_bits, const void *sh0, const void *sh1, size_t n,
+                   void *x_out);
+
+/* ---- non-interactive truncations and modulo switch ---------------------- */
+
+/* Alg. smltrc (SecureML): P0 cut([x]_0, k) mod 2^l, P1 2^l - cut(2^l - [x]_1, k)
+ * mod 2^l.  Outputs in Z_{2^l}.  0 <= k < l.  In-place allowed. */
+int bc_trunc_prob(bc_ctx *ctx, int ring_bits, int k, const void *sh0, const void *sh1,
+                  size_t n, void *o0, void *o1);
+/* Alg. newtrc2 (Alg. newtrc when k2 = 0): keep bits k1 .. l-k2-1; outputs in
+ * Z_{2^(l-k1-k2)} with that ring's lane width.  k1, k2 >= 0, k1 + k2 < l. */
+int bc_trunc_det(bc_ctx *ctx, int ring_bits, int k1, int k2, const void *sh0, const void *sh1,
+                 size_t n, void *o0, void *o1);
+/* Alg. modswitch: shares in Z_{2^lp} (uint32 lanes, 1 <= lp <= 31) to shares
+ * in Z_p (uint32), zero iff zero.  p prime, 2^lp < p < 2^32. */
+int bc_mod_switch(bc_ctx *ctx, int lp, uint32_t p, const void *sh0, const void *sh1, size_t n,
+                  uint32_t *o0, uint32_t *o1);
+
+/* Beaver multiplication (Table "notation", Alg. relu preprocessing): the
+ * triple comes from seed02/seed12, P2 sends [c]_1 to P1, d = x - a and
+ * e = y - b are opened; [xy] = de + d[b] + e[a] + [c].  Exact in Z_{2^l}. */
+int bc_mul_beaver(bc_ctx *ctx, int ring_bits, const void *x0, const void *x1, const void *y0,
+                  const void *y1, size_t n, uint32_t tensor_id, void *o0, void *o1);
+
+/* ---- DReLU / ReLU (Alg. drelu, Alg. relu) ------------------------------- */
+
+/* Shares of DReLU(x) in Z_{2^l}: one fused kernel runs P0's and P1's steps
+ * 1-8, P2's step 9 and the reply/unflip of steps 10-11 per element. */
+int bc_drelu(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+             size_t n, uint32_t tensor_id, void *o0, void *o1);
+/* Shares of ReLU(x) = x * DReLU(x) in Z_{2^l} via the seeded Beaver triple. */
+int bc_relu(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+            size_t n, uint32_t tensor_id, void *o0, void *o1);
+
+/* Materialise the messages of subsequent DReLU/ReLU calls into `bufs`
+ * (NULL turns auditing off).  The buffers must hold the call's n elements. */
+int bc_set_audit(bc_ctx *ctx, const bc_audit *bufs);
+
+int bc_get_comm(bc_ctx *ctx, bc_comm *out);
+int bc_reset_comm(bc_ctx *ctx);
+
+/* ---- batched ReLU over many tensors (persistent tile queue) -------------- */
+
+#define BC_OP_RELU 0
+#define BC_OP_DRELU 1
+
+typedef struct {
+  const void *sh0, *sh1;   /* input shares (lanes of params.ring_bits)   */
+  void *o0, *o1;           /* output shares                              */
+  uint64_t n;              /* elements                                   */
+  uint32_t tensor_id;      /* keys the randomness of this tensor          */
+  int op;                  /* BC_OP_RELU or BC_OP_DRELU                   */
+  bc_drelu_params params;
+} bc_tensor_desc;
+
+/* Tile configuration of the batched launch (0 fields = library default). */
+typedef struct {
+  int tile_elems;          /* elements per queue tile                     */
+  int ctas_per_sm;         /* resident CTAs per SM of the persistent grid */
+} bc_batch_config;
+
+/* Plan a batch: build the tile table of `count` tensors on the host and copy
+ * it to device workspace owned by the context (grown here, not in
+ * bc_relu_batch_run).  The plan stays valid until the next bc_relu_batch_plan. */
+int bc_relu_batch_plan(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
+                       const bc_batch_config *cfg);
+/* Run the planned batch as one persistent launch pulling tiles from an atomic
+ * work counter.  Stream-capturable (no host synchronisation inside). */
+int bc_relu_batch_run(bc_ctx *ctx);
+/* plan + run. */
+int bc_relu_batch(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
+                  const bc_batch_config *cfg);
+/* Status word of the last batched launch (BC_OK or BC_ETIMEOUT/BC_ECHECK);
+ * synchronises the context's stream. */
+int bc_batch_status(bc_ctx *ctx);
+
+/* ---- fused product -> truncation -> ReLU (Sec. 4, Alg. smltrc/newtrc, Alg. relu) */
+
+typedef struct {
+  int ring_bits;            /* l of x, y, the product and the ReLU           */
+  int trunc_bits;           /* k removed after the product (2f -> f)          */
+  bc_drelu_params relu;     /* ReLU parameters, relu.ring_bits == ring_bits   */
+  const void *x0, *x1, *y0, *y1;
+  size_t n;
+  uint32_t tensor_id;       /* product uses tensor_id, ReLU tensor_id + 1     */
+  void *prod0, *prod1;      /* product shares (workspace, l-bit lanes)        */
+  void *trc0, *trc1;        /* Alg. smltrc output (l-bit lanes)               */
+  void *det0, *det1;        /* Alg. newtrc output in Z_{2^(l-k)}              */
+  void *relu0, *relu1;      /* ReLU of the probabilistically truncated product */
+} bc_linear_relu_args;
+
+/* All device pointers: product, both truncations, ReLU, back to back. */
+int bc_linear_relu(bc_ctx *ctx, const bc_linear_relu_args *a);
+/* Same with HOST pointers for x0,x1,y0,y1 (input) and relu0,relu1,det0,det1
+ * (output); prod/trc fields are ignored.  Staged through device buffers
+ * reserved by bc_reserve(ctx, chunk) in chunks of at most `chunk` elements,
+ * copies overlapped with compute on two streams.  Returns after the results
+ * are in host memory. */
+int bc_linear_relu_host(bc_ctx *ctx, const bc_linear_relu_args *a);
+/* Reserve device staging for bc_linear_relu_host of chunks up to
+ * `max_chunk` elements at ring_bits <= 64. */
+int bc_reserve(bc_ctx *ctx, size_t max_chunk);
+
+/* ---- truncation-failure statistics (evaluation only) --------------------- */
+
+/* Count elements whose reconstructed truncation differs from the plaintext
+ * floor(x / 2^k) by more than one (the e1 failure of Sec. 3), given the
+ * plaintext x (int64, device) and output shares in Z_{2^out_bits}.
+ * *count (device uint64) is incremented. */
+int bc_count_trunc_failures(bc_ctx *ctx, int out_bits, int k, const int64_t *x, const void *o0,
+                            const void *o1, size_t n, unsigned long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BICOPTOR_H */

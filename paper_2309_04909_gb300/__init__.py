@@ -1,0 +1,306 @@
+"""GB300-native Bicoptor 2.0 hot path: secret-shared truncation, modulo switch
+and DReLU/ReLU over Z_{2^l} with three parties simulated on one GPU.
+
+This module is a thin binding over the C-ABI of include/bicoptor.h: it
+marshals torch tensors (device memory, streams) into plain pointers.  Every
+step of the protocol runs in the CUDA kernels of libbicoptor.so; there is no
+CPU fallback, and every call raises if the library is missing.
+
+Lanes: a ring element of Z_{2^l} is stored in an int32 tensor (l <= 32) or an
+int64 tensor (l <= 64), read as unsigned; Z_p values in int32 tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import torch
+
+from . import _native
+from ._native import Audit, BatchConfig, Comm, DreluParams, LinearReluArgs, TensorDesc
+
+__all__ = ["Context", "Params", "BicoptorError", "lane_dtype", "prime_above", "build"]
+
+OP_RELU, OP_DRELU = 0, 1
+
+
+class BicoptorError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    return _native.build(force=force)
+
+
+def lane_dtype(bits: int) -> torch.dtype:
+    return torch.int64 if bits > 32 else torch.int32
+
+
+def prime_above(lx: int) -> int:
+    return int(_native.lib().bc_prime_above(lx))
+
+
+@dataclass(frozen=True)
+class Params:
+    """Alg. drelu parameters: ring bits l, key bits lx, key offset c, prime p (0 = derive)."""
+    ring_bits: int
+    lx: int
+    key_off: int = 0
+    p: int = 0
+
+    def c_struct(self) -> DreluParams:
+        return DreluParams(self.ring_bits, self.lx, self.key_off, self.p)
+
+    @property
+    def slots(self) -> int:
+        return self.lx + 1
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A simulation context: one device, one stream, one 64-bit seed from which
+    every pre-shared seed (seed01, seed02, seed12, dealer) is keyed."""
+
+    def __init__(self, seed: int, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self._lib = _native.lib()
+        self.device = torch.device("cuda", device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        self._check(self._lib.bc_create(ctypes.byref(h), seed, device, self._stream_handle()))
+        self._h = h
+        self.seed = seed
+
+    # -- plumbing -------------------------------------------------------------
+    def _stream_handle(self):
+        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _sync_stream(self):
+        # calls follow torch's current stream unless a stream was pinned
+        self._lib.bc_set_stream(self._h, self._stream_handle())
+
+    def _check(self, rc: int):
+        if rc != 0:
+            msg = self._lib.bc_strerror(rc).decode()
+            extra = ""
+            if getattr(self, "_h", None) is not None:
+                extra = self._lib.bc_last_cuda_error(self._h).decode()
+            raise BicoptorError(f"bicoptor error {rc}: {msg} {extra}".strip())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.bc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, n: int, bits: int) -> torch.Tensor:
+        return torch.empty(n, dtype=lane_dtype(bits), device=self.device)
+
+    @staticmethod
+    def _need(t: torch.Tensor, bits: int, name: str):
+        if t.dtype != lane_dtype(bits) or not t.is_cuda or not t.is_contiguous():
+            raise BicoptorError(f"{name}: expected a contiguous CUDA {lane_dtype(bits)} tensor")
+
+    # -- sharing ----------------------------------------------------------------
+    def share(self, ring_bits: int, x_fixed: torch.Tensor, tensor_id: int):
+        if x_fixed.dtype != torch.int64 or not x_fixed.is_cuda:
+            raise BicoptorError("share: x must be a CUDA int64 tensor of fixed-point values")
+        x_fixed = x_fixed.contiguous()
+        n = x_fixed.numel()
+        s0, s1 = self._empty(n, ring_bits), self._empty(n, ring_bits)
+        self._sync_stream()
+        self._check(self._lib.bc_share(self._h, ring_bits, _ptr(x_fixed), n, tensor_id,
+                                       _ptr(s0), _ptr(s1)))
+        return s0, s1
+
+    def reconstruct(self, ring_bits: int, s0: torch.Tensor, s1: torch.Tensor) -> torch.Tensor:
+        self._need(s0, ring_bits, "s0")
+        self._need(s1, ring_bits, "s1")
+        out = self._empty(s0.numel(), ring_bits)
+        self._sync_stream()
+        self._check(self._lib.bc_reconstruct(self._h, ring_bits, _ptr(s0), _ptr(s1), s0.numel(),
+                                             _ptr(out)))
+        return out
+
+    # -- truncations, modulo switch, product ------------------------------------
+    def trunc_prob(self, ring_bits: int, k: int, s0, s1, out=None):
+        self._need(s0, ring_bits, "s0")
+        self._need(s1, ring_bits, "s1")
+        n = s0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, ring_bits), self._empty(n, ring_bits))
+        self._sync_stream()
+        self._check(self._lib.bc_trunc_prob(self._h, ring_bits, k, _ptr(s0), _ptr(s1), n,
+                                            _ptr(o0), _ptr(o1)))
+        return o0, o1
+
+    def trunc_det(self, ring_bits: int, k1: int, k2: int, s0, s1, out=None):
+        self._need(s0, ring_bits, "s0")
+        self._need(s1, ring_bits, "s1")
+        n, ob = s0.numel(), ring_bits - k1 - k2
+        o0, o1 = out if out is not None else (self._empty(n, ob), self._empty(n, ob))
+        self._sync_stream()
+        self._check(self._lib.bc_trunc_det(self._h, ring_bits, k1, k2, _ptr(s0), _ptr(s1), n,
+                                           _ptr(o0), _ptr(o1)))
+        return o0, o1
+
+    def mod_switch(self, lp: int, p: int, s0, s1):
+        self._need(s0, lp, "s0")
+        self._need(s1, lp, "s1")
+        n = s0.numel()
+        o0 = torch.empty(n, dtype=torch.int32, device=self.device)
+        o1 = torch.empty(n, dtype=torch.int32, device=self.device)
+        self._sync_stream()
+        self._check(self._lib.bc_mod_switch(self._h, lp, p, _ptr(s0), _ptr(s1), n, _ptr(o0),
+                                            _ptr(o1)))
+        return o0, o1
+
+    def mul_beaver(self, ring_bits: int, x0, x1, y0, y1, tensor_id: int, out=None):
+        for t, nm in ((x0, "x0"), (x1, "x1"), (y0, "y0"), (y1, "y1")):
+            self._need(t, ring_bits, nm)
+        n = x0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, ring_bits), self._empty(n, ring_bits))
+        self._sync_stream()
+        self._check(self._lib.bc_mul_beaver(self._h, ring_bits, _ptr(x0), _ptr(x1), _ptr(y0),
+                                            _ptr(y1), n, tensor_id, _ptr(o0), _ptr(o1)))
+        return o0, o1
+
+    # -- DReLU / ReLU -------------------------------------------------------------
+    def _protocol(self, fn, prm: Params, s0, s1, tensor_id, out, audit):
+        self._need(s0, prm.ring_bits, "s0")
+        self._need(s1, prm.ring_bits, "s1")
+        n = s0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, prm.ring_bits),
+                                              self._empty(n, prm.ring_bits))
+        bufs = None
+        self._sync_stream()
+        if audit:
+            L = prm.slots
+            dev = self.device
+            bufs = dict(w0=torch.empty(n * L, dtype=torch.int32, device=dev),
+                        w1=torch.empty(n * L, dtype=torch.int32, device=dev),
+                        reply=self._empty(n, prm.ring_bits), open0=self._empty(n, prm.ring_bits),
+                        open1=self._empty(n, prm.ring_bits), pre_c1=self._empty(n, prm.ring_bits),
+                        t=torch.empty(n, dtype=torch.uint8, device=dev),
+                        dprime=torch.empty(n, dtype=torch.uint8, device=dev))
+            a = Audit(*[_ptr(bufs[k]) for k in ("w0", "w1", "reply", "open0", "open1", "pre_c1",
+                                                 "t", "dprime")])
+            self._check(self._lib.bc_set_audit(self._h, ctypes.byref(a)))
+        try:
+            prm_c = prm.c_struct()
+            self._check(fn(self._h, ctypes.byref(prm_c), _ptr(s0), _ptr(s1), n, tensor_id,
+                           _ptr(o0), _ptr(o1)))
+        finally:
+            if audit:
+                self._lib.bc_set_audit(self._h, None)
+        return (o0, o1, bufs) if audit else (o0, o1)
+
+    def drelu(self, prm: Params, s0, s1, tensor_id: int, out=None, audit: bool = False):
+        return self._protocol(self._lib.bc_drelu, prm, s0, s1, tensor_id, out, audit)
+
+    def relu(self, prm: Params, s0, s1, tensor_id: int, out=None, audit: bool = False):
+        return self._protocol(self._lib.bc_relu, prm, s0, s1, tensor_id, out, audit)
+
+    # -- batched ------------------------------------------------------------------
+    def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0):
+        """items: (prm, s0, s1, o0, o1, tensor_id[, op]) per tensor."""
+        arr = (TensorDesc * max(1, len(items)))()
+        self._batch_keep = list(items)
+        for i, it in enumerate(items):
+            prm, s0, s1, o0, o1, tid = it[:6]
+            op = it[6] if len(it) > 6 else OP_RELU
+            for t, nm in ((s0, "s0"), (s1, "s1"), (o0, "o0"), (o1, "o1")):
+                self._need(t, prm.ring_bits, nm)
+            arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
+                                s0.numel(), tid, op, prm.c_struct())
+        cfg = BatchConfig(tile_elems, ctas_per_sm)
+        self._sync_stream()
+        self._check(self._lib.bc_relu_batch_plan(self._h, arr, len(items), ctypes.byref(cfg)))
+
+    def relu_batch_run(self):
+        self._sync_stream()
+        self._check(self._lib.bc_relu_batch_run(self._h))
+
+    def batch_status(self) -> int:
+        return int(self._lib.bc_batch_status(self._h))
+
+    # -- product -> truncations -> ReLU -------------------------------------------
+    def linear_relu(self, ring_bits: int, k: int, prm: Params, x0, x1, y0, y1, tensor_id: int,
+                    work=None):
+        """Beaver product, Alg. smltrc and Alg. newtrc by k bits, ReLU of the
+        probabilistically truncated product.  Returns dict of device tensors."""
+        n = x0.numel()
+        w = work or self.linear_relu_buffers(ring_bits, k, n)
+        a = LinearReluArgs(ring_bits, k, prm.c_struct(), x0.data_ptr(), x1.data_ptr(),
+                           y0.data_ptr(), y1.data_ptr(), n, tensor_id,
+                           *[w[nm].data_ptr() for nm in ("prod0", "prod1", "trc0", "trc1", "det0",
+                                                         "det1", "relu0", "relu1")])
+        self._sync_stream()
+        self._check(self._lib.bc_linear_relu(self._h, ctypes.byref(a)))
+        return w
+
+    def linear_relu_buffers(self, ring_bits: int, k: int, n: int) -> Dict[str, torch.Tensor]:
+        d = {nm: self._empty(n, ring_bits) for nm in ("prod0", "prod1", "trc0", "trc1", "relu0",
+                                                       "relu1")}
+        d["det0"] = self._empty(n, ring_bits - k)
+        d["det1"] = self._empty(n, ring_bits - k)
+        return d
+
+    def reserve(self, max_chunk: int):
+        self._check(self._lib.bc_reserve(self._h, max_chunk))
+
+    def linear_relu_host(self, ring_bits: int, k: int, prm: Params, x0, x1, y0, y1,
+                         tensor_id: int, out: Dict[str, torch.Tensor]):
+        """Host (CPU, ideally pinned) tensors in and out; copies happen inside."""
+        n = x0.numel()
+        a = LinearReluArgs(ring_bits, k, prm.c_struct(), x0.data_ptr(), x1.data_ptr(),
+                           y0.data_ptr(), y1.data_ptr(), n, tensor_id, None, None, None, None,
+                           out["det0"].data_ptr(), out["det1"].data_ptr(),
+                           out["relu0"].data_ptr(), out["relu1"].data_ptr())
+        self._sync_stream()
+        self._check(self._lib.bc_linear_relu_host(self._h, ctypes.byref(a)))
+        return out
+
+    # -- evaluation ---------------------------------------------------------------
+    def count_trunc_failures(self, out_bits: int, k: int, x: torch.Tensor, o0, o1) -> int:
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self._sync_stream()
+        self._check(self._lib.bc_count_trunc_failures(self._h, out_bits, k, _ptr(x), _ptr(o0),
+                                                      _ptr(o1), o0.numel(), _ptr(cnt)))
+        return int(cnt.item())
+
+    def comm(self) -> Dict[str, int]:
+        c = Comm()
+        self._check(self._lib.bc_get_comm(self._h, ctypes.byref(c)))
+        return c.as_dict()
+
+    def reset_comm(self):
+        self._check(self._lib.bc_reset_comm(self._h))
+
+    def synchronize(self):
+        self._check(self._lib.bc_synchronize(self._h))
+
+
+def to_unsigned_numpy(t: torch.Tensor):
+    """Copy a lane tensor to host as a uint32/uint64 numpy array."""
+    import numpy as np
+    a = t.detach().cpu().numpy()
+    return a.view(np.uint64 if a.dtype == np.int64 else np.uint32 if a.dtype == np.int32 else a.dtype)
+
+
+def from_unsigned_numpy(a, device) -> torch.Tensor:
+    import numpy as np
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a.copy()).to(device)

@@ -1,0 +1,116 @@
+"""Batched ReLU over many tensors: one persistent launch over a tile queue.
+
+A network's ReLU layers (and many inferences of uneven size) are planned once
+into a tile table (bc_relu_batch_plan) and run as a single persistent kernel
+(bc_relu_batch_run) whose CTAs pull tiles from an atomic counter.  The run is
+stream-capturable, so a ReluBatch can be replayed through a CUDA graph.
+The autotuner picks the tile size and CTAs per SM by timing the candidates on
+the actual tensors; its choice is cached per (tensor mix, GPU).
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import torch
+
+from . import Context, Params, OP_RELU
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+TILE_CANDIDATES = (1024, 2048, 4096, 8192, 16384)
+
+
+class ReluBatch:
+    """items: (Params, s0, s1, o0, o1, tensor_id[, op]) per tensor."""
+
+    def __init__(self, ctx: Context, items: Sequence[Tuple], tile_elems: int = 0,
+                 ctas_per_sm: int = 0):
+        self.ctx = ctx
+        self.items = list(items)
+        self.tile_elems = tile_elems
+        self.ctas_per_sm = ctas_per_sm
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+        self.plan()
+
+    @property
+    def elements(self) -> int:
+        return int(sum(it[1].numel() for it in self.items))
+
+    def plan(self):
+        self.ctx.relu_batch_plan(self.items, self.tile_elems, self.ctas_per_sm)
+        self.graph = None
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.ctx.relu_batch_run()
+
+    def capture(self):
+        """Capture one run in a CUDA graph; later run() calls replay it."""
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):          # warm the stream before capture
+            self.ctx.relu_batch_run()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.ctx.relu_batch_run()
+        torch.cuda.synchronize()
+        self.graph = g
+
+    def status(self) -> int:
+        return self.ctx.batch_status()
+
+
+def time_ms(fn, reps: int = 5, warmup: int = 2) -> float:
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def _mix_key(items) -> str:
+    rings = sorted({(it[0].ring_bits, it[0].lx) for it in items})
+    total = sum(it[1].numel() for it in items)
+    return f"{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}|t{len(items)}"
+
+
+def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
+             use_cache: bool = True) -> Dict[str, float]:
+    """Time every (tile, ctas_per_sm) candidate on `items`; returns the best
+    {"tile_elems", "ctas_per_sm", "ms"}.  Outputs of the tensors are written
+    (the protocol is deterministic, so reruns give identical results)."""
+    key = _mix_key(items)
+    cache = {}
+    if use_cache and os.path.exists(_CACHE):
+        try:
+            cache = json.load(open(_CACHE))
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return cache[key]
+    best = None
+    for tile in TILE_CANDIDATES:
+        for cps in (1, 2, 3, 4):
+            b = ReluBatch(ctx, items, tile, cps)
+            ms = time_ms(b.run, reps=reps, warmup=1)
+            if best is None or ms < best["ms"]:
+                best = {"tile_elems": tile, "ctas_per_sm": cps, "ms": ms}
+    cache[key] = best
+    try:
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        json.dump(cache, open(_CACHE, "w"), indent=1)
+    except OSError:
+        pass
+    return best

@@ -1,0 +1,595 @@
+// C-ABI of the library: context, argument checks, communication accounting,
+// the batched tile planner, and host-buffer staging.  Every entry point is
+// declared (with its citation) in include/bicoptor.h.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bc_internal.h"
+
+struct bc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;          // second stream of the host-staging pipeline
+  uint64_t seed = 0;
+  bc::RoundKeys rk{};
+  int num_sms = 1;
+  bc_comm comm{};
+  bc::AuditPtrs audit{};
+  char last_err[256] = {0};
+  // validated (lx, p) pairs
+  uint32_t ok_p[4] = {0, 0, 0, 0};
+  int ok_lx[4] = {0, 0, 0, 0};
+  int ok_next = 0;
+  // batched launch plan
+  bc::BatchTensor* d_tensors = nullptr;
+  bc::BatchTile* d_tiles = nullptr;
+  bc::BatchTensor* h_tensors = nullptr;   // pinned
+  bc::BatchTile* h_tiles = nullptr;       // pinned
+  size_t cap_tensors = 0, cap_tiles = 0;
+  unsigned int* d_counter = nullptr;
+  int* d_status = nullptr;
+  uint32_t ntiles = 0;
+  int batch_grid = 0;
+  bc_comm batch_comm{};                   // what one run of the plan adds
+  bool planned = false;
+  // host staging for bc_linear_relu_host: two sets of chunk buffers
+  size_t stage_cap = 0;
+  void* stage[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
+};
+
+namespace {
+
+int cuda_fail(bc_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) snprintf(ctx->last_err, sizeof(ctx->last_err), "%s: %s", where, cudaGetErrorString(e));
+  return BC_ECUDA;
+}
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+bool is_prime32(uint64_t q) {
+  if (q < 2) return false;
+  if (q % 2 == 0) return q == 2;
+  for (uint64_t d = 3; d * d <= q; d += 2)
+    if (q % d == 0) return false;
+  return true;
+}
+
+size_t lane_bytes(int bits) { return bits > 32 ? 8 : 4; }
+
+bc::RoundKeys make_round_keys(uint64_t seed) {
+  bc::RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += bc::kPhiloxW0;
+    k1 += bc::kPhiloxW1;
+  }
+  return rk;
+}
+
+bc::ModP make_modp(uint32_t p) {
+  bc::ModP m;
+  m.p = p;
+  uint32_t inv = p;                      // Newton: inv = p^{-1} mod 2^32
+  for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+  m.pinv = 0u - inv;
+  const uint64_t r1 = ((uint64_t)1 << 32) % p;
+  m.r2 = (uint32_t)((r1 * r1) % p);
+  m.pm1 = p - 1;
+  return m;
+}
+
+uint64_t ring_mask(int bits) { return bits >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1); }
+
+// Checks of Alg. drelu's parameters; fills the kernel constants.
+int make_consts(bc_ctx* ctx, const bc_drelu_params* prm, uint32_t tensor_id,
+                bc::ReluConsts* k) {
+  if (!prm) return BC_EINVAL;
+  const int ell = prm->ring_bits, lx = prm->lx, c = prm->key_off;
+  if (ell < 2 || ell > 64 || lx < 1 || lx > 31 || c < 0 || c + 2 * lx > ell) return BC_EINVAL;
+  uint32_t p = prm->p ? prm->p : bc_prime_above(lx);
+  const uint64_t lo = (uint64_t)1 << lx, hi = (uint64_t)1 << (lx + 1);
+  if ((uint64_t)p <= lo || (uint64_t)p >= hi) return BC_EINVAL;
+  bool known = false;
+  for (int i = 0; i < 4; ++i) known |= (ctx->ok_p[i] == p && ctx->ok_lx[i] == lx);
+  if (!known) {
+    if (!is_prime32(p)) return BC_EINVAL;
+    ctx->ok_p[ctx->ok_next] = p;
+    ctx->ok_lx[ctx->ok_next] = lx;
+    ctx->ok_next = (ctx->ok_next + 1) & 3;
+  }
+  k->rk = ctx->rk;
+  k->mp = make_modp(p);
+  k->ring_mask = ring_mask(ell);
+  k->ring_bits = (uint32_t)ell;
+  k->lx = (uint32_t)lx;
+  k->c = (uint32_t)c;
+  k->mx = (uint32_t)(lo - 1);
+  k->two_lx = (uint32_t)lo;
+  k->p_minus_2lx = p - (uint32_t)lo;
+  k->tensor_id = tensor_id;
+  k->elem_base = 0;
+  return BC_OK;
+}
+
+// Communication of one protocol call over n elements (bits).
+void add_comm(bc_comm* c, const bc_comm& d) {
+  c->p0_to_p2 += d.p0_to_p2;
+  c->p1_to_p2 += d.p1_to_p2;
+  c->p2_to_p0 += d.p2_to_p0;
+  c->p2_to_p1 += d.p2_to_p1;
+  c->p0_to_p1 += d.p0_to_p1;
+  c->p1_to_p0 += d.p1_to_p0;
+  c->pre_p2_to_p1 += d.pre_p2_to_p1;
+  c->rounds += d.rounds;
+  c->elements += d.elements;
+  c->calls += d.calls;
+}
+
+bc_comm relu_comm(int ell, int lx, uint64_t n, bool relu) {
+  bc_comm d{};
+  const uint64_t L = (uint64_t)lx + 1, zp_bits = (uint64_t)lx + 1;   // ceil(log2 p) = lx + 1
+  d.p0_to_p2 = n * L * zp_bits;    // Alg. drelu step 8
+  d.p1_to_p2 = n * L * zp_bits;
+  if (relu) {
+    d.p2_to_p0 = n * (uint64_t)ell;      // e = DReLU' - b
+    d.p2_to_p1 = n * (uint64_t)ell;
+    d.p0_to_p1 = n * (uint64_t)ell;      // share of d = x - a
+    d.p1_to_p0 = n * (uint64_t)ell;
+    d.pre_p2_to_p1 = n * (uint64_t)ell;  // [c]_1
+  } else {
+    d.p2_to_p1 = n * (uint64_t)ell;      // [DReLU']_1 (P0's share comes from seed02)
+  }
+  d.rounds = n ? 2 : 0;
+  d.elements = n;
+  d.calls = 1;
+  return d;
+}
+
+bc_comm mul_comm(int ell, uint64_t n) {
+  bc_comm d{};
+  d.p0_to_p1 = 2 * n * (uint64_t)ell;   // shares of d = x - a and e = y - b
+  d.p1_to_p0 = 2 * n * (uint64_t)ell;
+  d.pre_p2_to_p1 = n * (uint64_t)ell;   // [c]_1
+  d.rounds = n ? 1 : 0;
+  d.elements = n;
+  d.calls = 1;
+  return d;
+}
+
+int run_relu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
+             uint32_t tensor_id, void* o0, void* o1, bool relu, uint64_t elem_base,
+             cudaStream_t s, bool count) {
+  if (!ctx) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  bc::ReluConsts k;
+  int rc = make_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  k.elem_base = elem_base;
+  if (n) CK(bc::launch_relu(k, relu, sh0, sh1, n, o0, o1, ctx->audit, ctx->num_sms, s));
+  if (count) add_comm(&ctx->comm, relu_comm(prm->ring_bits, prm->lx, n, relu));
+  return BC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bc_strerror(int code) {
+  switch (code) {
+    case BC_OK: return "ok";
+    case BC_EINVAL: return "invalid argument";
+    case BC_ENOMEM: return "out of device memory";
+    case BC_ECUDA: return "CUDA error";
+    case BC_ETIMEOUT: return "bounded device wait timed out";
+    case BC_ECHECK: return "device consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+const char* bc_last_cuda_error(bc_ctx* ctx) { return ctx ? ctx->last_err : ""; }
+
+uint32_t bc_prime_above(int lx) {
+  if (lx < 1 || lx > 31) return 0;
+  uint64_t q = ((uint64_t)1 << lx) + 1;
+  while (!is_prime32(q)) ++q;
+  return (uint32_t)q;
+}
+
+int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
+  if (!out) return BC_EINVAL;
+  *out = nullptr;
+  bc_ctx* ctx = new bc_ctx();
+  ctx->device = device;
+  ctx->seed = seed;
+  ctx->rk = make_round_keys(seed);
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    int rc = (e == cudaErrorMemoryAllocation) ? BC_ENOMEM : BC_ECUDA;
+    bc_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return BC_OK;
+}
+
+int bc_destroy(bc_ctx* ctx) {
+  if (!ctx) return BC_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  cudaFree(ctx->d_tensors);
+  cudaFree(ctx->d_tiles);
+  cudaFreeHost(ctx->h_tensors);
+  cudaFreeHost(ctx->h_tiles);
+  cudaFree(ctx->d_counter);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->stage[0]);
+  cudaFree(ctx->stage[1]);
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  delete ctx;
+  return BC_OK;
+}
+
+int bc_set_stream(bc_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return BC_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return BC_OK;
+}
+
+int bc_synchronize(bc_ctx* ctx) {
+  if (!ctx) return BC_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BC_OK;
+}
+
+int bc_share(bc_ctx* ctx, int ring_bits, const int64_t* x, size_t n, uint32_t tensor_id,
+             void* sh0, void* sh1) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
+  if (n && (!x || !sh0 || !sh1)) return BC_EINVAL;
+  CK(bc::launch_share(ring_bits, ctx->rk, x, n, tensor_id, 0, sh0, sh1, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+int bc_reconstruct(bc_ctx* ctx, int ring_bits, const void* sh0, const void* sh1, size_t n,
+                   void* x_out) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !x_out)) return BC_EINVAL;
+  CK(bc::launch_reconstruct(ring_bits, sh0, sh1, n, x_out, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+int bc_trunc_prob(bc_ctx* ctx, int ring_bits, int k, const void* sh0, const void* sh1, size_t n,
+                  void* o0, void* o1) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64 || k < 0 || k >= ring_bits) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_trunc_prob(ring_bits, k, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+int bc_trunc_det(bc_ctx* ctx, int ring_bits, int k1, int k2, const void* sh0, const void* sh1,
+                 size_t n, void* o0, void* o1) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64 || k1 < 0 || k2 < 0 || k1 + k2 >= ring_bits)
+    return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  // outputs of a narrower lane than the inputs must not alias them
+  if (lane_bytes(ring_bits) != lane_bytes(ring_bits - k1 - k2) && (o0 == sh0 || o1 == sh1))
+    return BC_EINVAL;
+  CK(bc::launch_trunc_det(ring_bits, k1, k2, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+int bc_mod_switch(bc_ctx* ctx, int lp, uint32_t p, const void* sh0, const void* sh1, size_t n,
+                  uint32_t* o0, uint32_t* o1) {
+  if (!ctx || lp < 1 || lp > 31) return BC_EINVAL;
+  if ((uint64_t)p <= ((uint64_t)1 << lp) || !is_prime32(p)) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_mod_switch(lp, p, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+int bc_mul_beaver(bc_ctx* ctx, int ring_bits, const void* x0, const void* x1, const void* y0,
+                  const void* y1, size_t n, uint32_t tensor_id, void* o0, void* o1) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
+  if (n && (!x0 || !x1 || !y0 || !y1 || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_mul_beaver(ring_bits, ctx->rk, x0, x1, y0, y1, n, tensor_id, 0, o0, o1,
+                           ctx->num_sms, ctx->stream));
+  add_comm(&ctx->comm, mul_comm(ring_bits, n));
+  return BC_OK;
+}
+
+int bc_drelu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
+             uint32_t tensor_id, void* o0, void* o1) {
+  return run_relu(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, false, 0, ctx ? ctx->stream : nullptr,
+                  true);
+}
+
+int bc_relu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
+            uint32_t tensor_id, void* o0, void* o1) {
+  return run_relu(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, true, 0, ctx ? ctx->stream : nullptr,
+                  true);
+}
+
+int bc_set_audit(bc_ctx* ctx, const bc_audit* b) {
+  if (!ctx) return BC_EINVAL;
+  ctx->audit = bc::AuditPtrs{};
+  if (b) {
+    ctx->audit.w0 = b->w0;
+    ctx->audit.w1 = b->w1;
+    ctx->audit.reply = b->reply;
+    ctx->audit.open0 = b->open0;
+    ctx->audit.open1 = b->open1;
+    ctx->audit.pre_c1 = b->pre_c1;
+    ctx->audit.t = b->t;
+    ctx->audit.dprime = b->dprime;
+  }
+  return BC_OK;
+}
+
+int bc_get_comm(bc_ctx* ctx, bc_comm* out) {
+  if (!ctx || !out) return BC_EINVAL;
+  *out = ctx->comm;
+  return BC_OK;
+}
+
+int bc_reset_comm(bc_ctx* ctx) {
+  if (!ctx) return BC_EINVAL;
+  ctx->comm = bc_comm{};
+  return BC_OK;
+}
+
+// ---- batched launch -------------------------------------------------------
+
+int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
+                       const bc_batch_config* cfg) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return BC_EINVAL;
+  const int tile = (cfg && cfg->tile_elems > 0) ? cfg->tile_elems : 4096;
+  if (tile > (1 << 30)) return BC_EINVAL;
+  int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : bc::relu_batch_max_ctas_per_sm();
+  per_sm = std::min(per_sm, bc::relu_batch_max_ctas_per_sm());
+  // the pinned staging may still feed an earlier plan's copies
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<bc::BatchTensor> tens((size_t)count);
+  size_t ntiles = 0;
+  bc_comm add{};
+  for (int t = 0; t < count; ++t) {
+    const bc_tensor_desc& d = descs[t];
+    if (d.op != BC_OP_RELU && d.op != BC_OP_DRELU) return BC_EINVAL;
+    if (d.n && (!d.sh0 || !d.sh1 || !d.o0 || !d.o1)) return BC_EINVAL;
+    bc::ReluConsts k;
+    int rc = make_consts(ctx, &d.params, d.tensor_id, &k);
+    if (rc) return rc;
+    tens[t].sh0 = d.sh0;
+    tens[t].sh1 = d.sh1;
+    tens[t].o0 = d.o0;
+    tens[t].o1 = d.o1;
+    tens[t].n = d.n;
+    tens[t].k = k;
+    tens[t].op = d.op;
+    tens[t].lane64 = d.params.ring_bits > 32;
+    ntiles += (d.n + tile - 1) / tile;
+    add_comm(&add, relu_comm(d.params.ring_bits, d.params.lx, d.n, d.op == BC_OP_RELU));
+  }
+  if (ntiles > 0xFFFFFFF0u) return BC_EINVAL;
+  add.rounds = count ? 2 : 0;   // all tensors share the two rounds of one batched call
+  add.calls = count ? 1 : 0;
+  if ((size_t)count > ctx->cap_tensors) {
+    cudaFree(ctx->d_tensors);
+    cudaFreeHost(ctx->h_tensors);
+    ctx->d_tensors = nullptr;
+    ctx->h_tensors = nullptr;
+    ctx->cap_tensors = 0;
+    size_t cap = std::max<size_t>(count, 64);
+    if (cudaMalloc(&ctx->d_tensors, cap * sizeof(bc::BatchTensor)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_tensors, cap * sizeof(bc::BatchTensor)) != cudaSuccess)
+      return BC_ENOMEM;
+    ctx->cap_tensors = cap;
+  }
+  if (ntiles > ctx->cap_tiles) {
+    cudaFree(ctx->d_tiles);
+    cudaFreeHost(ctx->h_tiles);
+    ctx->d_tiles = nullptr;
+    ctx->h_tiles = nullptr;
+    ctx->cap_tiles = 0;
+    size_t cap = std::max<size_t>(ntiles, 1024);
+    if (cudaMalloc(&ctx->d_tiles, cap * sizeof(bc::BatchTile)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_tiles, cap * sizeof(bc::BatchTile)) != cudaSuccess)
+      return BC_ENOMEM;
+    ctx->cap_tiles = cap;
+  }
+  if (count) memcpy(ctx->h_tensors, tens.data(), sizeof(bc::BatchTensor) * count);
+  // Tiles are laid out largest-tensor-first so the long tensors start early
+  // and the short ones fill the tail of the persistent grid.
+  std::vector<int> order(count);
+  for (int t = 0; t < count; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return descs[a].n > descs[b].n; });
+  size_t w = 0;
+  for (int oi = 0; oi < count; ++oi) {
+    const int t = order[oi];
+    for (uint64_t s = 0; s < descs[t].n; s += tile) {
+      bc::BatchTile bt;
+      bt.tensor = (uint32_t)t;
+      bt.start = s;
+      bt.count = (uint32_t)std::min<uint64_t>(tile, descs[t].n - s);
+      ctx->h_tiles[w++] = bt;
+    }
+  }
+  if (count)
+    CK(cudaMemcpyAsync(ctx->d_tensors, ctx->h_tensors, sizeof(bc::BatchTensor) * count,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  if (w)
+    CK(cudaMemcpyAsync(ctx->d_tiles, ctx->h_tiles, sizeof(bc::BatchTile) * w,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  ctx->ntiles = (uint32_t)w;
+  ctx->batch_grid = (int)std::min<size_t>((size_t)ctx->num_sms * per_sm, std::max<size_t>(w, 1));
+  ctx->batch_comm = add;
+  ctx->planned = true;
+  return BC_OK;
+}
+
+int bc_relu_batch_run(bc_ctx* ctx) {
+  if (!ctx || !ctx->planned) return BC_EINVAL;
+  CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), ctx->stream));
+  CK(bc::launch_relu_batch(ctx->rk, ctx->d_tensors, ctx->d_tiles, ctx->ntiles, ctx->d_counter,
+                           ctx->d_status, ctx->batch_grid, ctx->stream));
+  add_comm(&ctx->comm, ctx->batch_comm);
+  return BC_OK;
+}
+
+int bc_relu_batch(bc_ctx* ctx, const bc_tensor_desc* descs, int count, const bc_batch_config* cfg) {
+  int rc = bc_relu_batch_plan(ctx, descs, count, cfg);
+  if (rc) return rc;
+  return bc_relu_batch_run(ctx);
+}
+
+int bc_batch_status(bc_ctx* ctx) {
+  if (!ctx) return BC_EINVAL;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return st;
+}
+
+// ---- product -> truncations -> ReLU ---------------------------------------
+
+namespace {
+
+int check_linear(const bc_linear_relu_args* a) {
+  if (!a) return BC_EINVAL;
+  if (a->ring_bits < 2 || a->ring_bits > 64 || a->relu.ring_bits != a->ring_bits) return BC_EINVAL;
+  if (a->trunc_bits < 0 || a->trunc_bits >= a->ring_bits) return BC_EINVAL;
+  return BC_OK;
+}
+
+int linear_relu_device(bc_ctx* ctx, const bc_linear_relu_args* a, const void* x0, const void* x1,
+                       const void* y0, const void* y1, void* prod0, void* prod1, void* trc0,
+                       void* trc1, void* det0, void* det1, void* relu0, void* relu1, size_t n,
+                       uint64_t base, cudaStream_t s) {
+  const int ell = a->ring_bits, k = a->trunc_bits;
+  CK(bc::launch_mul_beaver(ell, ctx->rk, x0, x1, y0, y1, n, a->tensor_id, base, prod0, prod1,
+                           ctx->num_sms, s));
+  CK(bc::launch_trunc_prob(ell, k, prod0, prod1, n, trc0, trc1, ctx->num_sms, s));
+  if (det0 && det1)
+    CK(bc::launch_trunc_det(ell, k, 0, prod0, prod1, n, det0, det1, ctx->num_sms, s));
+  return run_relu(ctx, &a->relu, trc0, trc1, n, a->tensor_id + 1, relu0, relu1, true, base, s,
+                  false);
+}
+
+}  // namespace
+
+int bc_linear_relu(bc_ctx* ctx, const bc_linear_relu_args* a) {
+  if (!ctx) return BC_EINVAL;
+  int rc = check_linear(a);
+  if (rc) return rc;
+  if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->prod0 || !a->prod1 || !a->trc0 ||
+               !a->trc1 || !a->relu0 || !a->relu1))
+    return BC_EINVAL;
+  rc = linear_relu_device(ctx, a, a->x0, a->x1, a->y0, a->y1, a->prod0, a->prod1, a->trc0,
+                          a->trc1, a->det0, a->det1, a->relu0, a->relu1, a->n, 0, ctx->stream);
+  if (rc) return rc;
+  add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
+  add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));
+  return BC_OK;
+}
+
+int bc_reserve(bc_ctx* ctx, size_t max_chunk) {
+  if (!ctx || max_chunk == 0) return BC_EINVAL;
+  if (max_chunk <= ctx->stage_cap) return BC_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaStreamSynchronize(ctx->aux));
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(ctx->stage[i]);
+    ctx->stage[i] = nullptr;
+  }
+  ctx->stage_cap = 0;
+  const size_t per = ((max_chunk * 8 + 255) / 256) * 256;   // one 64-bit array, 256 B aligned
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&ctx->stage[i], per * 12) != cudaSuccess) {
+      cudaGetLastError();
+      return BC_ENOMEM;
+    }
+  }
+  ctx->stage_cap = max_chunk;
+  return BC_OK;
+}
+
+int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
+  if (!ctx) return BC_EINVAL;
+  int rc = check_linear(a);
+  if (rc) return rc;
+  if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->relu0 || !a->relu1)) return BC_EINVAL;
+  if (a->n && ctx->stage_cap == 0) return BC_EINVAL;
+  const size_t lb = lane_bytes(a->ring_bits);
+  const size_t db = lane_bytes(a->ring_bits - a->trunc_bits);
+  const size_t per = ((ctx->stage_cap * 8 + 255) / 256) * 256;
+  const size_t chunk = ctx->stage_cap;
+  cudaStream_t st[2] = {ctx->stream, ctx->aux};
+  // the aux stream starts after everything queued on the context stream
+  CK(cudaEventRecord(ctx->ev_start, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
+  const char* hx0 = static_cast<const char*>(a->x0);
+  const char* hx1 = static_cast<const char*>(a->x1);
+  const char* hy0 = static_cast<const char*>(a->y0);
+  const char* hy1 = static_cast<const char*>(a->y1);
+  char* hr0 = static_cast<char*>(a->relu0);
+  char* hr1 = static_cast<char*>(a->relu1);
+  char* hd0 = static_cast<char*>(a->det0);
+  char* hd1 = static_cast<char*>(a->det1);
+  size_t j = 0;
+  for (size_t off = 0; off < a->n; off += chunk, ++j) {
+    const size_t m = std::min(chunk, a->n - off);
+    cudaStream_t s = st[j & 1];
+    char* base = static_cast<char*>(ctx->stage[j & 1]);
+    void* b[12];
+    for (int q = 0; q < 12; ++q) b[q] = base + per * q;
+    CK(cudaMemcpyAsync(b[0], hx0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b[1], hx1 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b[2], hy0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b[3], hy1 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
+    const bool det = hd0 && hd1;
+    rc = linear_relu_device(ctx, a, b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7],
+                            det ? b[8] : nullptr, det ? b[9] : nullptr, b[10], b[11], m, off, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(hr0 + off * lb, b[10], m * lb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hr1 + off * lb, b[11], m * lb, cudaMemcpyDeviceToHost, s));
+    if (det) {
+      CK(cudaMemcpyAsync(hd0 + off * db, b[8], m * db, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hd1 + off * db, b[9], m * db, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->aux));
+  CK(cudaStreamSynchronize(ctx->stream));
+  add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
+  add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));
+  return BC_OK;
+}
+
+int bc_count_trunc_failures(bc_ctx* ctx, int out_bits, int k, const int64_t* x, const void* o0,
+                            const void* o1, size_t n, unsigned long long* count) {
+  if (!ctx || out_bits < 1 || out_bits > 64 || k < 0 || k > 63 || !count) return BC_EINVAL;
+  if (n && (!x || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_count_failures(out_bits, k, x, o0, o1, n, count, ctx->num_sms, ctx->stream));
+  return BC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device building blocks of the Bicoptor 2.0 hot path (sm_103a).
+//
+// Integer-only: ring arithmetic in Z_{2^l} on uint32/uint64 lanes, Z_p
+// arithmetic for the masked messages (p < 2^32) by Montgomery multiplication
+// (P. L. Montgomery, "Modular multiplication without trial division", Math.
+// Comp. 1985), and the counter-based Philox-4x32-10 generator (Salmon et al.,
+// "Parallel random numbers: as easy as 1, 2, 3", SC 2011) that expands the
+// pre-shared seeds of Sec. 2.1 inside registers.
+#pragma once
+#include <stdint.h>
+
+namespace bc {
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10.  The ten round keys are precomputed on the host and passed
+// in kernel parameters, so each round is two 32x32->64 multiplies and two
+// three-input XORs, with the key read straight from the constant bank.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct RoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+struct U32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return U32x4{c0, c1, c2, c3};
+}
+
+// Stream tags: which pre-shared seed a draw belongs to, and what it is for.
+// counter = (lo32(elem), tensor_id, block, pair << 24 | purpose << 16 | elem >> 32)
+enum : uint32_t { kPair01 = 0x01, kPair02 = 0x02, kPair12 = 0x12, kPairDealer = 0xDE };
+enum : uint32_t {
+  kPurShare = 1,        // dealer: R of the 2-of-2 sharing
+  kPurPerm = 2,         // seed01: flip bit t and the shuffle words
+  kPurMask = 3,         // seed01: (r_k, z_k) of message slot k, block k
+  kPurReply = 4,        // seed02: P0's share of DReLU'
+  kPurReluTriple = 5,   // seed02: a0,b0,c0 / seed12: a1,b1 of the ReLU product
+  kPurMulTriple = 6,    // seed02: a0,b0,c0 / seed12: a1,b1 of a Beaver product
+};
+
+__device__ __forceinline__ uint32_t stream_tag(uint32_t pair, uint32_t purpose, uint64_t elem) {
+  return (pair << 24) | (purpose << 16) | (uint32_t)((elem >> 32) & 0xffffu);
+}
+
+__device__ __forceinline__ U32x4 draw_block(uint32_t pair, uint32_t purpose, uint32_t tensor_id,
+                                            uint64_t elem, uint32_t block, const RoundKeys& rk) {
+  return philox((uint32_t)elem, tensor_id, block, stream_tag(pair, purpose, elem), rk);
+}
+
+// ---------------------------------------------------------------------------
+// Ring Z_{2^l} on lanes.  Lane = uint32_t for l <= 32, uint64_t for l <= 64.
+// ---------------------------------------------------------------------------
+template <typename Lane>
+__device__ __forceinline__ Lane ring_neg(Lane a, Lane mask) {
+  return (Lane)(Lane(0) - a) & mask;
+}
+
+// The j-th ring element of a block (0 <= j < 4 for 32-bit lanes, 0 <= j < 2
+// for 64-bit lanes; 64-bit elements take two words, low word first).
+template <typename Lane>
+__device__ __forceinline__ Lane block_elem(const U32x4& b, int j);
+template <>
+__device__ __forceinline__ uint32_t block_elem<uint32_t>(const U32x4& b, int j) {
+  return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+}
+template <>
+__device__ __forceinline__ uint64_t block_elem<uint64_t>(const U32x4& b, int j) {
+  return j == 0 ? ((uint64_t)b.y << 32 | b.x) : ((uint64_t)b.w << 32 | b.z);
+}
+
+// low 32 bits of (a >> sh) for 0 <= sh < 64
+__device__ __forceinline__ uint32_t lo32_shr(uint64_t a, uint32_t sh) { return (uint32_t)(a >> sh); }
+__device__ __forceinline__ uint32_t lo32_shr(uint32_t a, uint32_t sh) { return a >> sh; }
+
+// ---------------------------------------------------------------------------
+// Z_p, odd p < 2^32 with p in (2^lx, 2^(lx+1)).
+// ---------------------------------------------------------------------------
+struct ModP {
+  uint32_t p;      // the prime
+  uint32_t pinv;   // -p^{-1} mod 2^32
+  uint32_t r2;     // 2^64 mod p
+  uint32_t pm1;    // p - 1
+};
+
+// Montgomery product a * b * 2^-32 mod p for a, b < p.  t + m p is a
+// multiple of 2^32 and below 2^64 for p < 2^32 with a, b < p; the quotient
+// is below 2p, so one conditional subtraction lands in [0, p).
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const ModP& m) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t q = (uint32_t)t * m.pinv;
+  const uint64_t u = t + (uint64_t)q * m.p;
+  const uint32_t r = (uint32_t)(u >> 32);
+  return r >= m.p ? r - m.p : r;
+}
+
+// a + b mod p and a - b mod p for a, b < p (p < 2^32 so the sum may wrap
+// 32 bits only when p > 2^31; handled through 64-bit compare).
+__device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t p) {
+  const uint64_t s = (uint64_t)a + b;
+  return (uint32_t)(s >= p ? s - p : s);
+}
+__device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p) {
+  return a >= b ? a - b : a + (p - b);
+}
+
+// floor(w * q / 2^64) for a 64-bit w given as (hi, lo) and a 32-bit q.
+__device__ __forceinline__ uint32_t mulhi_64x32(uint32_t lo, uint32_t hi, uint32_t q) {
+  const uint64_t a = (uint64_t)lo * q;
+  const uint64_t b = (uint64_t)hi * q + (a >> 32);
+  return (uint32_t)(b >> 32);
+}
+
+}  // namespace bc

@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bicoptor.h"
+#include "bc_device.cuh"
+
+namespace bc {
+
+constexpr int kBlock = 256;     // threads per CTA of every kernel
+constexpr int kMaxSlots = 32;   // lx + 1 <= 32
+
+// Per-call constants of Alg. drelu / Alg. relu, passed by value.
+struct ReluConsts {
+  RoundKeys rk;
+  ModP mp;
+  uint64_t ring_mask;   // 2^l - 1 (as the lane type)
+  uint32_t ring_bits;
+  uint32_t lx;          // key bits
+  uint32_t c;           // key offset
+  uint32_t mx;          // 2^lx - 1
+  uint32_t two_lx;      // 2^lx (= 2^lx mod p, since p > 2^lx)
+  uint32_t p_minus_2lx; // p - 2^lx
+  uint32_t tensor_id;
+  uint64_t elem_base;   // element index of the launch's first element
+};
+
+struct AuditPtrs {
+  uint32_t* w0;
+  uint32_t* w1;
+  void* reply;
+  void* open0;
+  void* open1;
+  void* pre_c1;
+  uint8_t* t;
+  uint8_t* dprime;
+  bool any() const { return w0 || w1 || reply || open0 || open1 || pre_c1 || t || dprime; }
+};
+
+// One tensor of a batched launch, resident in device memory.
+struct BatchTensor {
+  const void* sh0;
+  const void* sh1;
+  void* o0;
+  void* o1;
+  uint64_t n;
+  ReluConsts k;        // rk is unused here (taken from the kernel parameter)
+  int op;              // BC_OP_RELU / BC_OP_DRELU
+  int lane64;          // ring_bits > 32
+};
+
+struct BatchTile {
+  uint32_t tensor;     // index into the tensor table
+  uint32_t count;      // elements in this tile
+  uint64_t start;      // first element of the tile within its tensor
+};
+
+// Host-side launchers (return cudaError_t of the launch).
+cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
+                        uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
+                        cudaStream_t s);
+cudaError_t launch_relu_batch(const RoundKeys& rk, const BatchTensor* tensors,
+                              const BatchTile* tiles, uint32_t ntiles, unsigned int* counter,
+                              int* status, int grid, cudaStream_t s);
+int relu_batch_max_ctas_per_sm();
+
+cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
+                         uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,
+                         cudaStream_t s);
+cudaError_t launch_reconstruct(int ring_bits, const void* sh0, const void* sh1, uint64_t n,
+                               void* out, int num_sms, cudaStream_t s);
+cudaError_t launch_trunc_prob(int ring_bits, int k, const void* sh0, const void* sh1, uint64_t n,
+                              void* o0, void* o1, int num_sms, cudaStream_t s);
+cudaError_t launch_trunc_det(int ring_bits, int k1, int k2, const void* sh0, const void* sh1,
+                             uint64_t n, void* o0, void* o1, int num_sms, cudaStream_t s);
+cudaError_t launch_mod_switch(int lp, uint32_t p, const void* sh0, const void* sh1, uint64_t n,
+                              uint32_t* o0, uint32_t* o1, int num_sms, cudaStream_t s);
+cudaError_t launch_mul_beaver(int ring_bits, const RoundKeys& rk, const void* x0, const void* x1,
+                              const void* y0, const void* y1, uint64_t n, uint32_t tensor_id,
+                              uint64_t elem_base, void* o0, void* o1, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_count_failures(int out_bits, int k, const int64_t* x, const void* o0,
+                                  const void* o1, uint64_t n, unsigned long long* count,
+                                  int num_sms, cudaStream_t s);
+
+}  // namespace bc

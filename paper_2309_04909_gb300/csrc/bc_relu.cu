@@ -1,0 +1,346 @@
+// Fused Bicoptor 2.0 DReLU / ReLU kernels (Alg. drelu, Alg. relu).
+//
+// One thread owns one element at a time and runs, in registers, the local
+// work of all three parties:
+//   P0, P1  steps 1-2   flip both shares by (-1)^t, t from seed01
+//           step 3      windowed deterministic truncation (Alg. newtrc2) at
+//                       every key-bit position i = 0..lx
+//           step 4      pair sums v_i = u_i + u_(i+1) - 1
+//           step 5      Alg. modswitch into Z_p
+//           step 6      seed01 shuffle (Fisher-Yates, staged in shared memory)
+//           step 7-8    mask by r_k in Z_p^*, reshare by z_k
+//   P2      step 9      reconstruct each w_k and test it for zero
+//           step 10     reply: [DReLU']_1 to P1 (DReLU) or e = DReLU' - b (ReLU)
+//   P0, P1  step 11     unflip (DReLU) / Beaver finish (ReLU)
+// The lx+1 windows are never stored: message slot k recomputes the window of
+// the index i = perm[k] from the two shares, so the l-fold expansion of the
+// paper's step 3 costs two funnel shifts per slot and no memory traffic.
+// Draws shared by P0 and P1 (everything from seed01) are generated once per
+// element and used by both simulated parties.
+#include "bc_internal.h"
+
+namespace bc {
+namespace {
+
+template <int LX, bool WIDE>
+struct SlotMath;
+
+// p fits in 31 bits (lx <= 30): sums of two residues stay below 2^32.
+template <int LX>
+struct SlotMath<LX, false> {
+  static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t s = a + b;
+    const uint32_t d = s - p;
+    return d < s ? d : s;   // s >= p  <=>  s - p does not wrap
+  }
+  static __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t d = a - b;
+    return a >= b ? d : d + p;
+  }
+};
+template <int LX>
+struct SlotMath<LX, true> {
+  static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b, uint32_t p) {
+    return add_mod(a, b, p);
+  }
+  static __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b, uint32_t p) {
+    return sub_mod(a, b, p);
+  }
+};
+
+template <typename Lane>
+__device__ __forceinline__ void store_lane(void* base, uint64_t i, Lane v) {
+  reinterpret_cast<Lane*>(base)[i] = v;
+}
+
+// The Beaver triple of the ReLU product for one element (Alg. relu
+// preprocessing): a0,b0,c0 from seed02, a1,b1 from seed12.
+template <typename Lane>
+struct Triple {
+  Lane a0, b0, c0, a1, b1;
+};
+
+template <typename Lane>
+__device__ __forceinline__ Triple<Lane> draw_triple(uint32_t purpose, uint32_t tensor_id,
+                                                    uint64_t elem, Lane mask,
+                                                    const RoundKeys& rk) {
+  Triple<Lane> T;
+  const U32x4 q0 = draw_block(kPair02, purpose, tensor_id, elem, 0, rk);
+  const U32x4 q1 = draw_block(kPair12, purpose, tensor_id, elem, 0, rk);
+  if (sizeof(Lane) == 4) {
+    T.a0 = (Lane)q0.x;
+    T.b0 = (Lane)q0.y;
+    T.c0 = (Lane)q0.z;
+  } else {
+    const U32x4 q2 = draw_block(kPair02, purpose, tensor_id, elem, 1, rk);
+    T.a0 = block_elem<Lane>(q0, 0);
+    T.b0 = block_elem<Lane>(q0, 1);
+    T.c0 = block_elem<Lane>(q2, 0);
+  }
+  T.a1 = block_elem<Lane>(q1, 0);
+  T.b1 = block_elem<Lane>(q1, 1);
+  T.a0 &= mask; T.b0 &= mask; T.c0 &= mask; T.a1 &= mask; T.b1 &= mask;
+  return T;
+}
+
+// Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
+// column of the shared-memory shuffle table (stride kBlock words).
+template <typename Lane, int LX, bool RELU, bool AUDIT>
+__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, Lane s1,
+                                                 uint64_t elem, uint32_t* perm, Lane& out0,
+                                                 Lane& out1, const AuditPtrs& aud,
+                                                 uint64_t out_idx) {
+  constexpr bool kWide = (LX == 0) || (LX > 30);
+  using M = SlotMath<LX, kWide>;
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  const uint32_t L = lx + 1;
+  const Lane mask = (Lane)k.ring_mask;
+  const uint32_t p = k.mp.p;
+
+  // ---- seed01 stream: t (step 1) and the shuffle words (step 6) ----------
+#pragma unroll
+  for (uint32_t s = 0; s < (LX ? (uint32_t)(LX + 1) : (uint32_t)kMaxSlots); ++s) {
+    if (LX || s < L) perm[s * kBlock] = s;
+  }
+  uint32_t t = 0;
+  const uint32_t nblk = (L + 3) >> 2;
+#pragma unroll
+  for (uint32_t b = 0; b < (LX ? (uint32_t)((LX + 4) >> 2) : 8u); ++b) {
+    if (!LX && b >= nblk) break;
+    const U32x4 wb = draw_block(kPair01, kPurPerm, k.tensor_id, elem, b, k.rk);
+    const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t widx = 4 * b + q;
+      if (widx == 0) {
+        t = ws[0] & 1u;
+      } else if (widx < L) {
+        // Fisher-Yates step j = lx + 1 - widx: partner = floor(W (j+1) / 2^32)
+        const uint32_t j = L - widx;
+        const uint32_t partner = __umulhi(ws[q], j + 1);
+        const uint32_t a = perm[j * kBlock];
+        const uint32_t c = perm[partner * kBlock];
+        perm[j * kBlock] = c;
+        perm[partner * kBlock] = a;
+      }
+    }
+  }
+
+  // ---- steps 1-2: flip by (-1)^t --------------------------------------------
+  const Lane f0 = t ? ring_neg(s0, mask) : s0;
+  const Lane nf1 = t ? s1 : ring_neg(s1, mask);   // 2^l - [x]_1 of the flipped share
+
+  // ---- steps 3-9 over message slots k ----------------------------------------
+  uint32_t any_zero = 0;
+#pragma unroll 1
+  for (uint32_t slot = 0; slot < L; ++slot) {
+    const uint32_t i = perm[slot * kBlock];
+    const uint32_t sh = k.c + i;
+    const uint32_t y0 = lo32_shr(f0, sh);
+    const uint32_t y1 = lo32_shr(nf1, sh);
+    const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
+    // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
+    const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
+    const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
+    // step 5: Alg. modswitch
+    const uint32_t m0 = v0 ? v0 : k.two_lx;
+    const uint32_t m1 = v1 + k.p_minus_2lx;
+    // step 7: r_k in Z_p^*, z_k in Z_p from the slot's seed01 block
+    const U32x4 rz = draw_block(kPair01, kPurMask, k.tensor_id, elem, slot, k.rk);
+    const uint32_t r = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+    const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
+    const uint32_t r_mont = mont_mul(r, k.mp.r2, k.mp);   // r 2^32 mod p
+    uint32_t w0 = mont_mul(m0, r_mont, k.mp);              // m0 r mod p
+    uint32_t w1 = mont_mul(m1, r_mont, k.mp);              // m1 r mod p
+    // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
+    w0 = M::add(w0, z, p);
+    w1 = M::sub(w1, z, p);
+    if (AUDIT) {
+      if (aud.w0) aud.w0[out_idx * L + slot] = w0;
+      if (aud.w1) aud.w1[out_idx * L + slot] = w1;
+    }
+    // step 9: P2 reconstructs w_k and tests it
+    any_zero |= (M::add(w0, w1, p) == 0u) ? 1u : 0u;
+  }
+  const uint32_t dprime = any_zero;
+
+  if (!RELU) {
+    // step 10: [DReLU']_0 = d0 from seed02 (P0 derives it), [DReLU']_1 to P1
+    const U32x4 rb = draw_block(kPair02, kPurReply, k.tensor_id, elem, 0, k.rk);
+    const Lane d0 = block_elem<Lane>(rb, 0) & mask;
+    const Lane d1 = ((Lane)dprime - d0) & mask;
+    // step 11: [DReLU] = [DReLU' xor t], the public t added by P0
+    out0 = t ? (Lane)((Lane)1 - d0) & mask : d0;
+    out1 = t ? ring_neg(d1, mask) : d1;
+    if (AUDIT && aud.reply) store_lane<Lane>(aud.reply, out_idx, d1);
+  } else {
+    const Triple<Lane> T = draw_triple<Lane>(kPurReluTriple, k.tensor_id, elem, mask, k.rk);
+    const Lane c1 = (Lane)((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0) & mask;   // P2 -> P1 (pre)
+    const Lane e = (Lane)((Lane)dprime - T.b0 - T.b1) & mask;             // P2 -> P0, P1
+    const Lane open0 = (Lane)(s0 - T.a0) & mask;                          // P0 -> P1
+    const Lane open1 = (Lane)(s1 - T.a1) & mask;                          // P1 -> P0
+    const Lane d = (Lane)(open0 + open1) & mask;
+    const Lane xd0 = (Lane)(d * (e + T.b0) + e * T.a0 + T.c0) & mask;
+    const Lane xd1 = (Lane)(d * T.b1 + e * T.a1 + c1) & mask;
+    out0 = t ? (Lane)(s0 - xd0) & mask : xd0;
+    out1 = t ? (Lane)(s1 - xd1) & mask : xd1;
+    if (AUDIT) {
+      if (aud.reply) store_lane<Lane>(aud.reply, out_idx, e);
+      if (aud.open0) store_lane<Lane>(aud.open0, out_idx, open0);
+      if (aud.open1) store_lane<Lane>(aud.open1, out_idx, open1);
+      if (aud.pre_c1) store_lane<Lane>(aud.pre_c1, out_idx, c1);
+    }
+  }
+  if (AUDIT) {
+    if (aud.t) aud.t[out_idx] = (uint8_t)t;
+    if (aud.dprime) aud.dprime[out_idx] = (uint8_t)dprime;
+  }
+}
+
+template <typename Lane, int LX, bool RELU, bool AUDIT>
+__global__ void __launch_bounds__(kBlock)
+    relu_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
+                uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, const AuditPtrs aud) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, RELU, AUDIT>(k, sh0[i], sh1[i], k.elem_base + i, perm, r0, r1,
+                                            aud, i);
+    o0[i] = r0;
+    o1[i] = r1;
+  }
+}
+
+template <typename Lane, int LX, bool RELU, bool AUDIT>
+cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n, void* o0,
+                     void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
+  auto kern = relu_kernel<Lane, LX, RELU, AUDIT>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t need = (n + kBlock - 1) / kBlock;
+  const uint64_t full = (uint64_t)num_sms * per_sm;
+  const unsigned grid = (unsigned)(need < full ? need : full);
+  if (grid == 0) return cudaSuccess;
+  kern<<<grid, kBlock, 0, s>>>(k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1),
+                               n, static_cast<Lane*>(o0), static_cast<Lane*>(o1), aud);
+  return cudaGetLastError();
+}
+
+template <typename Lane, bool RELU, bool AUDIT>
+cudaError_t launch_lx(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n,
+                      void* o0, void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
+  switch (k.lx) {
+    case 24: return launch_t<Lane, 24, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 14: return launch_t<Lane, 14, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 9: return launch_t<Lane, 9, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 7: return launch_t<Lane, 7, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    default: return launch_t<Lane, 0, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: one persistent launch over a tile table of many tensors.
+// Each CTA takes the next tile from an atomic counter (no waits), so uneven
+// tensors and mixed rings balance across the SMs.
+// ---------------------------------------------------------------------------
+
+template <typename Lane, int LX, bool RELU>
+__device__ __forceinline__ void run_tile(const BatchTensor& bt, const RoundKeys& rk,
+                                         uint64_t start, uint32_t count, uint32_t* perm) {
+  ReluConsts k = bt.k;
+  k.rk = rk;
+  const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
+  const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
+  Lane* o0 = static_cast<Lane*>(bt.o0);
+  Lane* o1 = static_cast<Lane*>(bt.o1);
+  const AuditPtrs none{};
+  for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
+    const uint64_t i = start + j;
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, RELU, false>(k, sh0[i], sh1[i], i, perm, r0, r1, none, i);
+    o0[i] = r0;
+    o1[i] = r1;
+  }
+}
+
+template <bool RELU>
+__device__ __forceinline__ void dispatch_tile(const BatchTensor& bt, const RoundKeys& rk,
+                                              uint64_t start, uint32_t count, uint32_t* perm) {
+  if (bt.lane64) {
+    if (bt.k.lx == 24) run_tile<uint64_t, 24, RELU>(bt, rk, start, count, perm);
+    else run_tile<uint64_t, 0, RELU>(bt, rk, start, count, perm);
+  } else {
+    if (bt.k.lx == 14) run_tile<uint32_t, 14, RELU>(bt, rk, start, count, perm);
+    else if (bt.k.lx == 9) run_tile<uint32_t, 9, RELU>(bt, rk, start, count, perm);
+    else run_tile<uint32_t, 0, RELU>(bt, rk, start, count, perm);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    relu_batch_kernel(const RoundKeys rk, const BatchTensor* __restrict__ tensors,
+                      const BatchTile* __restrict__ tiles, uint32_t ntiles,
+                      unsigned int* __restrict__ counter, int* __restrict__ status) {
+  __shared__ uint32_t perm_s[kMaxSlots * kBlock];
+  __shared__ uint32_t tile_s;
+  uint32_t* perm = perm_s + threadIdx.x;
+  for (;;) {
+    if (threadIdx.x == 0) tile_s = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = tile_s;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    const BatchTile tl = tiles[tile];
+    const BatchTensor& bt = tensors[tl.tensor];
+    if (tl.start + tl.count > bt.n) {   // a malformed table: record, skip
+      if (threadIdx.x == 0) atomicExch(status, BC_ECHECK);
+      continue;
+    }
+    if (bt.op == BC_OP_DRELU) dispatch_tile<false>(bt, rk, tl.start, tl.count, perm);
+    else dispatch_tile<true>(bt, rk, tl.start, tl.count, perm);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
+                        uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
+                        cudaStream_t s) {
+  const bool lane64 = k.ring_bits > 32;
+  const bool audit = aud.any();
+  if (lane64) {
+    if (relu) {
+      return audit ? launch_lx<uint64_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                   : launch_lx<uint64_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    }
+    return audit ? launch_lx<uint64_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                 : launch_lx<uint64_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+  }
+  if (relu) {
+    return audit ? launch_lx<uint32_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                 : launch_lx<uint32_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+  }
+  return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+               : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+}
+
+int relu_batch_max_ctas_per_sm() {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relu_batch_kernel, kBlock, 0) !=
+      cudaSuccess)
+    return 1;
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+cudaError_t launch_relu_batch(const RoundKeys& rk, const BatchTensor* tensors,
+                              const BatchTile* tiles, uint32_t ntiles, unsigned int* counter,
+                              int* status, int grid, cudaStream_t s) {
+  if (grid <= 0 || ntiles == 0) return cudaSuccess;
+  relu_batch_kernel<<<grid, kBlock, 0, s>>>(rk, tensors, tiles, ntiles, counter, status);
+  return cudaGetLastError();
+}
+
+}  // namespace bc

@@ -1,0 +1,302 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Integer protocol: every comparison is bit-exact.  Sizes span many CTAs and
+end on a ragged tail; the large cases use the benchmark's launch shape and
+compare sampled elements the oracle computes one by one.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2309_04909_gb300 import Context, Params, workloads as W
+from tests._util import cuda_ok, encode_np, masked, to_dev, to_np
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+SEED = 0x5EED_0000_0001
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = Context(SEED)
+    yield c
+    c.close()
+
+
+def _shares(ctx, bits, x_int, tid):
+    xg = torch.from_numpy(x_int.astype(np.int64)).cuda()
+    s0, s1 = ctx.share(bits, xg, tid)
+    return s0, s1
+
+
+@pytest.mark.parametrize("bits", [8, 16, 31, 32, 33, 48, 64])
+@pytest.mark.parametrize("n", [0, 1, 5, 10007, 155_651])
+def test_share_reconstruct(ctx, bits, n):
+    x = W.magnitude_bounded_ints(n, min(bits - 2, 40), seed=bits * 7 + n)
+    s0, s1 = _shares(ctx, bits, x, tid=3)
+    e0, e1 = O.share(bits, masked(x, bits), seed=SEED, tid=3)
+    assert np.array_equal(to_np(s0), e0.astype(to_np(s0).dtype))
+    assert np.array_equal(to_np(s1), e1.astype(to_np(s1).dtype))
+    rec = ctx.reconstruct(bits, s0, s1)
+    assert np.array_equal(to_np(rec).astype(np.uint64), masked(x, bits))
+
+
+@pytest.mark.parametrize("bits,k", [(64, 16), (64, 1), (64, 63), (32, 12), (16, 4), (8, 4), (40, 7)])
+def test_trunc_prob(ctx, bits, k):
+    n = 100_003
+    rng = np.random.default_rng(bits + k)
+    a = rng.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=n, dtype=np.uint64)
+    b = rng.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(3)
+    a, b = masked(a, bits), masked(b, bits)
+    o0, o1 = ctx.trunc_prob(bits, k, to_dev(a, bits), to_dev(b, bits))
+    e0, e1 = O.trunc_prob(bits, k, a, b)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+@pytest.mark.parametrize("bits,k1,k2", [(64, 16, 0), (64, 16, 16), (64, 3, 40), (64, 0, 8),
+                                        (32, 4, 3), (32, 12, 0), (8, 4, 1), (48, 10, 10)])
+def test_trunc_det(ctx, bits, k1, k2):
+    n = 77_777
+    rng = np.random.default_rng(bits * 3 + k1 + k2)
+    a = masked(rng.integers(0, 2**64, size=n, dtype=np.uint64), bits)
+    b = masked(rng.integers(0, 2**64, size=n, dtype=np.uint64), bits)
+    o0, o1 = ctx.trunc_det(bits, k1, k2, to_dev(a, bits), to_dev(b, bits))
+    e0, e1 = O.trunc_det(bits, k1, k2, a, b)
+    assert to_np(o0).dtype == (np.uint64 if bits - k1 - k2 > 32 else np.uint32)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+@pytest.mark.parametrize("lp", [1, 5, 9, 14, 24, 31])
+def test_mod_switch(ctx, lp):
+    n = 50_001
+    rng = np.random.default_rng(lp)
+    a = masked(rng.integers(0, 2**32, size=n, dtype=np.uint64), lp)
+    b = masked(rng.integers(0, 2**32, size=n, dtype=np.uint64), lp)
+    b[:100] = (np.uint64(1 << lp) - a[:100]) & np.uint64((1 << lp) - 1)   # zeros
+    for p in (O.prime_above(lp),):
+        o0, o1 = ctx.mod_switch(lp, p, to_dev(a, 32), to_dev(b, 32))
+        e0, e1 = O.mod_switch(lp, p, a, b)
+        assert np.array_equal(to_np(o0), e0)
+        assert np.array_equal(to_np(o1), e1)
+
+
+@pytest.mark.parametrize("bits", [64, 32, 16])
+def test_mul_beaver(ctx, bits):
+    n = 65_537
+    x = W.magnitude_bounded_ints(n, bits // 2 - 2, seed=1)
+    y = W.magnitude_bounded_ints(n, bits // 2 - 2, seed=2)
+    x0, x1 = _shares(ctx, bits, x, 10)
+    y0, y1 = _shares(ctx, bits, y, 11)
+    o0, o1 = ctx.mul_beaver(bits, x0, x1, y0, y1, tensor_id=12)
+    ex0, ex1 = O.share(bits, masked(x, bits), SEED, 10)
+    ey0, ey1 = O.share(bits, masked(y, bits), SEED, 11)
+    e0, e1 = O.mul_beaver(bits, ex0, ex1, ey0, ey1, SEED, 12)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+PROTO = [
+    # (ring, lx, c, magnitude bits of inputs, n)
+    (64, 24, 0, 23, 40_013),
+    (32, 9, 14, 22, 65_536),
+    (32, 14, 4, 17, 30_011),
+    (64, 7, 0, 6, 9_999),       # the paper's lx = 7 (5+2)
+    (64, 31, 2, 32, 5_003),     # widest window: p > 2^31
+    (16, 5, 2, 6, 7_001),       # generic-lx kernel
+    (8, 3, 0, 2, 4_097),
+    (33, 10, 3, 12, 3_001),
+]
+
+
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+@pytest.mark.parametrize("ring,lx,c,mag,n", PROTO)
+def test_protocol_parity_with_audit(ctx, op, ring, lx, c, mag, n):
+    x = W.magnitude_bounded_ints(n, mag, seed=ring + lx + c)
+    tid = 100 + lx
+    s0, s1 = _shares(ctx, ring, x, tid)
+    prm = Params(ring, lx, c)
+    P = O.params(ring, lx, c)
+    fn = ctx.drelu if op == "drelu" else ctx.relu
+    o0, o1, aud = fn(prm, s0, s1, tensor_id=tid + 1, audit=True)
+    es0, es1 = O.share(ring, masked(x, ring), SEED, tid)
+    ofn = O.drelu if op == "drelu" else O.relu
+    e0, e1, eaud = ofn(P, es0, es1, SEED, tid + 1, audit=True, threads=8)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+    L = lx + 1
+    assert np.array_equal(to_np(aud["w0"]).reshape(n, L), eaud["w0"])
+    assert np.array_equal(to_np(aud["w1"]).reshape(n, L), eaud["w1"])
+    assert np.array_equal(to_np(aud["t"]), eaud["t"])
+    assert np.array_equal(to_np(aud["dprime"]), eaud["dprime"])
+    assert np.array_equal(to_np(aud["reply"]).astype(np.uint64), eaud["reply"])
+    if op == "relu":
+        for k in ("open0", "open1", "pre_c1"):
+            assert np.array_equal(to_np(aud[k]).astype(np.uint64), eaud[k])
+
+
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+@pytest.mark.parametrize("ring,lx,c,mag,n", PROTO[:4])
+def test_protocol_parity_no_audit(ctx, op, ring, lx, c, mag, n):
+    """The kernel without message materialisation gives the same outputs."""
+    x = W.magnitude_bounded_ints(n, mag, seed=ring * 3 + lx)
+    s0, s1 = _shares(ctx, ring, x, 7)
+    fn = ctx.drelu if op == "drelu" else ctx.relu
+    o0, o1 = fn(Params(ring, lx, c), s0, s1, tensor_id=8)
+    es0, es1 = O.share(ring, masked(x, ring), SEED, 7)
+    ofn = O.drelu if op == "drelu" else O.relu
+    e0, e1 = ofn(O.params(ring, lx, c), es0, es1, SEED, 8, threads=8)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+def test_protocol_empty_and_single(ctx):
+    prm = Params(64, 24, 0)
+    z = torch.empty(0, dtype=torch.int64, device="cuda")
+    o0, o1 = ctx.relu(prm, z, z, tensor_id=1)
+    assert o0.numel() == 0
+    x = np.array([-5 * 2**16], dtype=np.int64)
+    s0, s1 = _shares(ctx, 64, x, 4)
+    o0, o1 = ctx.relu(prm, s0, s1, tensor_id=5)
+    es0, es1 = O.share(64, masked(x, 64), SEED, 4)
+    e0, e1 = O.relu(O.params(64, 24, 0), es0, es1, SEED, 5)
+    assert to_np(o0)[0] == e0[0] and to_np(o1)[0] == e1[0]
+
+
+def test_invalid_parameters_rejected(ctx):
+    from paper_2309_04909_gb300 import BicoptorError
+    s = torch.zeros(16, dtype=torch.int64, device="cuda")
+    for prm in (Params(64, 32, 0), Params(64, 24, 17), Params(64, 24, 0, p=16777217),
+                Params(64, 24, 0, p=2**24 - 3), Params(65, 8, 0), Params(64, 0, 0)):
+        with pytest.raises(BicoptorError):
+            ctx.relu(prm, s, s, tensor_id=1)
+    with pytest.raises(BicoptorError):
+        ctx.trunc_prob(64, 64, s, s)
+    with pytest.raises(BicoptorError):
+        ctx.mod_switch(9, 512, s.to(torch.int32), s.to(torch.int32))
+
+
+def test_comm_counters(ctx):
+    ctx.reset_comm()
+    n = 1000
+    x = W.magnitude_bounded_ints(n, 20, seed=5)
+    s0, s1 = _shares(ctx, 64, x, 1)
+    ctx.drelu(Params(64, 24, 0), s0, s1, tensor_id=2)
+    c = ctx.comm()
+    assert c["p0_to_p2"] == n * 25 * 25 and c["p1_to_p2"] == n * 25 * 25   # (lx+1)^2 bits
+    assert c["p2_to_p1"] == n * 64 and c["p2_to_p0"] == 0 and c["rounds"] == 2
+    ctx.reset_comm()
+    ctx.relu(Params(64, 7, 0), s0, s1, tensor_id=2)
+    c = ctx.comm()
+    assert c["p0_to_p2"] == n * 64   # the paper's 8 * 8 = 64 bits at lx = 7
+    assert c["p2_to_p0"] == n * 64 and c["p0_to_p1"] == n * 64 and c["pre_p2_to_p1"] == n * 64
+
+
+def test_count_trunc_failures(ctx):
+    n = 1 << 18
+    x = W.magnitude_bounded_ints(n, 60, seed=9)
+    s0, s1 = _shares(ctx, 64, x, 2)
+    o0, o1 = ctx.trunc_prob(64, 16, s0, s1)
+    xg = torch.from_numpy(x).cuda()
+    got = ctx.count_trunc_failures(64, 16, xg, o0, o1)
+    es0, es1 = O.share(64, masked(x, 64), SEED, 2)
+    e0, e1 = O.trunc_prob(64, 16, es0, es1)
+    rec = O.to_signed(O.reconstruct(64, e0, e1), 64)
+    d = (rec.astype(object) - (x >> 16).astype(object)) % 2**64
+    want = int(sum(1 for v in d if v not in (0, 1, 2**64 - 1)))
+    assert got == want and got > 0
+    d0, d1 = ctx.trunc_det(64, 16, 0, s0, s1)
+    assert ctx.count_trunc_failures(48, 16, xg, d0, d1) == 0
+
+
+def test_linear_relu_chain(ctx):
+    """Config-2-shaped chain at reduced size: product, both truncations and
+    the ReLU of the prob-truncated product, device and host-buffer paths."""
+    n, f, k = 50_021, 16, 16
+    X = W.gaussian_reals(n, 4.0, seed=1, stream=0)
+    Y = W.gaussian_reals(n, 4.0, seed=1, stream=1)
+    xi, yi = encode_np(X, f), encode_np(Y, f)
+    x0, x1 = _shares(ctx, 64, xi, 20)
+    y0, y1 = _shares(ctx, 64, yi, 21)
+    prm = Params(64, 24, 0)
+    w = ctx.linear_relu(64, k, prm, x0, x1, y0, y1, tensor_id=30)
+    # oracle chain
+    ex0, ex1 = O.share(64, masked(xi, 64), SEED, 20)
+    ey0, ey1 = O.share(64, masked(yi, 64), SEED, 21)
+    p0, p1 = O.mul_beaver(64, ex0, ex1, ey0, ey1, SEED, 30)
+    t0, t1 = O.trunc_prob(64, k, p0, p1)
+    d0, d1 = O.trunc_det(64, k, 0, p0, p1)
+    r0, r1 = O.relu(O.params(64, 24, 0), t0, t1, SEED, 31, threads=8)
+    for name, want in (("prod0", p0), ("prod1", p1), ("trc0", t0), ("trc1", t1), ("det0", d0),
+                       ("det1", d1), ("relu0", r0), ("relu1", r1)):
+        assert np.array_equal(to_np(w[name]).astype(np.uint64), want), name
+    # host-buffer entry point, chunked so the element offsets matter
+    ctx.reserve(12_000)
+    hx = [t.cpu().pin_memory() for t in (x0, x1, y0, y1)]
+    out = {nm: torch.empty(n, dtype=torch.int64).pin_memory() for nm in ("relu0", "relu1", "det0",
+                                                                           "det1")}
+    ctx.linear_relu_host(64, k, prm, *hx, tensor_id=30, out=out)
+    for name, want in (("relu0", r0), ("relu1", r1), ("det0", d0), ("det1", d1)):
+        assert np.array_equal(out[name].numpy().view(np.uint64), want), name
+
+
+def test_batch_matches_single_calls(ctx):
+    """Many tensors of uneven size and mixed rings in one persistent launch
+    give bit-identical results to one call per tensor."""
+    specs = [(64, 24, 0, 23), (32, 14, 4, 17), (32, 9, 14, 22), (64, 7, 0, 6), (16, 5, 2, 6)]
+    rng = np.random.default_rng(0)
+    items, singles = [], []
+    for ti in range(23):
+        ring, lx, c, mag = specs[ti % len(specs)]
+        n = int(rng.integers(1, 40_000)) if ti % 4 else int(rng.integers(100_000, 200_000))
+        x = W.magnitude_bounded_ints(n, mag, seed=ti)
+        s0, s1 = _shares(ctx, ring, x, 500 + ti)
+        prm = Params(ring, lx, c)
+        o0, o1 = ctx._empty(n, ring), ctx._empty(n, ring)
+        op = ti % 3 == 0  # some DReLU
+        items.append((prm, s0, s1, o0, o1, 900 + ti, 1 if op else 0))
+        fn = ctx.drelu if op else ctx.relu
+        singles.append(fn(prm, s0, s1, tensor_id=900 + ti))
+    for tile in (0, 1000, 4096):
+        for it in items:
+            it[3].fill_(0)
+            it[4].fill_(0)
+        ctx.relu_batch_plan(items, tile_elems=tile)
+        ctx.relu_batch_run()
+        assert ctx.batch_status() == 0
+        for it, (r0, r1) in zip(items, singles):
+            assert torch.equal(it[3], r0) and torch.equal(it[4], r1)
+
+
+def test_full_size_config2_sampled(ctx):
+    """N = 2^22 at l = 64, the benchmark's launch configuration; 4,096 sampled
+    elements recomputed by the oracle."""
+    n = 1 << 22
+    X = W.gaussian_reals(n, 4.0, seed=1, stream=0)
+    Y = W.gaussian_reals(n, 4.0, seed=1, stream=1)
+    xi, yi = encode_np(X, 16), encode_np(Y, 16)
+    x0, x1 = _shares(ctx, 64, xi, 1)
+    y0, y1 = _shares(ctx, 64, yi, 2)
+    prm = Params(64, 24, 0)
+    w = ctx.linear_relu(64, 16, prm, x0, x1, y0, y1, tensor_id=3)
+    idx = np.sort(np.random.default_rng(4).choice(n, 4096, replace=False)).astype(np.uint64)
+    t0, t1 = to_np(w["trc0"])[idx], to_np(w["trc1"])[idx]
+    r0, r1 = O.relu(O.params(64, 24, 0), t0, t1, SEED, 4, idx=idx, threads=8)
+    assert np.array_equal(to_np(w["relu0"])[idx], r0)
+    assert np.array_equal(to_np(w["relu1"])[idx], r1)
+    ex0, ex1 = O.share(64, masked(xi[idx], 64), SEED, 1, idx=idx)
+    ey0, ey1 = O.share(64, masked(yi[idx], 64), SEED, 2, idx=idx)
+    p0, p1 = O.mul_beaver(64, ex0, ex1, ey0, ey1, SEED, 3, idx=idx)
+    assert np.array_equal(to_np(w["prod0"])[idx], p0)
+    assert np.array_equal(to_np(w["prod1"])[idx], p1)
+    # property at any size: reconstructed ReLU = product * DReLU bit, and it
+    # equals max(prod_trunc, 0) up to the exception set and e0
+    rel = O.to_signed(O.reconstruct(64, to_np(w["relu0"]), to_np(w["relu1"])), 64)
+    trc = O.to_signed(O.reconstruct(64, to_np(w["trc0"]), to_np(w["trc1"])), 64)
+    ok = (rel == trc) | (rel == 0)
+    assert ok.all()
+    assert ((rel == np.maximum(trc, 0)).mean()) > 0.9999
