@@ -42,6 +42,7 @@ extern "C" {
 #define BC_ECUDA (-3)    /* a CUDA call failed (see bc_last_cuda_error)          */
 #define BC_ETIMEOUT (-4) /* a bounded device wait gave up (persistent batch)     */
 #define BC_ECHECK (-5)   /* a device-side consistency check failed               */
+#define BC_ELIMIT (-6)   /* request exceeds a fixed capacity (bc_relu_batch_static) */
 
 typedef struct bc_ctx bc_ctx;
 
@@ -186,6 +187,33 @@ int bc_relu_batch(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
 /* Status word of the last batched launch (BC_OK or BC_ETIMEOUT/BC_ECHECK);
  * synchronises the context's stream. */
 int bc_batch_status(bc_ctx *ctx);
+
+/* Batched ReLU/DReLU that allocates nothing.  The paper has no counterpart:
+ * this serves callers that may not call cudaMalloc -- code running inside a
+ * host engine that owns all device memory through its own pool, or a loop
+ * under a fixed memory budget where an allocation could fail or synchronise
+ * the device.  Such callers cannot create a bc_ctx, so this entry point takes
+ * the seed, device and stream directly.  It runs the same persistent
+ * tile-queue kernel as bc_relu_batch (same results for the same seed) with its
+ * scratch -- tensor table, tile table, work counter, status word -- in one
+ * fixed file-scope device array of about 310 KB, which every GPU that loads
+ * the library holds until the process exits.
+ *   - At most BC_STATIC_MAX_TENSORS tensors and BC_STATIC_MAX_TILES tiles of
+ *     `tile_elems` elements (0 = 4096) per call; larger requests return
+ *     BC_ELIMIT before anything is launched.
+ *   - The first call on a device looks up the array's device address (set-up);
+ *     make that first call before any stream capture.
+ *   - Calls share the array, which keeps the last call's contents; each call
+ *     clears the counter and status word it needs.  Calls that overlap on the
+ *     GPU (e.g. on two streams) race on the array.
+ *   - The tables are copied from pageable host staging, which orders the copy
+ *     after work already queued on `cuda_stream`.
+ *   - No communication is counted (there is no context).
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define BC_STATIC_MAX_TENSORS 256
+#define BC_STATIC_MAX_TILES 16384
+int bc_relu_batch_static(uint64_t seed, int device, void *cuda_stream,
+                         const bc_tensor_desc *descs, int count, int tile_elems);
 
 /* ---- fused product -> truncation -> ReLU (Sec. 4, Alg. smltrc/newtrc, Alg. relu) */
 

@@ -289,6 +289,30 @@ class Context:
         self._check(self._lib.bc_synchronize(self._h))
 
 
+def relu_batch_static(seed: int, items: Sequence[Tuple], tile_elems: int = 0,
+                      device: int = 0, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Batched ReLU/DReLU through bc_relu_batch_static: for callers that may
+    not allocate device memory (no Context needed; the library's fixed device
+    scratch is used).  items as for Context.relu_batch_plan.  Raises on an
+    error code; -6 (BC_ELIMIT) means the batch exceeds the fixed capacity of
+    256 tensors / 16384 tiles."""
+    lib = _native.lib()
+    arr = (TensorDesc * max(1, len(items)))()
+    for i, it in enumerate(items):
+        prm, s0, s1, o0, o1, tid = it[:6]
+        op = it[6] if len(it) > 6 else OP_RELU
+        arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
+                            s0.numel(), tid, op, prm.c_struct())
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    rc = lib.bc_relu_batch_static(seed, device, ctypes.c_void_p(s.cuda_stream), arr, len(items),
+                                  tile_elems)
+    if rc == -6:
+        raise BicoptorError("bc_relu_batch_static: batch exceeds the fixed scratch capacity "
+                            "(256 tensors, 16384 tiles)")
+    if rc != 0:
+        raise BicoptorError(f"bc_relu_batch_static failed: {lib.bc_strerror(rc).decode()}")
+
+
 def to_unsigned_numpy(t: torch.Tensor):
     """Copy a lane tensor to host as a uint32/uint64 numpy array."""
     import numpy as np

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libbicoptor.so")
-SOURCES = ["bc_relu.cu", "bc_elementwise.cu", "bc_api.cu"]
+SOURCES = ["bc_relu.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu"]
 HEADERS = ["bc_device.cuh", "bc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -149,6 +149,7 @@ SIGNATURES = {
     "bc_reserve": (c_int, [c_void_p, c_size]),
     "bc_count_trunc_failures": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                         c_size, c_void_p]),
+    "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),
 }
 
 
