@@ -237,8 +237,10 @@ def main():
     relu_avg = sum(relu_ms) / len(relu_ms)
     value = n * args.steps * world / (total_ms / 1e3)
     ops = costmodel.int_ops_per_element(LX, RING, relu=True)
-    peak = costmodel.int_issue_peak_ops()
-    achieved = ops * n / (relu_avg / 1e3)
+    muls = costmodel.mul_ops_per_element(LX, RING, relu=True)
+    peak = costmodel.int_mul_peak_ops()
+    achieved = muls * n / (relu_avg / 1e3)
+    issue_frac = ops * n / (relu_avg / 1e3) / costmodel.int_issue_peak_ops()
 
     line = {
         "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
@@ -250,10 +252,15 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 384 MB per step > 129 MB L2; no flush"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "Tops/s (int32)", "frac": achieved / peak, "traffic": None,
-                     "kernel": "relu_kernel<uint64_t,24,ReLU>",
-                     "ops_per_element": ops, "kernel_ms": relu_avg,
-                     "peak_basis": "152 SM x 4 issue/clk x 32 lanes x 2070 MHz"},
+                     "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
+                     "mul_ops_per_element": muls, "kernel_ms": relu_avg,
+                     "peak_basis": "integer multiplier: 152 SM x 4 x 16-lane FMA-heavy pipe "
+                                   "x 2070 MHz (derived, see DESIGN.md)",
+                     "int_ops_per_element": ops,
+                     "issue_frac": issue_frac,
+                     "hbm_bytes_per_element": costmodel.hbm_bytes_per_element_relu(RING)},
         "gpu_launches": 4 * args.steps,
         "clocks": ck,
         "step_breakdown_ms": {"product_and_truncations": sum(pre_ms) / len(pre_ms),
@@ -331,6 +338,13 @@ def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):
     return out
 
 
+def b_persist_ms(ctx, items):
+    """Best persistent-schedule time over the autotuner's tile candidates."""
+    from paper_2309_04909_gb300.batch import TILE_CANDIDATES, ReluBatch, time_ms
+    return min(time_ms(ReluBatch(ctx, items, t, c, 0).run, reps=3, warmup=1)
+               for t in TILE_CANDIDATES for c in (0, 2))
+
+
 def vgg16_batched_vs_plain(ctx, dev, batch=128):
     """Config-3 shape: the 13 ReLU tensors of a VGG-16 on 32x32 inputs for
     `batch` images (1,664 tensors, 35,389,440 elements at batch 128), l = 64,
@@ -367,7 +381,7 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
         plain()
     plain_graph_ms = time_ms(g.replay, reps=5, warmup=1)
     best = autotune(ctx, items, reps=2, use_cache=False)
-    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"])
+    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"])
     batched_ms = time_ms(b.run, reps=5, warmup=1)
     b.capture()
     batched_graph_ms = time_ms(b.run, reps=5, warmup=1)
@@ -379,7 +393,9 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "speedup_vs_plain_eager": plain_ms / batched_graph_ms,
             "speedup_vs_plain_graph": plain_graph_ms / batched_graph_ms,
             "batched_elems_per_s": total / (batched_graph_ms / 1e3),
+            "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+            "persistent_best_ms": b_persist_ms(ctx, items),
             "status": b.status(), "identical_to_plain": identical}
 
 

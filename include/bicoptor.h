@@ -165,21 +165,35 @@ typedef struct {
   uint32_t tensor_id;      /* keys the randomness of this tensor          */
   int op;                  /* BC_OP_RELU or BC_OP_DRELU                   */
   bc_drelu_params params;
+  uint64_t elem_offset;    /* element index of sh0[0] within the tensor
+                              `tensor_id` (a slice of a larger tensor gets
+                              the randomness of those elements); usually 0 */
 } bc_tensor_desc;
 
-/* Tile configuration of the batched launch (0 fields = library default). */
+/* Schedule of the batched launch (0 fields = library default).
+ *   schedule     BC_SCHED_PERSISTENT: per parameter group, one persistent
+ *                grid whose warps take tiles from an atomic work counter;
+ *                BC_SCHED_GRID: one CTA per tile of 256 elements (the
+ *                hardware CTA scheduler is the queue; tile_elems ignored)
+ *   tile_elems   elements per queue tile (persistent schedule; default 512)
+ *   ctas_per_sm  resident CTAs per SM of the persistent grid (0 = occupancy) */
+#define BC_SCHED_PERSISTENT 0
+#define BC_SCHED_GRID 1
 typedef struct {
-  int tile_elems;          /* elements per queue tile                     */
-  int ctas_per_sm;         /* resident CTAs per SM of the persistent grid */
+  int tile_elems;
+  int ctas_per_sm;
+  int schedule;
 } bc_batch_config;
 
-/* Plan a batch: build the tile table of `count` tensors on the host and copy
- * it to device workspace owned by the context (grown here, not in
- * bc_relu_batch_run).  The plan stays valid until the next bc_relu_batch_plan. */
+/* Plan a batch: group the tensors by parameters (l, lx, c, p; at most 32
+ * groups), build the tile table on the host and copy it to device workspace
+ * owned by the context (grown here, not in bc_relu_batch_run).  The plan
+ * stays valid until the next bc_relu_batch_plan. */
 int bc_relu_batch_plan(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
                        const bc_batch_config *cfg);
-/* Run the planned batch as one persistent launch pulling tiles from an atomic
- * work counter.  Stream-capturable (no host synchronisation inside). */
+/* Run the planned batch: one launch per parameter group (one launch for a
+ * single-parameter batch), persistent or grid as planned.  Stream-capturable
+ * (no host synchronisation inside). */
 int bc_relu_batch_run(bc_ctx *ctx);
 /* plan + run. */
 int bc_relu_batch(bc_ctx *ctx, const bc_tensor_desc *descs, int count,

@@ -405,12 +405,26 @@ int orc_drelu_core(const orc_params *P, uint64_t s0, uint64_t s1, int t, const u
     return dprime;
 }
 
+/* 2^-32 mod p, by Fermat's little theorem: (2^32)^(p-2) mod p. */
+static uint32_t inv_two32_mod_p(uint32_t p)
+{
+    uint64_t base = ((uint64_t)1 << 32) % p, acc = 1, e = (uint64_t)p - 2;
+    while (e) {
+        if (e & 1) acc = (acc * base) % p;
+        base = (base * base) % p;
+        e >>= 1;
+    }
+    return (uint32_t)acc;
+}
+
 /* The seed01 draws of one element: t, the shuffle words, and (r_k, z_k).
- * READING: r_k = 1 + floor(W64 * (p-1) / 2^64), z_k = floor(W64' * p / 2^64)
- * from two 64-bit words of the slot's mask block (words 4k..4k+3, low word
- * first), which keeps every draw within 2^-(64 - log2 p) of uniform. */
+ * READING: from two 64-bit words W, W' of the slot's mask block (words
+ * 4k..4k+3, low word first), rho_k = 1 + floor(W (p-1) / 2^64) and
+ * z_k = floor(W' p / 2^64), each within 2^-(64 - log2 p) of uniform; the
+ * mask is r_k = rho_k * 2^-32 mod p, which is as uniform on Z_p^* as rho_k
+ * (multiplying by the unit 2^-32 permutes Z_p^*). */
 static void draw_seed01(const orc_params *P, uint64_t seed, uint32_t tid, uint64_t elem,
-                        int *t, uint32_t *fy, uint32_t *r, uint32_t *z)
+                        uint32_t inv32, int *t, uint32_t *fy, uint32_t *r, uint32_t *z)
 {
     const int L = P->lx + 1;
     *t = (int)(orc_stream_word(seed, PAIR_01, PUR_PERM, tid, elem, 0) & 1u);
@@ -420,7 +434,8 @@ static void draw_seed01(const orc_params *P, uint64_t seed, uint32_t tid, uint64
                       ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 1) << 32);
         uint64_t wz = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 2) |
                       ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 3) << 32);
-        r[k] = 1u + (uint32_t)(((u128)wr * (u128)(P->p - 1u)) >> 64);
+        uint32_t rho = 1u + (uint32_t)(((u128)wr * (u128)(P->p - 1u)) >> 64);
+        r[k] = (uint32_t)(((uint64_t)rho * inv32) % P->p);
         z[k] = (uint32_t)(((u128)wz * (u128)P->p) >> 64);
     }
 }
@@ -461,6 +476,7 @@ int orc_drelu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const
 {
     if (check_params(P)) return -1;
     const int ell = P->ell, L = P->lx + 1;
+    const uint32_t inv32 = inv_two32_mod_p(P->p);
     (void)threads;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
@@ -470,7 +486,7 @@ int orc_drelu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const
         uint64_t elem = elem_index(idx, i);
         int t;
         uint32_t fy[MAXL], r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
-        draw_seed01(P, seed, tid, elem, &t, fy, r, z);
+        draw_seed01(P, seed, tid, elem, inv32, &t, fy, r, z);
         int dprime = orc_drelu_core(P, s0[i], s1[i], t, fy, r, z, msg0, msg1);
         uint64_t d0 = stream_ring(seed, PAIR_02, PUR_REPLY, tid, elem, 0, ell);
         uint64_t d1 = rmod((uint64_t)dprime - d0, ell);
@@ -498,6 +514,7 @@ int orc_relu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const 
 {
     if (check_params(P)) return -1;
     const int ell = P->ell, L = P->lx + 1;
+    const uint32_t inv32 = inv_two32_mod_p(P->p);
     (void)threads;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
@@ -510,7 +527,7 @@ int orc_relu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const 
         /* P0, P1 run Alg. drelu up to step 8; P2 runs step 9 */
         int t;
         uint32_t fy[MAXL], r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
-        draw_seed01(P, seed, tid, elem, &t, fy, r, z);
+        draw_seed01(P, seed, tid, elem, inv32, &t, fy, r, z);
         int dprime = orc_drelu_core(P, s0[i], s1[i], t, fy, r, z, msg0, msg1);
         /* P2 responds e = DReLU' - b */
         uint64_t e = rmod((uint64_t)dprime - (T.b0 + T.b1), ell);

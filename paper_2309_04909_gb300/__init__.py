@@ -210,18 +210,21 @@ class Context:
         return self._protocol(self._lib.bc_relu, prm, s0, s1, tensor_id, out, audit)
 
     # -- batched ------------------------------------------------------------------
-    def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0):
-        """items: (prm, s0, s1, o0, o1, tensor_id[, op]) per tensor."""
+    def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0,
+                        schedule: int = 0):
+        """items: (prm, s0, s1, o0, o1, tensor_id[, op[, elem_offset]]) per tensor;
+        schedule 0 = persistent tile queue, 1 = one CTA per 256-element tile."""
         arr = (TensorDesc * max(1, len(items)))()
         self._batch_keep = list(items)
         for i, it in enumerate(items):
             prm, s0, s1, o0, o1, tid = it[:6]
             op = it[6] if len(it) > 6 else OP_RELU
+            off = it[7] if len(it) > 7 else 0
             for t, nm in ((s0, "s0"), (s1, "s1"), (o0, "o0"), (o1, "o1")):
                 self._need(t, prm.ring_bits, nm)
             arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
-                                s0.numel(), tid, op, prm.c_struct())
-        cfg = BatchConfig(tile_elems, ctas_per_sm)
+                                s0.numel(), tid, op, prm.c_struct(), off)
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule)
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_plan(self._h, arr, len(items), ctypes.byref(cfg)))
 
@@ -302,7 +305,7 @@ def relu_batch_static(seed: int, items: Sequence[Tuple], tile_elems: int = 0,
         prm, s0, s1, o0, o1, tid = it[:6]
         op = it[6] if len(it) > 6 else OP_RELU
         arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
-                            s0.numel(), tid, op, prm.c_struct())
+                            s0.numel(), tid, op, prm.c_struct(), it[7] if len(it) > 7 else 0)
     s = stream if stream is not None else torch.cuda.current_stream(device)
     rc = lib.bc_relu_batch_static(seed, device, ctypes.c_void_p(s.cuda_stream), arr, len(items),
                                   tile_elems)

@@ -99,11 +99,12 @@ class Audit(ctypes.Structure):
 
 class TensorDesc(ctypes.Structure):
     _fields_ = [("sh0", c_void_p), ("sh1", c_void_p), ("o0", c_void_p), ("o1", c_void_p),
-                ("n", c_u64), ("tensor_id", c_u32), ("op", c_int), ("params", DreluParams)]
+                ("n", c_u64), ("tensor_id", c_u32), ("op", c_int), ("params", DreluParams),
+                ("elem_offset", c_u64)]
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("tile_elems", c_int), ("ctas_per_sm", c_int)]
+    _fields_ = [("tile_elems", c_int), ("ctas_per_sm", c_int), ("schedule", c_int)]
 
 
 class LinearReluArgs(ctypes.Structure):

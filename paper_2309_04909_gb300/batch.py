@@ -19,18 +19,19 @@ from . import Context, Params, OP_RELU
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-TILE_CANDIDATES = (1024, 2048, 4096, 8192, 16384)
+TILE_CANDIDATES = (128, 256, 512, 1024, 2048)
 
 
 class ReluBatch:
     """items: (Params, s0, s1, o0, o1, tensor_id[, op]) per tensor."""
 
     def __init__(self, ctx: Context, items: Sequence[Tuple], tile_elems: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, schedule: int = 0):
         self.ctx = ctx
         self.items = list(items)
         self.tile_elems = tile_elems
         self.ctas_per_sm = ctas_per_sm
+        self.schedule = schedule
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.plan()
 
@@ -39,7 +40,7 @@ class ReluBatch:
         return int(sum(it[1].numel() for it in self.items))
 
     def plan(self):
-        self.ctx.relu_batch_plan(self.items, self.tile_elems, self.ctas_per_sm)
+        self.ctx.relu_batch_plan(self.items, self.tile_elems, self.ctas_per_sm, self.schedule)
         self.graph = None
 
     def run(self):
@@ -88,8 +89,9 @@ def _mix_key(items) -> str:
 
 def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
              use_cache: bool = True) -> Dict[str, float]:
-    """Time every (tile, ctas_per_sm) candidate on `items`; returns the best
-    {"tile_elems", "ctas_per_sm", "ms"}.  Outputs of the tensors are written
+    """Time the grid schedule and every persistent (tile, ctas_per_sm)
+    candidate on `items`; returns the best {"schedule", "tile_elems",
+    "ctas_per_sm", "ms"}.  Outputs of the tensors are written
     (the protocol is deterministic, so reruns give identical results)."""
     key = _mix_key(items)
     cache = {}
@@ -100,13 +102,15 @@ def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
             cache = {}
         if key in cache:
             return cache[key]
-    best = None
+    b = ReluBatch(ctx, items, 0, 0, schedule=1)
+    best = {"schedule": 1, "tile_elems": 256, "ctas_per_sm": 0,
+            "ms": time_ms(b.run, reps=reps, warmup=1)}
     for tile in TILE_CANDIDATES:
-        for cps in (1, 2, 3, 4):
-            b = ReluBatch(ctx, items, tile, cps)
+        for cps in (0, 1, 2, 3):
+            b = ReluBatch(ctx, items, tile, cps, schedule=0)
             ms = time_ms(b.run, reps=reps, warmup=1)
-            if best is None or ms < best["ms"]:
-                best = {"tile_elems": tile, "ctas_per_sm": cps, "ms": ms}
+            if ms < best["ms"]:
+                best = {"schedule": 0, "tile_elems": tile, "ctas_per_sm": cps, "ms": ms}
     cache[key] = best
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

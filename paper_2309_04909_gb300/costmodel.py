@@ -1,37 +1,42 @@
 """Algorithmic work of the hot path, per element, for the roofline.
 
-The fused DReLU/ReLU kernel is bound by integer issue, not by HBM: per element
-it moves 32 bytes (l = 64: two input shares, two output shares) but executes
-thousands of 32-bit integer operations.  This module fixes the count of
-integer operations the protocol needs per element (the "algorithmic ops"),
-step by step, so that achieved = ops x elements / time can be set against the
-GPU's integer issue peak.  Counting rules (one op = one 32-bit integer
-instruction a GPU thread must issue at minimum):
+The fused DReLU/ReLU kernel is bound by the GPU's integer units, not by HBM:
+per element it moves 32 bytes (l = 64: two input shares, two output shares)
+but needs thousands of 32-bit integer operations, about a third of them
+multiplications.  On GB300 integer multiplies (IMAD, IMAD.WIDE, IMAD.HI) run on
+the 16-lane FMA-heavy pipe of each SM sub-partition, half the width of the
+issue port, so the multiplier is the binding unit; the remaining operations
+(XOR, add, shift, compare, select) go to the 16-lane ALU pipe.
 
-  Philox-4x32-10 block          10 rounds x (2 widening multiplies + 2 three-input XORs) = 40
-  per message slot (lx+1 slots), both parties and the helper:
-      window (Alg. newtrc2)     2 parties x 2 windows x (shift + mask)                   =  8
-      pair sum (step 4)         2 parties x (add + mask)                                 =  4
-      modulo switch (step 5)    P0 test + select, P1 add                                 =  3
-      r_k, z_k from 128 bits    2 x 2 multiplies + 1 add                                 =  5
-      masking (step 7)          3 Montgomery products x 5 (r to Montgomery form, 2 shares)= 15
-      reshare (step 8)          2 x (add, compare, select)                               =  6
-      P2 (step 9)               add mod p (3) + zero test and OR (2)                     =  5
-  shuffle (step 6)              lx swaps x (index multiply + 2 loads + 2 stores)         = 5 lx
-  flip (steps 1-2)              2 negations on 64/32-bit lanes                           =  6
-  ReLU finish (Alg. relu)       triple completion, openings, 3 products, select:
-                                40 ops on 64-bit lanes, 20 on 32-bit lanes
-  DReLU finish (steps 10-11)    8 ops
-Philox blocks per element: ceil((lx+1)/4) (t and shuffle) + (lx+1) (masks) +
-3 (ReLU triple at l > 32; 2 at l <= 32) or 1 (DReLU reply).
+Counting rules, per element, of what the protocol as specified needs (the
+implementation may do less, e.g. by reusing a product across Philox blocks;
+that shows up as a higher fraction of the roofline, not as less work):
 
-The elementwise kernels (sharing, truncations, modulo switch) are HBM-bound;
-their algorithmic bytes are the lanes read plus the lanes written.
+  Philox-4x32-10 block   10 rounds x (2 widening 32x32->64 multiplies + 2 three-input XORs)
+  per message slot (lx + 1 slots), both parties and the helper:
+      window (Alg. newtrc2)     2 parties x 2 windows x (shift + mask)              8 ops
+      pair sum (step 4)         2 parties x (add + mask)                            4
+      modulo switch (step 5)    P0 test + select, P1 add                            3
+      rho_k, z_k from 128 bits  2 x (high product of the low word + widening)       5 ops, 2x3 mul
+      masking (step 7)          2 Montgomery products (wide, low, wide, cmp, sel)  10 ops, 2x5 mul
+      reshare (step 8)          2 x (add, compare, select)                          6
+      P2 (step 9)               add mod p (3) + zero test and OR (2)                5
+  shuffle (step 6)    lx swaps x (index high-multiply + 2 loads + 2 stores)         5 lx, lx mul
+  flip (steps 1-2)    2 negations                                                   6
+  ReLU finish         triple completion, openings, 5 ring products, select          40 ops (l>32) / 20
+  DReLU finish        reply and unflip                                              8 ops
+Philox blocks per element: ceil((lx+1)/4) (t and the shuffle) + (lx+1) (masks) +
+3 (ReLU triple, l > 32; 2 at l <= 32) or 1 (DReLU reply).
+
+"mul" counts multiplier lane-operations: a widening 32x32->64 product is 2, a
+low or high 32-bit product 1, a 64-bit low product 4.
 """
 from __future__ import annotations
 
 PHILOX_BLOCK_OPS = 40
-SLOT_OPS = 8 + 4 + 3 + 5 + 15 + 6 + 5     # = 46
+PHILOX_BLOCK_MUL = 40             # 20 widening products
+SLOT_OPS = 8 + 4 + 3 + 5 + 10 + 6 + 5     # = 41
+SLOT_MUL = 6 + 10                          # draws + 2 Montgomery products
 
 
 def philox_blocks(lx: int, ring_bits: int, relu: bool) -> int:
@@ -47,13 +52,29 @@ def int_ops_per_element(lx: int, ring_bits: int, relu: bool = True) -> int:
             + finish)
 
 
+def mul_ops_per_element(lx: int, ring_bits: int, relu: bool = True) -> int:
+    """Multiplier lane-operations per element (see module doc)."""
+    L = lx + 1
+    finish = (20 if ring_bits > 32 else 5) if relu else 0
+    return philox_blocks(lx, ring_bits, relu) * PHILOX_BLOCK_MUL + L * SLOT_MUL + lx + finish
+
+
 def hbm_bytes_per_element_relu(ring_bits: int) -> int:
     lane = 8 if ring_bits > 32 else 4
     return 4 * lane            # read [x]_0, [x]_1; write two output shares
 
 
-def int_issue_peak_ops(sm_count: int = 152, sm_mhz: float = 2070.0) -> float:
-    """Integer issue peak: each SM issues 4 warp instructions per clock (one
-    per scheduler), i.e. 128 32-bit lane operations per clock when the ALU and
-    FMA (IMAD) pipes are both fed.  Uses the maximum SM clock."""
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def int_issue_peak_ops(sm_count: int = SM_COUNT, sm_mhz: float = SM_MAX_MHZ) -> float:
+    """Issue peak: 4 schedulers per SM each issue one warp instruction (32
+    lanes) per clock."""
     return sm_count * 4 * 32 * sm_mhz * 1e6
+
+
+def int_mul_peak_ops(sm_count: int = SM_COUNT, sm_mhz: float = SM_MAX_MHZ) -> float:
+    """Integer-multiplier peak: 4 sub-partitions per SM, each with a 16-lane
+    FMA-heavy pipe that executes IMAD-class instructions."""
+    return sm_count * 4 * 16 * sm_mhz * 1e6

@@ -27,13 +27,20 @@ struct bc_ctx {
   // batched launch plan
   bc::BatchTensor* d_tensors = nullptr;
   bc::BatchTile* d_tiles = nullptr;
-  bc::BatchTensor* h_tensors = nullptr;   // pinned
-  bc::BatchTile* h_tiles = nullptr;       // pinned
+  // pinned host staging of the tables, double-buffered: buffer i may be
+  // refilled once the copy recorded by plan_ev[i] has finished
+  bc::BatchTensor* h_tensors[2] = {nullptr, nullptr};
+  bc::BatchTile* h_tiles[2] = {nullptr, nullptr};
+  cudaEvent_t plan_ev[2] = {nullptr, nullptr};
+  bool plan_ev_live[2] = {false, false};
+  int plan_next = 0;
   size_t cap_tensors = 0, cap_tiles = 0;
-  unsigned int* d_counter = nullptr;
+  unsigned int* d_counter = nullptr;     // one work counter per parameter group
   int* d_status = nullptr;
   uint32_t ntiles = 0;
-  int batch_grid = 0;
+  int batch_ctas_per_sm = 0;
+  bc::BatchGroup groups[bc::kMaxBatchGroups];
+  int ngroups = 0;
   bc_comm batch_comm{};                   // what one run of the plan adds
   bool planned = false;
   // host staging for bc_linear_relu_host: two sets of chunk buffers
@@ -216,10 +223,12 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int) * bc::kMaxBatchGroups);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&ctx->plan_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     int rc = (e == cudaErrorMemoryAllocation) ? BC_ENOMEM : BC_ECUDA;
     bc_destroy(ctx);
@@ -239,8 +248,11 @@ int bc_destroy(bc_ctx* ctx) {
   }
   cudaFree(ctx->d_tensors);
   cudaFree(ctx->d_tiles);
-  cudaFreeHost(ctx->h_tensors);
-  cudaFreeHost(ctx->h_tiles);
+  for (int i = 0; i < 2; ++i) {
+    cudaFreeHost(ctx->h_tensors[i]);
+    cudaFreeHost(ctx->h_tiles[i]);
+    if (ctx->plan_ev[i]) cudaEventDestroy(ctx->plan_ev[i]);
+  }
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_status);
   cudaFree(ctx->stage[0]);
@@ -362,13 +374,17 @@ int bc_reset_comm(bc_ctx* ctx) {
 int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
                        const bc_batch_config* cfg) {
   if (!ctx || count < 0 || (count > 0 && !descs)) return BC_EINVAL;
-  const int tile = (cfg && cfg->tile_elems > 0) ? cfg->tile_elems : 4096;
+  const bool grid_sched = cfg && cfg->schedule == BC_SCHED_GRID;
+  if (cfg && cfg->schedule != BC_SCHED_GRID && cfg->schedule != BC_SCHED_PERSISTENT)
+    return BC_EINVAL;
+  const int tile = grid_sched ? bc::kBlock : (cfg && cfg->tile_elems > 0) ? cfg->tile_elems : 512;
   if (tile > (1 << 30)) return BC_EINVAL;
-  int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : bc::relu_batch_max_ctas_per_sm();
-  per_sm = std::min(per_sm, bc::relu_batch_max_ctas_per_sm());
-  // the pinned staging may still feed an earlier plan's copies
-  CK(cudaStreamSynchronize(ctx->stream));
+  // persistent: CTAs per SM (0 = occupancy); grid schedule: -1
+  const int per_sm = grid_sched ? -1 : (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 0;
   std::vector<bc::BatchTensor> tens((size_t)count);
+  std::vector<int> grp((size_t)count);
+  bc::BatchGroup groups[bc::kMaxBatchGroups];
+  int ngroups = 0;
   size_t ntiles = 0;
   bc_comm add{};
   for (int t = 0; t < count; ++t) {
@@ -376,72 +392,103 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
     if (d.op != BC_OP_RELU && d.op != BC_OP_DRELU) return BC_EINVAL;
     if (d.n && (!d.sh0 || !d.sh1 || !d.o0 || !d.o1)) return BC_EINVAL;
     bc::ReluConsts k;
-    int rc = make_consts(ctx, &d.params, d.tensor_id, &k);
+    int rc = make_consts(ctx, &d.params, 0, &k);
     if (rc) return rc;
+    int g = 0;
+    while (g < ngroups && !(groups[g].k.ring_bits == k.ring_bits && groups[g].k.lx == k.lx &&
+                            groups[g].k.c == k.c && groups[g].k.mp.p == k.mp.p))
+      ++g;
+    if (g == ngroups) {
+      if (ngroups == bc::kMaxBatchGroups) return BC_EINVAL;   // too many parameter sets
+      groups[ngroups].k = k;
+      groups[ngroups].begin = groups[ngroups].end = 0;
+      ++ngroups;
+    }
+    grp[t] = g;
     tens[t].sh0 = d.sh0;
     tens[t].sh1 = d.sh1;
     tens[t].o0 = d.o0;
     tens[t].o1 = d.o1;
     tens[t].n = d.n;
-    tens[t].k = k;
+    tens[t].tensor_id = d.tensor_id;
     tens[t].op = d.op;
-    tens[t].lane64 = d.params.ring_bits > 32;
+    tens[t].elem_offset = d.elem_offset;
     ntiles += (d.n + tile - 1) / tile;
     add_comm(&add, relu_comm(d.params.ring_bits, d.params.lx, d.n, d.op == BC_OP_RELU));
   }
   if (ntiles > 0xFFFFFFF0u) return BC_EINVAL;
   add.rounds = count ? 2 : 0;   // all tensors share the two rounds of one batched call
   add.calls = count ? 1 : 0;
-  if ((size_t)count > ctx->cap_tensors) {
+  if ((size_t)count > ctx->cap_tensors || ntiles > ctx->cap_tiles) {
+    // growing: everything queued that may read the old tables must finish
+    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t capt = std::max<size_t>(std::max<size_t>(count, 64), ctx->cap_tensors);
+    const size_t capl = std::max<size_t>(std::max<size_t>(ntiles, 1024), ctx->cap_tiles);
     cudaFree(ctx->d_tensors);
-    cudaFreeHost(ctx->h_tensors);
-    ctx->d_tensors = nullptr;
-    ctx->h_tensors = nullptr;
-    ctx->cap_tensors = 0;
-    size_t cap = std::max<size_t>(count, 64);
-    if (cudaMalloc(&ctx->d_tensors, cap * sizeof(bc::BatchTensor)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_tensors, cap * sizeof(bc::BatchTensor)) != cudaSuccess)
-      return BC_ENOMEM;
-    ctx->cap_tensors = cap;
-  }
-  if (ntiles > ctx->cap_tiles) {
     cudaFree(ctx->d_tiles);
-    cudaFreeHost(ctx->h_tiles);
+    ctx->d_tensors = nullptr;
     ctx->d_tiles = nullptr;
-    ctx->h_tiles = nullptr;
-    ctx->cap_tiles = 0;
-    size_t cap = std::max<size_t>(ntiles, 1024);
-    if (cudaMalloc(&ctx->d_tiles, cap * sizeof(bc::BatchTile)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_tiles, cap * sizeof(bc::BatchTile)) != cudaSuccess)
+    for (int i = 0; i < 2; ++i) {
+      cudaFreeHost(ctx->h_tensors[i]);
+      cudaFreeHost(ctx->h_tiles[i]);
+      ctx->h_tensors[i] = nullptr;
+      ctx->h_tiles[i] = nullptr;
+      ctx->plan_ev_live[i] = false;
+    }
+    ctx->cap_tensors = ctx->cap_tiles = 0;
+    bool ok = cudaMalloc(&ctx->d_tensors, capt * sizeof(bc::BatchTensor)) == cudaSuccess &&
+              cudaMalloc(&ctx->d_tiles, capl * sizeof(bc::BatchTile)) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+      ok = cudaMallocHost(&ctx->h_tensors[i], capt * sizeof(bc::BatchTensor)) == cudaSuccess &&
+           cudaMallocHost(&ctx->h_tiles[i], capl * sizeof(bc::BatchTile)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
       return BC_ENOMEM;
-    ctx->cap_tiles = cap;
+    }
+    ctx->cap_tensors = capt;
+    ctx->cap_tiles = capl;
   }
-  if (count) memcpy(ctx->h_tensors, tens.data(), sizeof(bc::BatchTensor) * count);
-  // Tiles are laid out largest-tensor-first so the long tensors start early
-  // and the short ones fill the tail of the persistent grid.
+  // this plan's staging buffer: wait only for ITS previous copy to finish
+  const int sb = ctx->plan_next;
+  if (ctx->plan_ev_live[sb]) CK(cudaEventSynchronize(ctx->plan_ev[sb]));
+  bc::BatchTensor* h_tensors = ctx->h_tensors[sb];
+  bc::BatchTile* h_tiles = ctx->h_tiles[sb];
+  if (count) memcpy(h_tensors, tens.data(), sizeof(bc::BatchTensor) * count);
+  // Tiles grouped by parameter group; within a group the largest tensors come
+  // first so the long ones start early and short ones fill the tail.
   std::vector<int> order(count);
   for (int t = 0; t < count; ++t) order[t] = t;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return descs[a].n > descs[b].n; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return grp[a] != grp[b] ? grp[a] < grp[b] : descs[a].n > descs[b].n;
+  });
   size_t w = 0;
   for (int oi = 0; oi < count; ++oi) {
     const int t = order[oi];
+    if (oi == 0 || grp[order[oi - 1]] != grp[t]) groups[grp[t]].begin = (uint32_t)w;
     for (uint64_t s = 0; s < descs[t].n; s += tile) {
       bc::BatchTile bt;
       bt.tensor = (uint32_t)t;
       bt.start = s;
       bt.count = (uint32_t)std::min<uint64_t>(tile, descs[t].n - s);
-      ctx->h_tiles[w++] = bt;
+      h_tiles[w++] = bt;
     }
+    groups[grp[t]].end = (uint32_t)w;
   }
+  // Stream order puts these copies after every kernel already queued, so a
+  // batch still running keeps reading the previous tables until it is done.
   if (count)
-    CK(cudaMemcpyAsync(ctx->d_tensors, ctx->h_tensors, sizeof(bc::BatchTensor) * count,
+    CK(cudaMemcpyAsync(ctx->d_tensors, h_tensors, sizeof(bc::BatchTensor) * count,
                        cudaMemcpyHostToDevice, ctx->stream));
   if (w)
-    CK(cudaMemcpyAsync(ctx->d_tiles, ctx->h_tiles, sizeof(bc::BatchTile) * w,
+    CK(cudaMemcpyAsync(ctx->d_tiles, h_tiles, sizeof(bc::BatchTile) * w,
                        cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(ctx->plan_ev[sb], ctx->stream));
+  ctx->plan_ev_live[sb] = true;
+  ctx->plan_next = sb ^ 1;
+  for (int g = 0; g < ngroups; ++g) ctx->groups[g] = groups[g];
+  ctx->ngroups = ngroups;
   ctx->ntiles = (uint32_t)w;
-  ctx->batch_grid = (int)std::min<size_t>((size_t)ctx->num_sms * per_sm, std::max<size_t>(w, 1));
+  ctx->batch_ctas_per_sm = per_sm;
   ctx->batch_comm = add;
   ctx->planned = true;
   return BC_OK;
@@ -449,9 +496,10 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
 
 int bc_relu_batch_run(bc_ctx* ctx) {
   if (!ctx || !ctx->planned) return BC_EINVAL;
-  CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), ctx->stream));
-  CK(bc::launch_relu_batch(ctx->rk, ctx->d_tensors, ctx->d_tiles, ctx->ntiles, ctx->d_counter,
-                           ctx->d_status, ctx->batch_grid, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int) * bc::kMaxBatchGroups, ctx->stream));
+  CK(bc::launch_relu_batch(ctx->d_tensors, ctx->d_tiles, ctx->groups, ctx->ngroups,
+                           ctx->d_counter, ctx->d_status, ctx->num_sms, ctx->batch_ctas_per_sm,
+                           ctx->stream));
   add_comm(&ctx->comm, ctx->batch_comm);
   return BC_OK;
 }

@@ -46,6 +46,23 @@ __device__ __forceinline__ U32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return U32x4{c0, c1, c2, c3};
 }
 
+// Rounds 2..10 of Philox-4x32-10 (round 1 done by the caller).
+__device__ __forceinline__ U32x4 philox_rounds_2_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                    uint32_t c3, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return U32x4{c0, c1, c2, c3};
+}
+
 // Stream tags: which pre-shared seed a draw belongs to, and what it is for.
 // counter = (lo32(elem), tensor_id, block, pair << 24 | purpose << 16 | elem >> 32)
 enum : uint32_t { kPair01 = 0x01, kPair02 = 0x02, kPair12 = 0x12, kPairDealer = 0xDE };
@@ -66,6 +83,33 @@ __device__ __forceinline__ U32x4 draw_block(uint32_t pair, uint32_t purpose, uin
                                             uint64_t elem, uint32_t block, const RoundKeys& rk) {
   return philox((uint32_t)elem, tensor_id, block, stream_tag(pair, purpose, elem), rk);
 }
+
+// Philox blocks of one element with round 1 factored: every block of the
+// element shares c0 = lo32(elem), so M0 * c0 is computed once per element;
+// M1 * c2 (c2 = block index) is a constant or a running sum in the caller.
+struct ElemPhilox {
+  uint32_t e_hi, e_lo;    // M0 * lo32(elem)
+  uint32_t elem_hi16;     // (elem >> 32) & 0xffff
+  uint32_t tensor_id;
+  __device__ __forceinline__ ElemPhilox(uint64_t elem, uint32_t tid) {
+    const uint64_t pe = (uint64_t)kPhiloxM0 * (uint32_t)elem;
+    e_hi = (uint32_t)(pe >> 32);
+    e_lo = (uint32_t)pe;
+    elem_hi16 = (uint32_t)((elem >> 32) & 0xffffu);
+    tensor_id = tid;
+  }
+  // block with M1 * block = mb (64-bit)
+  __device__ __forceinline__ U32x4 block(uint32_t pair, uint32_t purpose, uint64_t mb,
+                                         const RoundKeys& rk) const {
+    const uint32_t tag = (pair << 24) | (purpose << 16) | elem_hi16;
+    return philox_rounds_2_10((uint32_t)(mb >> 32) ^ tensor_id ^ rk.k0[0], (uint32_t)mb,
+                              e_hi ^ tag ^ rk.k1[0], e_lo, rk);
+  }
+  __device__ __forceinline__ U32x4 block_at(uint32_t pair, uint32_t purpose, uint32_t b,
+                                            const RoundKeys& rk) const {
+    return block(pair, purpose, (uint64_t)kPhiloxM1 * b, rk);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Ring Z_{2^l} on lanes.  Lane = uint32_t for l <= 32, uint64_t for l <= 64.

@@ -38,16 +38,18 @@ struct AuditPtrs {
   bool any() const { return w0 || w1 || reply || open0 || open1 || pre_c1 || t || dprime; }
 };
 
-// One tensor of a batched launch, resident in device memory.
+// One tensor of a batched launch, resident in device memory.  The protocol
+// constants are shared by every tensor of a parameter group and travel as a
+// kernel parameter (ReluConsts), not per tensor.
 struct BatchTensor {
   const void* sh0;
   const void* sh1;
   void* o0;
   void* o1;
   uint64_t n;
-  ReluConsts k;        // rk is unused here (taken from the kernel parameter)
+  uint32_t tensor_id;
   int op;              // BC_OP_RELU / BC_OP_DRELU
-  int lane64;          // ring_bits > 32
+  uint64_t elem_offset;  // Philox element index of element 0
 };
 
 struct BatchTile {
@@ -56,14 +58,25 @@ struct BatchTile {
   uint64_t start;      // first element of the tile within its tensor
 };
 
+// A parameter group: tensors with the same (l, lx, c, p) own the tiles
+// [begin, end) of the table and run as one persistent kernel.
+constexpr int kMaxBatchGroups = 32;
+struct BatchGroup {
+  ReluConsts k;        // tensor_id / elem_base unused
+  uint32_t begin, end;
+};
+
 // Host-side launchers (return cudaError_t of the launch).
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
                         cudaStream_t s);
-cudaError_t launch_relu_batch(const RoundKeys& rk, const BatchTensor* tensors,
-                              const BatchTile* tiles, uint32_t ntiles, unsigned int* counter,
-                              int* status, int grid, cudaStream_t s);
-int relu_batch_max_ctas_per_sm();
+// Launches one kernel per non-empty group.  ctas_per_sm >= 0: persistent
+// schedule (0 = occupancy), `counters` holds one zeroed work counter per
+// group.  ctas_per_sm < 0: grid schedule, one CTA per tile of <= kBlock
+// elements (counters unused).
+cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
+                              const BatchGroup* groups, int ngroups, unsigned int* counters,
+                              int* status, int num_sms, int ctas_per_sm, cudaStream_t s);
 
 cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
                          uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,

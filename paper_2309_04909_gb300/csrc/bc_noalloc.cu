@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr size_t kHeaderBytes = 256;   // work counter at 0, status word at 4
+constexpr size_t kHeaderBytes = 256;   // work counters at 0 (one per group), status at 128
 constexpr size_t kTensorBytes =
     ((BC_STATIC_MAX_TENSORS * sizeof(bc::BatchTensor) + 255) / 256) * 256;
 constexpr size_t kTileBytes = ((BC_STATIC_MAX_TILES * sizeof(bc::BatchTile) + 255) / 256) * 256;
@@ -105,8 +105,8 @@ extern "C" int bc_relu_batch_static(uint64_t seed, int device, void* cuda_stream
       g_scratch_addr[device] = static_cast<unsigned char*>(addr);
     }
     unsigned char* base = g_scratch_addr[device];
-    unsigned int* counter = reinterpret_cast<unsigned int*>(base);
-    int* status = reinterpret_cast<int*>(base + 4);
+    unsigned int* counters = reinterpret_cast<unsigned int*>(base);
+    int* status = reinterpret_cast<int*>(base + 4 * bc::kMaxBatchGroups);
     bc::BatchTensor* d_tensors = reinterpret_cast<bc::BatchTensor*>(base + kHeaderBytes);
     bc::BatchTile* d_tiles = reinterpret_cast<bc::BatchTile*>(base + kHeaderBytes + kTensorBytes);
 
@@ -118,27 +118,58 @@ extern "C" int bc_relu_batch_static(uint64_t seed, int device, void* cuda_stream
       k0 += bc::kPhiloxW0;
       k1 += bc::kPhiloxW1;
     }
-    size_t w = 0;
+    // parameter groups of the batch (same l, lx, c, p); tiles of one group
+    // are contiguous in the table
+    int grp[BC_STATIC_MAX_TENSORS];
+    bc::BatchGroup groups[bc::kMaxBatchGroups];
+    int ngroups = 0;
     for (int t = 0; t < count && rc == BC_OK; ++t) {
       const bc_tensor_desc& d = descs[t];
+      bc::ReluConsts k;
+      rc = static_consts(&d.params, 0, &k);
+      if (rc != BC_OK) break;
+      k.rk = rk;
+      int g = 0;
+      while (g < ngroups && !(groups[g].k.ring_bits == k.ring_bits && groups[g].k.lx == k.lx &&
+                              groups[g].k.c == k.c && groups[g].k.mp.p == k.mp.p))
+        ++g;
+      if (g == ngroups) {
+        if (ngroups == bc::kMaxBatchGroups) {
+          rc = BC_ELIMIT;
+          break;
+        }
+        groups[ngroups].k = k;
+        groups[ngroups].begin = groups[ngroups].end = 0;
+        ++ngroups;
+      }
+      grp[t] = g;
       bc::BatchTensor& bt = g_host_tensors[t];
-      rc = static_consts(&d.params, d.tensor_id, &bt.k);
-      bt.k.rk = rk;
       bt.sh0 = d.sh0;
       bt.sh1 = d.sh1;
       bt.o0 = d.o0;
       bt.o1 = d.o1;
       bt.n = d.n;
+      bt.tensor_id = d.tensor_id;
       bt.op = d.op;
-      bt.lane64 = d.params.ring_bits > 32;
-      for (uint64_t s = 0; s < d.n; s += tile) {
-        g_host_tiles[w].tensor = (uint32_t)t;
-        g_host_tiles[w].start = s;
-        g_host_tiles[w].count = (uint32_t)(d.n - s < (uint64_t)tile ? d.n - s : (uint64_t)tile);
-        ++w;
-      }
+      bt.elem_offset = d.elem_offset;
     }
-    if (rc != BC_OK || w == 0) break;
+    if (rc != BC_OK) break;
+    size_t w = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      groups[g].begin = (uint32_t)w;
+      for (int t = 0; t < count; ++t) {
+        if (grp[t] != g) continue;
+        const uint64_t n = descs[t].n;
+        for (uint64_t s = 0; s < n; s += tile) {
+          g_host_tiles[w].tensor = (uint32_t)t;
+          g_host_tiles[w].start = s;
+          g_host_tiles[w].count = (uint32_t)(n - s < (uint64_t)tile ? n - s : (uint64_t)tile);
+          ++w;
+        }
+      }
+      groups[g].end = (uint32_t)w;
+    }
+    if (w == 0) break;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int num_sms = 1;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
@@ -146,14 +177,12 @@ extern "C" int bc_relu_batch_static(uint64_t seed, int device, void* cuda_stream
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_tiles, g_host_tiles, sizeof(bc::BatchTile) * w, cudaMemcpyHostToDevice,
                         s) != cudaSuccess ||
-        cudaMemsetAsync(base, 0, 8, s) != cudaSuccess) {   // counter and status start at 0
+        cudaMemsetAsync(base, 0, kHeaderBytes, s) != cudaSuccess) {   // counters, status = 0
       rc = BC_ECUDA;
       break;
     }
-    const size_t full = (size_t)num_sms * bc::relu_batch_max_ctas_per_sm();
-    const int grid = (int)(w < full ? w : full);
-    if (bc::launch_relu_batch(rk, d_tensors, d_tiles, (uint32_t)w, counter, status, grid, s) !=
-        cudaSuccess)
+    if (bc::launch_relu_batch(d_tensors, d_tiles, groups, ngroups, counters, status, num_sms, 0,
+                              s) != cudaSuccess)
       rc = BC_ECUDA;
   } while (0);
   if (prev != device) cudaSetDevice(prev);

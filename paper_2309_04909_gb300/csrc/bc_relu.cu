@@ -61,18 +61,17 @@ struct Triple {
 };
 
 template <typename Lane>
-__device__ __forceinline__ Triple<Lane> draw_triple(uint32_t purpose, uint32_t tensor_id,
-                                                    uint64_t elem, Lane mask,
-                                                    const RoundKeys& rk) {
+__device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32_t purpose,
+                                                    Lane mask, const RoundKeys& rk) {
   Triple<Lane> T;
-  const U32x4 q0 = draw_block(kPair02, purpose, tensor_id, elem, 0, rk);
-  const U32x4 q1 = draw_block(kPair12, purpose, tensor_id, elem, 0, rk);
+  const U32x4 q0 = ep.block_at(kPair02, purpose, 0, rk);
+  const U32x4 q1 = ep.block_at(kPair12, purpose, 0, rk);
   if (sizeof(Lane) == 4) {
     T.a0 = (Lane)q0.x;
     T.b0 = (Lane)q0.y;
     T.c0 = (Lane)q0.z;
   } else {
-    const U32x4 q2 = draw_block(kPair02, purpose, tensor_id, elem, 1, rk);
+    const U32x4 q2 = ep.block_at(kPair02, purpose, 1, rk);
     T.a0 = block_elem<Lane>(q0, 0);
     T.b0 = block_elem<Lane>(q0, 1);
     T.c0 = block_elem<Lane>(q2, 0);
@@ -83,10 +82,23 @@ __device__ __forceinline__ Triple<Lane> draw_triple(uint32_t purpose, uint32_t t
   return T;
 }
 
+// The 32 window bits starting at bit sh of a lane.  SHORT: sh < 32 is known
+// (c + lx < 32), so a single funnel shift of the two halves suffices.
+template <bool SHORT>
+__device__ __forceinline__ uint32_t window32(uint64_t a, uint32_t sh) {
+  if (SHORT) return __funnelshift_r((uint32_t)a, (uint32_t)(a >> 32), sh);
+  return (uint32_t)(a >> sh);
+}
+template <bool SHORT>
+__device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
+  return a >> sh;
+}
+
 // Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
 // column of the shared-memory shuffle table (stride kBlock words).
-template <typename Lane, int LX, bool RELU, bool AUDIT>
-__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, Lane s1,
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
+__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
+                                                 uint32_t tensor_id, Lane s0, Lane s1,
                                                  uint64_t elem, uint32_t* perm, Lane& out0,
                                                  Lane& out1, const AuditPtrs& aud,
                                                  uint64_t out_idx) {
@@ -96,6 +108,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
   const uint32_t L = lx + 1;
   const Lane mask = (Lane)k.ring_mask;
   const uint32_t p = k.mp.p;
+  const ElemPhilox ep(elem, tensor_id);
 
   // ---- seed01 stream: t (step 1) and the shuffle words (step 6) ----------
 #pragma unroll
@@ -107,7 +120,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
 #pragma unroll
   for (uint32_t b = 0; b < (LX ? (uint32_t)((LX + 4) >> 2) : 8u); ++b) {
     if (!LX && b >= nblk) break;
-    const U32x4 wb = draw_block(kPair01, kPurPerm, k.tensor_id, elem, b, k.rk);
+    const U32x4 wb = ep.block_at(kPair01, kPurPerm, b, rk);
     const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -132,12 +145,13 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
 
   // ---- steps 3-9 over message slots k ----------------------------------------
   uint32_t any_zero = 0;
-#pragma unroll 1
-  for (uint32_t slot = 0; slot < L; ++slot) {
+  uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
+#pragma unroll 2
+  for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     const uint32_t i = perm[slot * kBlock];
     const uint32_t sh = k.c + i;
-    const uint32_t y0 = lo32_shr(f0, sh);
-    const uint32_t y1 = lo32_shr(nf1, sh);
+    const uint32_t y0 = window32<SHORT>(f0, sh);
+    const uint32_t y1 = window32<SHORT>(nf1, sh);
     const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
     // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
     const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
@@ -145,13 +159,13 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
     // step 5: Alg. modswitch
     const uint32_t m0 = v0 ? v0 : k.two_lx;
     const uint32_t m1 = v1 + k.p_minus_2lx;
-    // step 7: r_k in Z_p^*, z_k in Z_p from the slot's seed01 block
-    const U32x4 rz = draw_block(kPair01, kPurMask, k.tensor_id, elem, slot, k.rk);
-    const uint32_t r = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+    // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
+    // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
+    const U32x4 rz = ep.block(kPair01, kPurMask, mb, rk);
+    const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
-    const uint32_t r_mont = mont_mul(r, k.mp.r2, k.mp);   // r 2^32 mod p
-    uint32_t w0 = mont_mul(m0, r_mont, k.mp);              // m0 r mod p
-    uint32_t w1 = mont_mul(m1, r_mont, k.mp);              // m1 r mod p
+    uint32_t w0 = mont_mul(m0, rho, k.mp);
+    uint32_t w1 = mont_mul(m1, rho, k.mp);
     // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
     w0 = M::add(w0, z, p);
     w1 = M::sub(w1, z, p);
@@ -166,7 +180,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
 
   if (!RELU) {
     // step 10: [DReLU']_0 = d0 from seed02 (P0 derives it), [DReLU']_1 to P1
-    const U32x4 rb = draw_block(kPair02, kPurReply, k.tensor_id, elem, 0, k.rk);
+    const U32x4 rb = ep.block_at(kPair02, kPurReply, 0, rk);
     const Lane d0 = block_elem<Lane>(rb, 0) & mask;
     const Lane d1 = ((Lane)dprime - d0) & mask;
     // step 11: [DReLU] = [DReLU' xor t], the public t added by P0
@@ -174,7 +188,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
     out1 = t ? ring_neg(d1, mask) : d1;
     if (AUDIT && aud.reply) store_lane<Lane>(aud.reply, out_idx, d1);
   } else {
-    const Triple<Lane> T = draw_triple<Lane>(kPurReluTriple, k.tensor_id, elem, mask, k.rk);
+    const Triple<Lane> T = draw_triple<Lane>(ep, kPurReluTriple, mask, rk);
     const Lane c1 = (Lane)((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0) & mask;   // P2 -> P1 (pre)
     const Lane e = (Lane)((Lane)dprime - T.b0 - T.b1) & mask;             // P2 -> P0, P1
     const Lane open0 = (Lane)(s0 - T.a0) & mask;                          // P0 -> P1
@@ -197,111 +211,163 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, Lane s0, L
   }
 }
 
-template <typename Lane, int LX, bool RELU, bool AUDIT>
+// One element per thread; the grid covers the tensor once, so the CTA
+// scheduler hands out work as CTAs retire (no static tail).
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
 __global__ void __launch_bounds__(kBlock)
     relu_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
                 uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, const AuditPtrs aud) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
   uint32_t* perm = perm_s + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
-    Lane r0, r1;
-    bicoptor_element<Lane, LX, RELU, AUDIT>(k, sh0[i], sh1[i], k.elem_base + i, perm, r0, r1,
-                                            aud, i);
-    o0[i] = r0;
-    o1[i] = r1;
-  }
+  const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  Lane r0, r1;
+  bicoptor_element<Lane, LX, SHORT, RELU, AUDIT>(k, k.rk, k.tensor_id, sh0[i], sh1[i],
+                                                 k.elem_base + i, perm, r0, r1, aud, i);
+  o0[i] = r0;
+  o1[i] = r1;
 }
 
-template <typename Lane, int LX, bool RELU, bool AUDIT>
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
 cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n, void* o0,
-                     void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
-  auto kern = relu_kernel<Lane, LX, RELU, AUDIT>;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t need = (n + kBlock - 1) / kBlock;
-  const uint64_t full = (uint64_t)num_sms * per_sm;
-  const unsigned grid = (unsigned)(need < full ? need : full);
+                     void* o1, const AuditPtrs& aud, cudaStream_t s) {
+  const uint64_t grid = (n + kBlock - 1) / kBlock;
   if (grid == 0) return cudaSuccess;
-  kern<<<grid, kBlock, 0, s>>>(k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1),
-                               n, static_cast<Lane*>(o0), static_cast<Lane*>(o1), aud);
+  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  relu_kernel<Lane, LX, SHORT, RELU, AUDIT><<<(unsigned)grid, kBlock, 0, s>>>(
+      k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1), n, static_cast<Lane*>(o0),
+      static_cast<Lane*>(o1), aud);
   return cudaGetLastError();
 }
 
 template <typename Lane, bool RELU, bool AUDIT>
 cudaError_t launch_lx(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n,
-                      void* o0, void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
+                      void* o0, void* o1, const AuditPtrs& aud, cudaStream_t s) {
+  const bool shrt = sizeof(Lane) == 8 && k.c + k.lx < 32;
   switch (k.lx) {
-    case 24: return launch_t<Lane, 24, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
-    case 14: return launch_t<Lane, 14, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
-    case 9: return launch_t<Lane, 9, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
-    case 7: return launch_t<Lane, 7, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
-    default: return launch_t<Lane, 0, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 24:
+      return shrt ? launch_t<Lane, 24, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s)
+                  : launch_t<Lane, 24, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+    case 14: return launch_t<Lane, 14, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+    case 9: return launch_t<Lane, 9, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+    case 7:
+      return shrt ? launch_t<Lane, 7, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s)
+                  : launch_t<Lane, 7, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+    default: return launch_t<Lane, 0, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Batched form: one persistent launch over a tile table of many tensors.
-// Each CTA takes the next tile from an atomic counter (no waits), so uneven
-// tensors and mixed rings balance across the SMs.
+// Batched form: one persistent launch per (lane width, key bits) class over
+// that class's range of a tile table of many tensors.  Every warp takes the
+// next tile from the class's atomic counter on its own (no block barrier, no
+// waits), so uneven tensors balance across the SMs down to one tile per warp;
+// per-class kernels keep the register allocation of a single variant.
 // ---------------------------------------------------------------------------
 
-template <typename Lane, int LX, bool RELU>
-__device__ __forceinline__ void run_tile(const BatchTensor& bt, const RoundKeys& rk,
-                                         uint64_t start, uint32_t count, uint32_t* perm) {
-  ReluConsts k = bt.k;
-  k.rk = rk;
+template <typename Lane, int LX, bool SHORT, bool RELU>
+__device__ __forceinline__ void run_tile(const ReluConsts& k, const BatchTensor& bt,
+                                         uint64_t start, uint32_t count, uint32_t lane,
+                                         uint32_t* perm) {
   const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
   const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
   Lane* o0 = static_cast<Lane*>(bt.o0);
   Lane* o1 = static_cast<Lane*>(bt.o1);
   const AuditPtrs none{};
-  for (uint32_t j = threadIdx.x; j < count; j += kBlock) {
+#pragma unroll 1
+  for (uint32_t j = lane; j < count; j += 32) {
     const uint64_t i = start + j;
     Lane r0, r1;
-    bicoptor_element<Lane, LX, RELU, false>(k, sh0[i], sh1[i], i, perm, r0, r1, none, i);
+    bicoptor_element<Lane, LX, SHORT, RELU, false>(k, k.rk, bt.tensor_id, sh0[i], sh1[i],
+                                                   bt.elem_offset + i, perm, r0, r1, none, i);
     o0[i] = r0;
     o1[i] = r1;
   }
 }
 
-template <bool RELU>
-__device__ __forceinline__ void dispatch_tile(const BatchTensor& bt, const RoundKeys& rk,
-                                              uint64_t start, uint32_t count, uint32_t* perm) {
-  if (bt.lane64) {
-    if (bt.k.lx == 24) run_tile<uint64_t, 24, RELU>(bt, rk, start, count, perm);
-    else run_tile<uint64_t, 0, RELU>(bt, rk, start, count, perm);
-  } else {
-    if (bt.k.lx == 14) run_tile<uint32_t, 14, RELU>(bt, rk, start, count, perm);
-    else if (bt.k.lx == 9) run_tile<uint32_t, 9, RELU>(bt, rk, start, count, perm);
-    else run_tile<uint32_t, 0, RELU>(bt, rk, start, count, perm);
+template <typename Lane, int LX, bool SHORT>
+__global__ void __launch_bounds__(kBlock)
+    relu_batch_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
+                      const BatchTile* __restrict__ tiles, uint32_t begin, uint32_t end,
+                      unsigned int* __restrict__ counter, int* __restrict__ status) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = begin + atomicAdd(counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= end) break;
+    const BatchTile tl = tiles[tile];
+    const BatchTensor bt = tensors[tl.tensor];
+    if (tl.start + tl.count > bt.n) {   // a malformed table: record, skip
+      if (lane == 0) atomicExch(status, BC_ECHECK);
+      continue;
+    }
+    if (bt.op == BC_OP_DRELU) run_tile<Lane, LX, SHORT, false>(k, bt, tl.start, tl.count, lane, perm);
+    else run_tile<Lane, LX, SHORT, true>(k, bt, tl.start, tl.count, lane, perm);
   }
 }
 
+// Grid schedule: one CTA per tile of at most kBlock elements, one element per
+// thread, no loop; the hardware CTA scheduler hands out the tiles.
+template <typename Lane, int LX, bool SHORT>
 __global__ void __launch_bounds__(kBlock)
-    relu_batch_kernel(const RoundKeys rk, const BatchTensor* __restrict__ tensors,
-                      const BatchTile* __restrict__ tiles, uint32_t ntiles,
-                      unsigned int* __restrict__ counter, int* __restrict__ status) {
-  __shared__ uint32_t perm_s[kMaxSlots * kBlock];
-  __shared__ uint32_t tile_s;
+    relu_batch_grid_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
+                           const BatchTile* __restrict__ tiles, uint32_t begin,
+                           int* __restrict__ status) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
   uint32_t* perm = perm_s + threadIdx.x;
-  for (;;) {
-    if (threadIdx.x == 0) tile_s = atomicAdd(counter, 1u);
-    __syncthreads();
-    const uint32_t tile = tile_s;
-    __syncthreads();
-    if (tile >= ntiles) break;
-    const BatchTile tl = tiles[tile];
-    const BatchTensor& bt = tensors[tl.tensor];
-    if (tl.start + tl.count > bt.n) {   // a malformed table: record, skip
-      if (threadIdx.x == 0) atomicExch(status, BC_ECHECK);
-      continue;
-    }
-    if (bt.op == BC_OP_DRELU) dispatch_tile<false>(bt, rk, tl.start, tl.count, perm);
-    else dispatch_tile<true>(bt, rk, tl.start, tl.count, perm);
+  const BatchTile tl = tiles[begin + blockIdx.x];
+  const BatchTensor bt = tensors[tl.tensor];
+  if (tl.count > kBlock || tl.start + tl.count > bt.n) {   // a malformed table: record, skip
+    if (threadIdx.x == 0) atomicExch(status, BC_ECHECK);
+    return;
   }
+  if (threadIdx.x >= tl.count) return;
+  const uint64_t i = tl.start + threadIdx.x;
+  const AuditPtrs none{};
+  if (bt.op == BC_OP_DRELU) {
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, SHORT, false, false>(
+        k, k.rk, bt.tensor_id, static_cast<const Lane*>(bt.sh0)[i],
+        static_cast<const Lane*>(bt.sh1)[i], bt.elem_offset + i, perm, r0, r1, none, i);
+    static_cast<Lane*>(bt.o0)[i] = r0;
+    static_cast<Lane*>(bt.o1)[i] = r1;
+  } else {
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, SHORT, true, false>(
+        k, k.rk, bt.tensor_id, static_cast<const Lane*>(bt.sh0)[i],
+        static_cast<const Lane*>(bt.sh1)[i], bt.elem_offset + i, perm, r0, r1, none, i);
+    static_cast<Lane*>(bt.o0)[i] = r0;
+    static_cast<Lane*>(bt.o1)[i] = r1;
+  }
+}
+
+template <typename Lane, int LX, bool SHORT>
+cudaError_t launch_group(const BatchGroup& g, const BatchTensor* tensors, const BatchTile* tiles,
+                         unsigned int* counter, int* status, int num_sms, int ctas_per_sm,
+                         cudaStream_t s) {
+  if (ctas_per_sm < 0) {   // grid schedule
+    const uint32_t ntiles = g.end - g.begin;
+    if (ntiles == 0) return cudaSuccess;
+    relu_batch_grid_kernel<Lane, LX, SHORT><<<ntiles, kBlock, 0, s>>>(g.k, tensors, tiles, g.begin,
+                                                                      status);
+    return cudaGetLastError();
+  }
+  auto kern = relu_batch_kernel<Lane, LX, SHORT>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  const uint64_t warps_needed = g.end - g.begin;             // at most one tile per warp
+  uint64_t grid = (uint64_t)num_sms * per_sm;
+  const uint64_t cap = (warps_needed * 32 + kBlock - 1) / kBlock;
+  if (cap < grid) grid = cap;
+  if (grid == 0) return cudaSuccess;
+  kern<<<(unsigned)grid, kBlock, 0, s>>>(g.k, tensors, tiles, g.begin, g.end, counter, status);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -309,38 +375,49 @@ __global__ void __launch_bounds__(kBlock)
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
                         cudaStream_t s) {
+  (void)num_sms;
   const bool lane64 = k.ring_bits > 32;
   const bool audit = aud.any();
   if (lane64) {
     if (relu) {
-      return audit ? launch_lx<uint64_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
-                   : launch_lx<uint64_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+      return audit ? launch_lx<uint64_t, true, true>(k, sh0, sh1, n, o0, o1, aud, s)
+                   : launch_lx<uint64_t, true, false>(k, sh0, sh1, n, o0, o1, aud, s);
     }
-    return audit ? launch_lx<uint64_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
-                 : launch_lx<uint64_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    return audit ? launch_lx<uint64_t, false, true>(k, sh0, sh1, n, o0, o1, aud, s)
+                 : launch_lx<uint64_t, false, false>(k, sh0, sh1, n, o0, o1, aud, s);
   }
   if (relu) {
-    return audit ? launch_lx<uint32_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
-                 : launch_lx<uint32_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    return audit ? launch_lx<uint32_t, true, true>(k, sh0, sh1, n, o0, o1, aud, s)
+                 : launch_lx<uint32_t, true, false>(k, sh0, sh1, n, o0, o1, aud, s);
   }
-  return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
-               : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+  return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, s)
+               : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, s);
 }
 
-int relu_batch_max_ctas_per_sm() {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relu_batch_kernel, kBlock, 0) !=
-      cudaSuccess)
-    return 1;
-  return per_sm < 1 ? 1 : per_sm;
-}
-
-cudaError_t launch_relu_batch(const RoundKeys& rk, const BatchTensor* tensors,
-                              const BatchTile* tiles, uint32_t ntiles, unsigned int* counter,
-                              int* status, int grid, cudaStream_t s) {
-  if (grid <= 0 || ntiles == 0) return cudaSuccess;
-  relu_batch_kernel<<<grid, kBlock, 0, s>>>(rk, tensors, tiles, ntiles, counter, status);
-  return cudaGetLastError();
+cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
+                              const BatchGroup* groups, int ngroups, unsigned int* counters,
+                              int* status, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const BatchGroup& g = groups[gi];
+    if (g.end <= g.begin) continue;
+    unsigned int* ctr = counters + gi;
+    const bool lane64 = g.k.ring_bits > 32;
+    cudaError_t e;
+    if (lane64) {
+      if (g.k.lx == 24 && g.k.c + g.k.lx < 32)
+        e = launch_group<uint64_t, 24, true>(g, tensors, tiles, ctr, status, num_sms, ctas_per_sm, s);
+      else
+        e = launch_group<uint64_t, 0, false>(g, tensors, tiles, ctr, status, num_sms, ctas_per_sm, s);
+    } else if (g.k.lx == 14) {
+      e = launch_group<uint32_t, 14, false>(g, tensors, tiles, ctr, status, num_sms, ctas_per_sm, s);
+    } else if (g.k.lx == 9) {
+      e = launch_group<uint32_t, 9, false>(g, tensors, tiles, ctr, status, num_sms, ctas_per_sm, s);
+    } else {
+      e = launch_group<uint32_t, 0, false>(g, tensors, tiles, ctr, status, num_sms, ctas_per_sm, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace bc

@@ -1,0 +1,364 @@
+"""Serving loop: continuous batching of private-inference ReLU requests.
+
+Requests (a private-inference activation batch: the ReLU tensors of 1..64
+images of a LeNet- or VGG-16-shaped network, secret-shared in Z_{2^64}) arrive
+over time.  The loop admits a request as soon as it has arrived and its
+output shares fit in the device-memory budget, and every scheduler iteration
+launches ONE batched DReLU/ReLU call (the persistent/grid batch kernel of the
+library) over the next chunks of all admitted requests.  Requests that arrive
+while others are on the GPU join the next iteration, so their work overlaps on
+the device; a finished request frees its memory at once.  Up to `max_inflight`
+iterations are queued on the stream while the host plans the next one.
+
+A request is one flattened tensor keyed by its own tensor id; a chunk carries
+its element offset, so every element gets the randomness it would get alone:
+a request's result is bit-identical alone and in the mix.
+
+Randomness (masks, shuffles, Beaver triples) is derived from the pre-shared
+seeds inside the kernel, so the device-memory budget covers the input and
+output shares only: 32 bytes per element at l = 64.  A request larger than
+the whole budget is rejected.
+"""
+from __future__ import annotations
+
+import bisect
+import collections
+import dataclasses
+import time
+from typing import Callable, Deque, Dict, List, Optional, Sequence, Tuple
+
+
+# ---------------------------------------------------------------------------
+# Device arena: first-fit allocation with coalescing, in bytes (host logic).
+# ---------------------------------------------------------------------------
+
+class Arena:
+    """First-fit allocator over [0, capacity) with 256-byte alignment."""
+
+    ALIGN = 256
+
+    def __init__(self, capacity: int):
+        self.capacity = capacity
+        self._free: List[Tuple[int, int]] = [(0, capacity)]   # sorted (offset, size)
+        self.used = 0
+        self.peak = 0
+
+    def alloc(self, size: int) -> Optional[int]:
+        size = (size + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        for i, (off, sz) in enumerate(self._free):
+            if sz >= size:
+                if sz == size:
+                    self._free.pop(i)
+                else:
+                    self._free[i] = (off + size, sz - size)
+                self.used += size
+                self.peak = max(self.peak, self.used)
+                return off
+        return None
+
+    def free(self, off: int, size: int) -> None:
+        size = (size + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        i = bisect.bisect_left(self._free, (off, 0))
+        self._free.insert(i, (off, size))
+        self.used -= size
+        # coalesce with neighbours
+        if i + 1 < len(self._free) and self._free[i][0] + self._free[i][1] == self._free[i + 1][0]:
+            self._free[i] = (self._free[i][0], self._free[i][1] + self._free[i + 1][1])
+            self._free.pop(i + 1)
+        if i > 0 and self._free[i - 1][0] + self._free[i - 1][1] == self._free[i][0]:
+            self._free[i - 1] = (self._free[i - 1][0], self._free[i - 1][1] + self._free[i][1])
+            self._free.pop(i)
+
+    @property
+    def free_blocks(self) -> int:
+        return len(self._free)
+
+
+# ---------------------------------------------------------------------------
+# Requests and the scheduler
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class ServeRequest:
+    rid: int
+    arrival_s: float
+    elements: int
+    net: str = ""
+    images: int = 0
+    # filled by the engine
+    offset: Optional[int] = None        # arena offset (bytes) of the request's shares
+    rejected: bool = False
+    done: int = 0                       # elements launched so far
+    retired: int = 0                    # elements whose iteration finished
+    admitted_s: Optional[float] = None
+    finished_s: Optional[float] = None
+
+    @property
+    def latency_s(self) -> Optional[float]:
+        if self.finished_s is None:
+            return None
+        return self.finished_s - self.arrival_s
+
+
+@dataclasses.dataclass
+class Chunk:
+    req: ServeRequest
+    start: int          # first element of the chunk within the request
+    count: int
+
+
+class Executor:
+    """What the engine needs from the device: bytes per element of output,
+    launching one iteration, and polling it.  `launch` returns a handle whose
+    `done()` says whether the iteration finished and whose `finish_s()` gives
+    its completion time on the engine clock."""
+
+    bytes_per_element: int = 32      # input + output shares, both parties, l = 64
+
+    def launch(self, chunks: Sequence[Chunk]):
+        raise NotImplementedError
+
+    def now(self) -> float:
+        raise NotImplementedError
+
+    def wait(self, handle) -> None:
+        raise NotImplementedError
+
+    def sleep_until(self, t: float) -> None:
+        raise NotImplementedError
+
+
+@dataclasses.dataclass
+class ServeStats:
+    requests: int
+    completed: int
+    elements: int
+    wall_s: float
+    latencies_s: List[float]
+    iterations: int
+    peak_bytes: int
+    max_waiting: int
+    rejected: int = 0
+
+    def summary(self) -> Dict[str, float]:
+        lat = sorted(self.latencies_s)
+
+        def pct(q):
+            if not lat:
+                return None
+            return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+
+        return {"requests": self.requests, "completed": self.completed,
+                "elements": self.elements, "wall_s": self.wall_s,
+                "elems_per_s": self.elements / self.wall_s if self.wall_s > 0 else 0.0,
+                "p50_ms": None if not lat else 1e3 * pct(0.50),
+                "p99_ms": None if not lat else 1e3 * pct(0.99),
+                "max_ms": None if not lat else 1e3 * lat[-1],
+                "iterations": self.iterations, "peak_bytes": self.peak_bytes,
+                "max_waiting": self.max_waiting, "rejected": self.rejected}
+
+
+class Engine:
+    """Continuous-batching scheduler (host side; the executor runs the GPU)."""
+
+    def __init__(self, executor: Executor, budget_bytes: int, max_iter_elems: int = 1 << 24,
+                 max_inflight: int = 2, min_chunk: int = 1 << 16):
+        self.ex = executor
+        self.arena = Arena(budget_bytes)
+        self.max_iter_elems = max_iter_elems
+        self.max_inflight = max_inflight
+        self.min_chunk = min_chunk
+
+    def _plan_iteration(self, active: List[ServeRequest]) -> List[Chunk]:
+        """Fair share: every admitted request with work left gets an equal
+        quantum of the iteration (small requests finish in their first
+        iteration); what the quantum leaves unused goes to the oldest
+        requests first."""
+        live = [r for r in active if r.elements > r.done]
+        if not live:
+            return []
+        budget = self.max_iter_elems
+        quantum = max(budget // len(live), self.min_chunk)
+        take: Dict[int, int] = {}
+        for r in live:
+            if budget == 0:
+                break
+            t = min(r.elements - r.done, quantum, budget)
+            take[r.rid] = t
+            budget -= t
+        for r in live:
+            if budget == 0:
+                break
+            extra = min(r.elements - r.done - take.get(r.rid, 0), budget)
+            if extra > 0:
+                take[r.rid] = take.get(r.rid, 0) + extra
+                budget -= extra
+        chunks = []
+        for r in live:
+            t = take.get(r.rid, 0)
+            if t:
+                chunks.append(Chunk(r, r.done, t))
+                r.done += t
+        return chunks
+
+    def run(self, requests: Sequence[ServeRequest]) -> ServeStats:
+        pending: Deque[ServeRequest] = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        waiting: Deque[ServeRequest] = collections.deque()
+        active: List[ServeRequest] = []
+        inflight: Deque[Tuple[object, List[Chunk]]] = collections.deque()
+        out_b = self.ex.bytes_per_element
+        iterations, max_waiting, done_elems, rejected = 0, 0, 0, 0
+        t0 = self.ex.now()
+        while pending or waiting or active or inflight:
+            now = self.ex.now() - t0
+            while pending and pending[0].arrival_s <= now:
+                r = pending.popleft()
+                if r.elements * out_b > self.arena.capacity:
+                    r.rejected = True
+                    rejected += 1
+                else:
+                    waiting.append(r)
+            max_waiting = max(max_waiting, len(waiting))
+            # admission: FIFO while the output shares fit in the budget
+            while waiting:
+                r = waiting[0]
+                off = self.arena.alloc(r.elements * out_b)
+                if off is None:
+                    break
+                r.offset, r.admitted_s = off, now
+                active.append(waiting.popleft())
+            # retire finished iterations in order
+            progressed = False
+            while inflight and inflight[0][0].done():
+                handle, chunks = inflight.popleft()
+                fin = handle.finish_s() - t0
+                for c in chunks:
+                    c.req.retired += c.count
+                    done_elems += c.count
+                    if c.req.retired == c.req.elements:
+                        c.req.finished_s = fin
+                        self.arena.free(c.req.offset, c.req.elements * out_b)
+                progressed = True
+            active = [r for r in active if r.retired < r.elements]
+            # launch the next iteration over the admitted requests' next chunks
+            if len(inflight) < self.max_inflight:
+                chunks = self._plan_iteration(active)
+                if chunks:
+                    inflight.append((self.ex.launch(chunks), chunks))
+                    iterations += 1
+                    continue
+            if not progressed:
+                if inflight:
+                    self.ex.wait(inflight[0][0])
+                elif pending and not waiting:
+                    self.ex.sleep_until(t0 + pending[0].arrival_s)
+        wall = self.ex.now() - t0
+        lat = [r.latency_s for r in requests if r.latency_s is not None]
+        return ServeStats(len(requests), len(lat), done_elems, wall, lat, iterations,
+                          self.arena.peak, max_waiting, rejected)
+
+
+# ---------------------------------------------------------------------------
+# Executors
+# ---------------------------------------------------------------------------
+
+class FakeExecutor(Executor):
+    """A simulated device for host-logic tests: an iteration of n elements
+    takes n / rate seconds of simulated time, iterations run back to back."""
+
+    def __init__(self, rate_elems_per_s: float, bytes_per_element: int = 32):
+        self.rate = rate_elems_per_s
+        self.bytes_per_element = bytes_per_element
+        self.t = 0.0
+        self.device_free_at = 0.0
+        self.launched: List[List[Tuple[int, int, int]]] = []
+
+    class _H:
+        def __init__(self, ex, end):
+            self.ex, self.end = ex, end
+
+        def done(self):
+            return self.ex.t >= self.end
+
+        def finish_s(self):
+            return self.end
+
+    def now(self):
+        return self.t
+
+    def launch(self, chunks):
+        n = sum(c.count for c in chunks)
+        start = max(self.t, self.device_free_at)
+        self.device_free_at = start + n / self.rate
+        self.launched.append([(c.req.rid, c.start, c.count) for c in chunks])
+        return FakeExecutor._H(self, self.device_free_at)
+
+    def wait(self, handle):
+        self.t = max(self.t, handle.end)
+
+    def sleep_until(self, t):
+        self.t = max(self.t, t)
+
+
+class GpuExecutor(Executor):
+    """Runs each iteration as one batched ReLU launch through the C-ABI.
+
+    Inputs come from a device-resident pool of input shares; request r's
+    element j reads pool element (pool_base(r) + j).  Its output shares go to
+    out0/out1 at element slot offset // 32 + j: the arena accounts 32 bytes
+    per element (the request's input and output shares), and out0/out1 hold
+    budget / 32 slots each.  Completion times come from CUDA events on the
+    launching stream, measured against an event recorded at construction."""
+
+    def __init__(self, ctx, params, pool0, pool1, arena_tensor0, arena_tensor1,
+                 pool_base: Callable[[ServeRequest], int], tensor_id: Callable[[ServeRequest], int],
+                 schedule: int = 1, tile_elems: int = 0):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        self.prm = params
+        self.pool0, self.pool1 = pool0, pool1
+        self.out0, self.out1 = arena_tensor0, arena_tensor1   # int64 lanes, one per element slot
+        self.pool_base = pool_base
+        self.tensor_id = tensor_id
+        self.schedule = schedule
+        self.tile_elems = tile_elems
+        self.bytes_per_element = 32
+        self.t_host0 = time.perf_counter()
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev0.record()
+
+    class _H:
+        def __init__(self, ex, ev):
+            self.ex, self.ev = ex, ev
+
+        def done(self):
+            return self.ev.query()
+
+        def finish_s(self):
+            return self.ex.ev0.elapsed_time(self.ev) / 1e3
+
+    def now(self):
+        return time.perf_counter() - self.t_host0
+
+    def launch(self, chunks):
+        items = []
+        for c in chunks:
+            base = self.pool_base(c.req) + c.start
+            o = c.req.offset // 32 + c.start      # element slot of the request's outputs
+            items.append((self.prm, self.pool0[base:base + c.count], self.pool1[base:base + c.count],
+                          self.out0[o:o + c.count], self.out1[o:o + c.count],
+                          self.tensor_id(c.req), 0, c.start))
+        self.ctx.relu_batch_plan(items, tile_elems=self.tile_elems, schedule=self.schedule)
+        self.ctx.relu_batch_run()
+        ev = self.torch.cuda.Event(enable_timing=True)
+        ev.record()
+        return GpuExecutor._H(self, ev)
+
+    def wait(self, handle):
+        handle.ev.synchronize()
+
+    def sleep_until(self, t):
+        d = t - self.now()
+        if d > 0:
+            time.sleep(min(d, 0.01))

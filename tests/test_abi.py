@@ -51,3 +51,4 @@ def test_costmodel_counts():
     assert C.philox_blocks(24, 64, True) == 7 + 25 + 3
     assert C.philox_blocks(9, 32, False) == 3 + 10 + 1
     assert C.int_ops_per_element(24, 64) > C.int_ops_per_element(9, 32)
+    assert C.mul_ops_per_element(24, 64) == 35 * 40 + 25 * 16 + 24 + 20

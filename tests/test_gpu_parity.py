@@ -261,11 +261,11 @@ def test_batch_matches_single_calls(ctx):
         items.append((prm, s0, s1, o0, o1, 900 + ti, 1 if op else 0))
         fn = ctx.drelu if op else ctx.relu
         singles.append(fn(prm, s0, s1, tensor_id=900 + ti))
-    for tile in (0, 1000, 4096):
+    for tile, sched, cps in ((0, 0, 0), (1000, 0, 2), (4096, 0, 1), (0, 1, 0)):
         for it in items:
             it[3].fill_(0)
             it[4].fill_(0)
-        ctx.relu_batch_plan(items, tile_elems=tile)
+        ctx.relu_batch_plan(items, tile_elems=tile, ctas_per_sm=cps, schedule=sched)
         ctx.relu_batch_run()
         assert ctx.batch_status() == 0
         for it, (r0, r1) in zip(items, singles):

@@ -1,0 +1,102 @@
+"""Host logic of the serving loop (no GPU): arena allocation and the
+continuous-batching scheduler on a simulated device."""
+import random
+
+import pytest
+
+from paper_2309_04909_gb300.serve import Arena, Engine, FakeExecutor, ServeRequest
+
+
+def test_arena_first_fit_and_coalescing():
+    a = Arena(1 << 20)
+    x = a.alloc(1000)
+    y = a.alloc(5000)
+    z = a.alloc(256)
+    assert x == 0 and y == 1024 and z == 1024 + 5120
+    assert a.alloc(1 << 20) is None
+    a.free(y, 5000)
+    assert a.alloc(4000) == 1024          # first fit reuses the hole
+    a.free(1024, 4000)
+    a.free(x, 1000)
+    a.free(z, 256)
+    assert a.used == 0 and a.free_blocks == 1
+    rng = random.Random(1)
+    live = []
+    for _ in range(2000):
+        if live and rng.random() < 0.45:
+            off, sz = live.pop(rng.randrange(len(live)))
+            a.free(off, sz)
+        else:
+            sz = rng.randrange(1, 20000)
+            off = a.alloc(sz)
+            if off is not None:
+                live.append((off, sz))
+        spans = sorted((o, (s + 255) // 256 * 256) for o, s in live)
+        assert all(s0 + l0 <= s1 for (s0, l0), (s1, _) in zip(spans, spans[1:]))
+        assert a.used <= a.capacity
+    for off, sz in live:
+        a.free(off, sz)
+    assert a.free_blocks == 1 and a.used == 0
+
+
+def _trace(n, rate, seed=0, max_elems=5_000_000):
+    rng = random.Random(seed)
+    t, out = 0.0, []
+    for i in range(n):
+        t += rng.expovariate(rate)
+        out.append(ServeRequest(i, t, rng.randrange(1000, max_elems)))
+    return out
+
+
+def test_engine_completes_every_request_in_budget():
+    reqs = _trace(300, rate=2000.0)
+    ex = FakeExecutor(rate_elems_per_s=8e9)
+    budget = 4 << 30
+    st = Engine(ex, budget, max_iter_elems=1 << 23).run(reqs)
+    assert st.completed == len(reqs) and st.rejected == 0
+    assert st.peak_bytes <= budget
+    assert st.elements == sum(r.elements for r in reqs)
+    for r in reqs:
+        # no result before its own work could have run
+        assert r.finished_s >= r.arrival_s + r.elements / 8e9 - 1e-12
+        assert r.admitted_s >= r.arrival_s
+    # every request's elements were launched exactly once, in order
+    seen = {}
+    for it in ex.launched:
+        for rid, start, count in it:
+            assert seen.get(rid, 0) == start
+            seen[rid] = start + count
+    assert all(seen[r.rid] == r.elements for r in reqs)
+
+
+def test_engine_overlaps_requests_in_one_iteration():
+    """Continuous batching: requests that arrive while others run share the
+    next iteration instead of waiting for the device to drain."""
+    reqs = [ServeRequest(0, 0.0, 4_000_000)] + [ServeRequest(i, 1e-4 * i, 10_000) for i in range(1, 6)]
+    ex = FakeExecutor(rate_elems_per_s=1e9)
+    Engine(ex, 1 << 30, max_iter_elems=1 << 20).run(reqs)
+    mixed = [it for it in ex.launched if len({rid for rid, _, _ in it}) > 1]
+    assert mixed, "no iteration mixed requests"
+    small_done = max(r.finished_s for r in reqs[1:])
+    assert small_done < reqs[0].finished_s     # the small requests did not wait for the big one
+
+
+def test_engine_memory_budget_blocks_and_rejects():
+    reqs = [ServeRequest(i, 0.0, 1_000_000) for i in range(10)] + [ServeRequest(99, 0.0, 10 ** 9)]
+    ex = FakeExecutor(rate_elems_per_s=1e9)
+    budget = 3 * 1_000_000 * 32 + 1000          # three requests at a time
+    st = Engine(ex, budget, max_iter_elems=1 << 22).run(reqs)
+    assert st.rejected == 1 and reqs[-1].rejected
+    assert st.completed == 10
+    assert st.peak_bytes <= budget
+    # admissions were spaced by completions
+    adm = sorted(r.admitted_s for r in reqs[:10])
+    assert adm[3] > 0.0
+
+
+def test_summary_percentiles():
+    reqs = _trace(50, rate=100.0, max_elems=100_000)
+    st = Engine(FakeExecutor(1e9), 1 << 30).run(reqs)
+    s = st.summary()
+    assert s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+    assert s["completed"] == 50
