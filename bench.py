@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu extras")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window of each serving run (60 s in the full trace)")
     return ap.parse_args()
 
 
@@ -179,6 +181,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2309_04909_gb300 import Context, Params, costmodel
+    from paper_2309_04909_gb300.replicas import max_over_ranks, rank_seed
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -190,7 +193,7 @@ def main():
 
     n = args.n
     xi, yi = workload_inputs(n, seed=SEED + rank)   # each rank its own batch (replicas)
-    ctx = Context(0xB1C0_2309_0490_9000 + rank, device=local)
+    ctx = Context(rank_seed(0xB1C0_2309_0490_9000, rank), device=local)
     x0, x1 = ctx.share(RING, torch.from_numpy(xi).to(dev), tensor_id=1)
     y0, y1 = ctx.share(RING, torch.from_numpy(yi).to(dev), tensor_id=2)
     prm = Params(RING, LX, KEY_OFF)
@@ -227,11 +230,7 @@ def main():
     if world > 1:
         dist.barrier()
     ck = clocks.stop() if clocks else None
-    total_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(end), device=dev)
     relu_ms = [e[1].elapsed_time(e[2]) for e in evs]
     pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
     relu_avg = sum(relu_ms) / len(relu_ms)
@@ -276,7 +275,11 @@ def main():
                                     "kind": "oracle",
                                     "sample": f"first {m2} elements of the workload, full step "
                                               f"(share, product, both truncations, ReLU), {dt:.1f} s"}
-        line["batched_vs_plain"] = vgg16_batched_vs_plain(ctx, dev)
+        line["config1"] = config1_check(ctx, dev)
+        line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
+        line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
+        line["serving"] = serving_bench(ctx, dev, bvp["batched_elems_per_s"],
+                                        args.serve_seconds, bvp)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -397,6 +400,131 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "persistent_best_ms": b_persist_ms(ctx, items),
             "status": b.status(), "identical_to_plain": identical}
+
+
+def config1_check(ctx, dev):
+    """Config 1: DReLU of 65,536 uniform reals in [-1000, 1000] (f = 12) in
+    Z_{2^32}, (lx, c) = (9, 14).  Checks every element against the oracle
+    (bit-exact shares) and the reconstructed sign against the plaintext; every
+    mismatch must lie in the predicted set |x| < 2^c or the band around
+    xi* 2^c."""
+    import torch
+    import oracle as O
+    from paper_2309_04909_gb300 import Params, workloads as W
+    n, ring, lx, c = 65536, 32, 9, 14
+    X = W.uniform_reals(n, -1000.0, 1000.0, seed=0)
+    xi = np.rint(np.ldexp(X, 12)).astype(np.int64)
+    s0, s1 = ctx.share(ring, torch.from_numpy(xi).to(dev), tensor_id=100)
+    prm = Params(ring, lx, c)
+    for _ in range(3):
+        o0, o1 = ctx.drelu(prm, s0, s1, tensor_id=101)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(20):
+        o0, o1 = ctx.drelu(prm, s0, s1, tensor_id=101, out=(o0, o1))
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / 20
+    g0 = o0.cpu().numpy().view(np.uint32)
+    g1 = o1.cpu().numpy().view(np.uint32)
+    m = np.uint64(0xFFFFFFFF)
+    e0, e1 = O.share(ring, xi.astype(np.uint64) & m, ctx.seed, 100)
+    r0, r1 = O.drelu(O.params(ring, lx, c), e0, e1, ctx.seed, 101, threads=O.max_threads())
+    parity_mismatch = int((g0 != r0).sum() + (g1 != r1).sum())
+    drelu = (g0.astype(np.uint64) + g1.astype(np.uint64)) & m
+    want = (xi >= 0).astype(np.uint64)
+    bad = np.nonzero(drelu != want)[0]
+    mags = np.abs(xi[bad])
+    xi_star = [v for v in range(1, 1 << lx) if v + (v + 1) // 2 in ((1 << lx) - 1, 1 << lx)]
+    predicted = (mags < (1 << c)) | np.any(
+        [np.abs(mags - e * (1 << c)) < (1 << c) for e in xi_star], axis=0)
+    return {"workload": "65,536 U[-1000,1000] reals, f=12, Z_2^32, (lx, c) = (9, 14), DReLU",
+            "kernel_ms": ms, "elems_per_s": n / (ms / 1e3),
+            "oracle_mismatches": parity_mismatch, "sign_mismatches": int(bad.size),
+            "sign_mismatches_outside_predicted_set": int((~predicted).sum()) if bad.size else 0}
+
+
+def resnet18_batched(ctx, dev, batch=32):
+    """Config-4 shape: ResNet-18 224x224 ReLU set for `batch` images, once at
+    l = 64 (f = 16, lx = 24) and once at l = 32 (f = 12, (lx, c) = (14, 4)),
+    Laplace(0, 2) activations: 1,088 tensors, 147,718,144 elements.  One
+    CUDA-graph-captured batched run (one launch per parameter group) vs one
+    launch per tensor (graph-replayed)."""
+    import torch
+    from paper_2309_04909_gb300 import Params, workloads as W
+    from paper_2309_04909_gb300.batch import ReluBatch, autotune, time_ms
+    ts = W.resnet18_mixed_batch(batch, seed=3)
+    items, plain, keep = [], [], []
+    for ring, frac, prm in ((64, 16, Params(64, 24, 0)), (32, 12, Params(32, 14, 4))):
+        idx = [i for i in range(len(ts.sizes)) if ts.ring_bits[i] == ring]
+        allx = np.concatenate([np.rint(np.ldexp(ts.reals[i], frac)).astype(np.int64) for i in idx])
+        s0, s1 = ctx.share(ring, torch.from_numpy(allx).to(dev), tensor_id=30 + ring)
+        dt = torch.int64 if ring > 32 else torch.int32
+        o0 = torch.empty(allx.size, dtype=dt, device=dev)
+        o1 = torch.empty_like(o0)
+        q0, q1 = torch.empty_like(o0), torch.empty_like(o0)
+        keep += [s0, s1, o0, o1, q0, q1]
+        off = 0
+        for i in idx:
+            sl = slice(off, off + ts.sizes[i])
+            items.append((prm, s0[sl], s1[sl], o0[sl], o1[sl], 40000 + i))
+            plain.append((prm, s0[sl], s1[sl], q0[sl], q1[sl], 40000 + i))
+            off += ts.sizes[i]
+        del allx
+    total = ts.total
+    ts.reals = None
+
+    def run_plain():
+        for it in plain:
+            ctx.relu(it[0], it[1], it[2], it[5], out=(it[3], it[4]))
+
+    run_plain()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run_plain()
+    plain_ms = time_ms(g.replay, reps=3, warmup=1)
+    best = autotune(ctx, items, reps=1, use_cache=False)
+    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"])
+    b.capture()
+    batched_ms = time_ms(b.run, reps=3, warmup=1)
+    identical = all(torch.equal(a[3], p[3]) and torch.equal(a[4], p[4])
+                    for a, p in zip(items, plain))
+    return {"workload": f"ResNet-18 224x224 ReLU set x{batch} at l=64 and l=32: "
+                        f"{len(items)} tensors, {total} elements",
+            "plain_graph_ms": plain_ms, "batched_graph_ms": batched_ms,
+            "speedup_vs_plain_graph": plain_ms / batched_ms,
+            "batched_elems_per_s": total / (batched_ms / 1e3),
+            "schedule": "grid" if best["schedule"] == 1 else "persistent",
+            "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+            "status": b.status(), "identical_to_plain": bool(identical)}
+
+
+def serving_bench(ctx, dev, capacity, seconds, bvp, budget=40 << 30):
+    """Continuous-batching serving: Poisson arrivals of 1-64-image LeNet /
+    VGG-16 ReLU requests (50/50), l = 64, under a 40 GB admission budget.
+    Runs the offered 2,000 req/s and 50 % / 90 % of the measured batched
+    capacity, each for `seconds` of arrivals; reports p50/p99 latency."""
+    from paper_2309_04909_gb300 import Params, workloads as W
+    from paper_2309_04909_gb300.serve import Engine, ServingSetup
+    prm = Params(64, 24, 0)
+    setup = ServingSetup(ctx, prm, budget, seed=4, pool_images=64)
+    mean_elems = 0.5 * 32.5 * (setup.per_image["vgg16"] + setup.per_image["lenet"])
+    sched = 1 if bvp.get("schedule") == "grid" else 0
+    out = {"budget_bytes": budget, "arrival_window_s": seconds,
+           "mean_elems_per_request": mean_elems, "capacity_elems_per_s": capacity}
+    for label, rate in (("offered_2000_rps", 2000.0),
+                        ("load_90pct", 0.9 * capacity / mean_elems),
+                        ("load_50pct", 0.5 * capacity / mean_elems)):
+        trace = W.serving_trace(rate, seconds, seed=4)
+        reqs = setup.requests_from_trace(trace)
+        st = Engine(setup.executor(schedule=sched), budget, max_iter_elems=1 << 24).run(reqs)
+        s = st.summary()
+        s["rate_rps"] = rate
+        s["offered_elems_per_s"] = rate * mean_elems
+        out[label] = s
+    return out
 
 
 if __name__ == "__main__":

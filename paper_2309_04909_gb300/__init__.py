@@ -228,6 +228,14 @@ class Context:
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_plan(self._h, arr, len(items), ctypes.byref(cfg)))
 
+    def relu_batch_plan_descs(self, descs, count: int, tile_elems: int = 0, ctas_per_sm: int = 0,
+                              schedule: int = 0):
+        """Plan from a prepared ctypes array of TensorDesc (raw device
+        pointers; the caller keeps the memory alive)."""
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule)
+        self._sync_stream()
+        self._check(self._lib.bc_relu_batch_plan(self._h, descs, count, ctypes.byref(cfg)))
+
     def relu_batch_run(self):
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_run(self._h))

@@ -162,19 +162,20 @@ class Engine:
     """Continuous-batching scheduler (host side; the executor runs the GPU)."""
 
     def __init__(self, executor: Executor, budget_bytes: int, max_iter_elems: int = 1 << 24,
-                 max_inflight: int = 2, min_chunk: int = 1 << 16):
+                 max_inflight: int = 2, min_chunk: int = 1 << 16, max_share: int = 32):
         self.ex = executor
         self.arena = Arena(budget_bytes)
         self.max_iter_elems = max_iter_elems
         self.max_inflight = max_inflight
         self.min_chunk = min_chunk
+        self.max_share = max_share
 
     def _plan_iteration(self, active: List[ServeRequest]) -> List[Chunk]:
-        """Fair share: every admitted request with work left gets an equal
-        quantum of the iteration (small requests finish in their first
-        iteration); what the quantum leaves unused goes to the oldest
-        requests first."""
-        live = [r for r in active if r.elements > r.done]
+        """Fair share among the `max_share` oldest admitted requests with work
+        left: each gets an equal quantum of the iteration (small requests
+        finish in their first iteration); what the quanta leave unused goes
+        to the oldest requests first."""
+        live = [r for r in active if r.elements > r.done][:self.max_share]
         if not live:
             return []
         budget = self.max_iter_elems
@@ -201,7 +202,11 @@ class Engine:
                 r.done += t
         return chunks
 
-    def run(self, requests: Sequence[ServeRequest]) -> ServeStats:
+    def run(self, requests: Sequence[ServeRequest],
+            on_complete: Optional[Callable[[ServeRequest], None]] = None) -> ServeStats:
+        """Serve `requests` to completion.  `on_complete(req)` runs when a
+        request's last iteration has finished, before its memory is freed
+        (work it queues on the stream is ordered before any reuse)."""
         pending: Deque[ServeRequest] = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
         waiting: Deque[ServeRequest] = collections.deque()
         active: List[ServeRequest] = []
@@ -237,6 +242,8 @@ class Engine:
                     done_elems += c.count
                     if c.req.retired == c.req.elements:
                         c.req.finished_s = fin
+                        if on_complete is not None:
+                            on_complete(c.req)
                         self.arena.free(c.req.offset, c.req.elements * out_b)
                 progressed = True
             active = [r for r in active if r.retired < r.elements]
@@ -323,7 +330,10 @@ class GpuExecutor(Executor):
         self.tensor_id = tensor_id
         self.schedule = schedule
         self.tile_elems = tile_elems
+        self.prm_c = params.c_struct()
         self.bytes_per_element = 32
+        if params.ring_bits <= 32:
+            raise ValueError("the serving pool holds 64-bit lanes (l > 32)")
         self.t_host0 = time.perf_counter()
         self.ev0 = torch.cuda.Event(enable_timing=True)
         self.ev0.record()
@@ -342,14 +352,19 @@ class GpuExecutor(Executor):
         return time.perf_counter() - self.t_host0
 
     def launch(self, chunks):
-        items = []
-        for c in chunks:
-            base = self.pool_base(c.req) + c.start
-            o = c.req.offset // 32 + c.start      # element slot of the request's outputs
-            items.append((self.prm, self.pool0[base:base + c.count], self.pool1[base:base + c.count],
-                          self.out0[o:o + c.count], self.out1[o:o + c.count],
-                          self.tensor_id(c.req), 0, c.start))
-        self.ctx.relu_batch_plan(items, tile_elems=self.tile_elems, schedule=self.schedule)
+        from ._native import TensorDesc
+        n = len(chunks)
+        arr = (TensorDesc * n)()
+        p0, p1 = self.pool0.data_ptr(), self.pool1.data_ptr()
+        q0, q1 = self.out0.data_ptr(), self.out1.data_ptr()
+        prm = self.prm_c
+        for j, c in enumerate(chunks):
+            ib = 8 * (self.pool_base(c.req) + c.start)
+            ob = 8 * (c.req.offset // 32 + c.start)
+            arr[j] = TensorDesc(p0 + ib, p1 + ib, q0 + ob, q1 + ob, c.count,
+                                self.tensor_id(c.req), 0, prm, c.start)
+        self.ctx.relu_batch_plan_descs(arr, n, tile_elems=self.tile_elems,
+                                       schedule=self.schedule)
         self.ctx.relu_batch_run()
         ev = self.torch.cuda.Event(enable_timing=True)
         ev.record()
@@ -362,3 +377,66 @@ class GpuExecutor(Executor):
         d = t - self.now()
         if d > 0:
             time.sleep(min(d, 0.01))
+
+
+# ---------------------------------------------------------------------------
+# GPU set-up for the LeNet / VGG-16 serving workload
+# ---------------------------------------------------------------------------
+
+class ServingSetup:
+    """Device-resident input pool and output arena for serving runs.
+
+    The pool holds the secret-shared activations of `pool_images` seeded
+    images of each network (VGG-16 32x32 and LeNet 28x28 ReLU sets), laid out
+    image-major, so a request of k images reads the pool prefix of k images
+    of its network.  The arena holds budget / 32 element slots per output
+    share array."""
+
+    def __init__(self, ctx, params, budget_bytes: int, seed: int, pool_images: int = 64,
+                 frac_bits: int = 16, tensor_id_base: int = 0x40000000):
+        import numpy as np
+        import torch
+
+        from . import workloads as W
+        self.ctx = ctx
+        self.prm = params
+        self.budget = budget_bytes
+        self.per_image = {"vgg16": sum(W.VGG16_32_LAYERS), "lenet": sum(W.LENET_28_LAYERS)}
+        parts, self.base = [], {}
+        off = 0
+        for net, layers in (("vgg16", W.VGG16_32_LAYERS), ("lenet", W.LENET_28_LAYERS)):
+            self.base[net] = off
+            g = np.random.Generator(np.random.PCG64([seed, 11, len(parts)]))
+            sig = g.uniform(0.5, 8.0, size=len(layers))
+            for _ in range(pool_images):
+                for li, sz in enumerate(layers):
+                    parts.append(np.rint(np.ldexp(g.normal(0.0, sig[li], size=sz), frac_bits))
+                                 .astype(np.int64))
+            off += pool_images * self.per_image[net]
+        allx = torch.from_numpy(np.concatenate(parts)).to(ctx.device)
+        self.pool0, self.pool1 = ctx.share(params.ring_bits, allx, tensor_id=0x3FFFFFFF)
+        slots = budget_bytes // 32
+        self.out0 = torch.empty(slots, dtype=torch.int64, device=ctx.device)
+        self.out1 = torch.empty(slots, dtype=torch.int64, device=ctx.device)
+        self.tid_base = tensor_id_base
+        torch.cuda.synchronize()
+
+    def requests_from_trace(self, trace) -> List[ServeRequest]:
+        return [ServeRequest(r.rid, r.arrival_s, r.images * self.per_image[r.net], r.net, r.images)
+                for r in trace]
+
+    def tensor_id(self, r: ServeRequest) -> int:
+        return self.tid_base + r.rid
+
+    def executor(self, schedule: int = 1, tile_elems: int = 0) -> GpuExecutor:
+        return GpuExecutor(self.ctx, self.prm, self.pool0, self.pool1, self.out0, self.out1,
+                           pool_base=lambda r: self.base[r.net], tensor_id=self.tensor_id,
+                           schedule=schedule, tile_elems=tile_elems)
+
+    def outputs(self, r: ServeRequest):
+        o = r.offset // 32
+        return self.out0[o:o + r.elements], self.out1[o:o + r.elements]
+
+    def inputs(self, r: ServeRequest):
+        b = self.base[r.net]
+        return self.pool0[b:b + r.elements], self.pool1[b:b + r.elements]
