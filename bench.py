@@ -300,9 +300,18 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, dev):
     out = {k: torch.empty(n, dtype=torch.int64).pin_memory() for k in ("relu0", "relu1")}
     out["det0"] = torch.empty(n, dtype=torch.int64).pin_memory()
     out["det1"] = torch.empty(n, dtype=torch.int64).pin_memory()
-    ctx.reserve(1 << 20)
-    for _ in range(3):
-        ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+    best = None
+    for chunk_log2 in (18, 19, 20):         # pick the staging chunk, then time
+        ctx.reserve(1 << chunk_log2)
+        for _ in range(2):
+            ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+        dt = time.perf_counter() - t0
+        if best is None or dt < best[1]:
+            best = (chunk_log2, dt)
+    ctx.reserve(1 << best[0])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -310,7 +319,8 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, dev):
     dt = time.perf_counter() - t0
     return {"value": n * steps / dt, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
             "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
-            "api": "bc_linear_relu_host (chunks of 2^20, two streams)"}
+            "api": f"bc_linear_relu_host (pinned host buffers, chunks of 2^{best[0]}, "
+                   f"three streams)"}
 
 
 def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):

@@ -248,13 +248,14 @@ typedef struct {
 int bc_linear_relu(bc_ctx *ctx, const bc_linear_relu_args *a);
 /* Same with HOST pointers for x0,x1,y0,y1 (input) and relu0,relu1,det0,det1
  * (output); prod/trc fields are ignored.  Staged through device buffers
- * reserved by bc_reserve(ctx, chunk) in chunks of at most `chunk` elements,
- * copies overlapped with compute on two streams.  Returns after the results
- * are in host memory. */
+ * reserved by bc_reserve in chunks of its `chunk` elements, three chunks in
+ * flight on three streams so that host-to-device copies, kernels and
+ * device-to-host copies of different chunks overlap (pinned host memory
+ * needed for the overlap).  Returns after the results are in host memory. */
 int bc_linear_relu_host(bc_ctx *ctx, const bc_linear_relu_args *a);
-/* Reserve device staging for bc_linear_relu_host of chunks up to
- * `max_chunk` elements at ring_bits <= 64. */
-int bc_reserve(bc_ctx *ctx, size_t max_chunk);
+/* Set the chunk of bc_linear_relu_host to `chunk` elements, growing the
+ * device staging (3 sets of 12 arrays of `chunk` 64-bit lanes) if needed. */
+int bc_reserve(bc_ctx *ctx, size_t chunk);
 
 /* ---- truncation-failure statistics (evaluation only) --------------------- */
 

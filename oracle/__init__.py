@@ -17,8 +17,12 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "bicoptor_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# BICOPTOR_ORACLE_SRC points the oracle at another copy of its source (the
+# mutation tests build planted-mistake copies this way); the library of such a
+# copy is built beside it, never over the real one.
+_SRC = os.environ.get("BICOPTOR_ORACLE_SRC") or os.path.join(_HERE, "bicoptor_oracle.c")
+_LIB_PATH = (os.path.join(os.path.dirname(os.path.abspath(_SRC)), "_build", "liboracle.so")
+             if os.environ.get("BICOPTOR_ORACLE_SRC") else os.path.join(_HERE, "_build", "liboracle.so"))
 _lock = threading.Lock()
 _lib = None
 

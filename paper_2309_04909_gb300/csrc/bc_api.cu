@@ -13,7 +13,7 @@
 struct bc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaStream_t aux = nullptr;          // second stream of the host-staging pipeline
+  cudaStream_t aux[2] = {nullptr, nullptr};   // more streams of the host-staging pipeline
   uint64_t seed = 0;
   bc::RoundKeys rk{};
   int num_sms = 1;
@@ -43,9 +43,10 @@ struct bc_ctx {
   int ngroups = 0;
   bc_comm batch_comm{};                   // what one run of the plan adds
   bool planned = false;
-  // host staging for bc_linear_relu_host: two sets of chunk buffers
-  size_t stage_cap = 0;
-  void* stage[2] = {nullptr, nullptr};
+  // host staging for bc_linear_relu_host: one set of chunk buffers per stream
+  size_t stage_cap = 0;       // allocated elements per array
+  size_t stage_chunk = 0;     // elements per chunk (<= stage_cap)
+  void* stage[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev_start = nullptr;
 };
 
@@ -222,7 +223,8 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int) * bc::kMaxBatchGroups);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
@@ -242,9 +244,11 @@ int bc_destroy(bc_ctx* ctx) {
   if (!ctx) return BC_EINVAL;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  if (ctx->aux) {
-    cudaStreamSynchronize(ctx->aux);
-    cudaStreamDestroy(ctx->aux);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->aux[i]) {
+      cudaStreamSynchronize(ctx->aux[i]);
+      cudaStreamDestroy(ctx->aux[i]);
+    }
   }
   cudaFree(ctx->d_tensors);
   cudaFree(ctx->d_tiles);
@@ -255,8 +259,7 @@ int bc_destroy(bc_ctx* ctx) {
   }
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_status);
-  cudaFree(ctx->stage[0]);
-  cudaFree(ctx->stage[1]);
+  for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   delete ctx;
   return BC_OK;
@@ -562,22 +565,24 @@ int bc_linear_relu(bc_ctx* ctx, const bc_linear_relu_args* a) {
 
 int bc_reserve(bc_ctx* ctx, size_t max_chunk) {
   if (!ctx || max_chunk == 0) return BC_EINVAL;
-  if (max_chunk <= ctx->stage_cap) return BC_OK;
-  CK(cudaStreamSynchronize(ctx->stream));
-  CK(cudaStreamSynchronize(ctx->aux));
-  for (int i = 0; i < 2; ++i) {
-    cudaFree(ctx->stage[i]);
-    ctx->stage[i] = nullptr;
-  }
-  ctx->stage_cap = 0;
-  const size_t per = ((max_chunk * 8 + 255) / 256) * 256;   // one 64-bit array, 256 B aligned
-  for (int i = 0; i < 2; ++i) {
-    if (cudaMalloc(&ctx->stage[i], per * 12) != cudaSuccess) {
-      cudaGetLastError();
-      return BC_ENOMEM;
+  if (max_chunk > ctx->stage_cap) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
+    for (int i = 0; i < 3; ++i) {
+      cudaFree(ctx->stage[i]);
+      ctx->stage[i] = nullptr;
     }
+    ctx->stage_cap = ctx->stage_chunk = 0;
+    const size_t per = ((max_chunk * 8 + 255) / 256) * 256;   // one 64-bit array, 256 B aligned
+    for (int i = 0; i < 3; ++i) {
+      if (cudaMalloc(&ctx->stage[i], per * 12) != cudaSuccess) {
+        cudaGetLastError();
+        return BC_ENOMEM;
+      }
+    }
+    ctx->stage_cap = max_chunk;
   }
-  ctx->stage_cap = max_chunk;
+  ctx->stage_chunk = max_chunk;
   return BC_OK;
 }
 
@@ -586,15 +591,16 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   int rc = check_linear(a);
   if (rc) return rc;
   if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->relu0 || !a->relu1)) return BC_EINVAL;
-  if (a->n && ctx->stage_cap == 0) return BC_EINVAL;
+  if (a->n && ctx->stage_chunk == 0) return BC_EINVAL;
   const size_t lb = lane_bytes(a->ring_bits);
   const size_t db = lane_bytes(a->ring_bits - a->trunc_bits);
   const size_t per = ((ctx->stage_cap * 8 + 255) / 256) * 256;
-  const size_t chunk = ctx->stage_cap;
-  cudaStream_t st[2] = {ctx->stream, ctx->aux};
-  // the aux stream starts after everything queued on the context stream
+  const size_t chunk = ctx->stage_chunk;
+  cudaStream_t st[3] = {ctx->stream, ctx->aux[0], ctx->aux[1]};
+  // the other streams start after everything queued on the context stream
   CK(cudaEventRecord(ctx->ev_start, ctx->stream));
-  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
+  CK(cudaStreamWaitEvent(ctx->aux[0], ctx->ev_start, 0));
+  CK(cudaStreamWaitEvent(ctx->aux[1], ctx->ev_start, 0));
   const char* hx0 = static_cast<const char*>(a->x0);
   const char* hx1 = static_cast<const char*>(a->x1);
   const char* hy0 = static_cast<const char*>(a->y0);
@@ -603,11 +609,14 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   char* hr1 = static_cast<char*>(a->relu1);
   char* hd0 = static_cast<char*>(a->det0);
   char* hd1 = static_cast<char*>(a->det1);
+  // chunk j runs on stream j % 3 with stage set j % 3: copies in, compute,
+  // copies out; three chunks in flight let the two copy directions and the
+  // kernels of different chunks overlap
   size_t j = 0;
   for (size_t off = 0; off < a->n; off += chunk, ++j) {
     const size_t m = std::min(chunk, a->n - off);
-    cudaStream_t s = st[j & 1];
-    char* base = static_cast<char*>(ctx->stage[j & 1]);
+    cudaStream_t s = st[j % 3];
+    char* base = static_cast<char*>(ctx->stage[j % 3]);
     void* b[12];
     for (int q = 0; q < 12; ++q) b[q] = base + per * q;
     CK(cudaMemcpyAsync(b[0], hx0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
@@ -625,7 +634,7 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
       CK(cudaMemcpyAsync(hd1 + off * db, b[9], m * db, cudaMemcpyDeviceToHost, s));
     }
   }
-  CK(cudaStreamSynchronize(ctx->aux));
+  for (int i = 0; i < 2; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
   CK(cudaStreamSynchronize(ctx->stream));
   add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
   add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));

@@ -1,0 +1,58 @@
+"""The oracle's pins are sensitive: a plausible mistake planted anywhere in a
+copy of the oracle (a dropped term, a wrong sign or index, a swapped
+operand, a wrong constant) makes the pin suite fail.  Each mutant is a text
+substitution in oracle/bicoptor_oracle.c, built into a temporary directory
+and run against tests/test_oracle_pins.py in a subprocess."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "bicoptor_oracle.c")
+
+MUTANTS = {
+    "cut_keeps_weights": ("out |= bit << (i - k1);", "out |= bit << i;"),
+    "p1_trunc_no_negation": ("return rneg(orc_cut(a, ell, k1, k2), ell - k1 - k2);",
+                             "return rmod(orc_cut(a, ell, k1, k2), ell - k1 - k2);"),
+    "newtrc2_k1_k2_swapped": ("return rmod(orc_cut(s0, ell, k1, k2), ell - k1 - k2);",
+                              "return rmod(orc_cut(s0, ell, k2, k1), ell - k1 - k2);"),
+    "step4_dropped_minus_one": ("v0[i] = rmod(u0[i] + u0[i + 1] - 1, lx);",
+                                "v0[i] = rmod(u0[i] + u0[i + 1], lx);"),
+    "step4_wrong_neighbour": ("v1[i] = rmod(u1[i] + u1[i + 1], lx);",
+                              "v1[i] = rmod(u1[i] + u1[i], lx);"),
+    "modswitch_p1_dropped_term": ("return (uint32_t)(((uint64_t)p + b - pow2) % p);",
+                                  "return (uint32_t)(((uint64_t)p + b) % p);"),
+    "reshare_wrong_sign": ("msg1[k] = (uint32_t)(((uint64_t)sh1[k] + p - z[k]) % p);",
+                           "msg1[k] = (uint32_t)(((uint64_t)sh1[k] + z[k]) % p);"),
+    "flip_inverted": ("if (t) { s0 = rneg(s0, ell); s1 = rneg(s1, ell); }",
+                      "if (!t) { s0 = rneg(s0, ell); s1 = rneg(s1, ell); }"),
+    "shuffle_off_by_one": ("int partner = (int)(((uint64_t)W * (uint64_t)(j + 1)) >> 32);",
+                           "int partner = (int)(((uint64_t)W * (uint64_t)j) >> 32);"),
+    "beaver_dropped_de": ("o0[i] = rmod(d * e + d * T.b0 + e * T.a0 + T.c0, ell);",
+                          "o0[i] = rmod(d * T.b0 + e * T.a0 + T.c0, ell);"),
+    "relu_unflip_dropped_t_x": ("o0[i] = rmod((uint64_t)t * s0[i] + one_m2t * xd0, ell);",
+                                "o0[i] = rmod(one_m2t * xd0, ell);"),
+    "philox_wrong_multiplier": ("#define PHILOX_M0 0xD2511F53u", "#define PHILOX_M0 0xD2511F55u"),
+    "philox_key_bump_order": ("if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }",
+                              "{ k0 += PHILOX_W0; k1 += PHILOX_W1; }"),
+    "share_sign": ("*s1 = rneg(r, ell);", "*s1 = rmod(r, ell);"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutant {name} no longer matches the oracle source"
+    mutant = tmp_path / "bicoptor_oracle.c"
+    mutant.write_text(src.replace(old, new))
+    env = dict(os.environ, BICOPTOR_ORACLE_SRC=str(mutant), PYTHONPATH=ROOT)
+    proc = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(HERE, "test_oracle_pins.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert proc.returncode != 0, f"no pin caught mutant {name}:\n{proc.stdout[-1500:]}"
+    assert "failed" in proc.stdout or "error" in proc.stdout.lower()

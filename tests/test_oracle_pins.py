@@ -294,6 +294,41 @@ def test_drelu_exception_l64():
     assert (O.reconstruct(64, o0, o1) == (xs >= 0)).all()
 
 
+def test_shuffle_moves_the_zero_uniformly():
+    """Alg. drelu step 6: the shuffle is a uniform permutation, so the
+    message slot k* that carries the zero of v (elements with exactly one
+    zero) is uniform over the lx+1 slots, and k* equals the zero's source
+    index i* (a fixed point) with probability 1/(lx+1).  i* comes from the
+    closed form of Thm. newtrc2, k* from P2's view of the messages."""
+    ell, lx, c = 16, 5, 0
+    P = O.params(ell, lx, c)
+    L, m, mx = lx + 1, (1 << ell) - 1, (1 << lx) - 1
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(60000, lx, seed=12)
+    s0, s1 = O.share(ell, xs.astype(np.uint64) & np.uint64(m), seed=8, tid=1)
+    o0, o1, aud = O.drelu(P, s0, s1, seed=9, tid=2, audit=True)
+    t = aud["t"].astype(object)
+    fs0 = np.array([(-int(a) if tt else int(a)) & m for a, tt in zip(s0, t)], dtype=object)
+    fs1 = np.array([(-int(b) if tt else int(b)) & m for b, tt in zip(s1, t)], dtype=object)
+    xp = (fs0 + fs1) & m
+    Rp = (-fs1) & m
+    u = [((xp >> i) + (((xp % (1 << i)) + (Rp % (1 << i))) >= (1 << i)).astype(object)) & mx
+         for i in range(L)]
+    zero = np.stack([((u[i] + (u[i + 1] if i < lx else 0) - 1) & mx) == 0 for i in range(L)], 1)
+    w = (aud["w0"].astype(np.uint64) + aud["w1"].astype(np.uint64)) % np.uint64(P.p)
+    one = zero.sum(1) == 1
+    i_star = zero[one].argmax(1)
+    k_star = (w[one] == 0).argmax(1)
+    n1 = int(one.sum())
+    assert n1 > 20000
+    assert ((w[one] == 0).sum(1) == 1).all()
+    fixed = (i_star == k_star).mean()
+    assert abs(fixed - 1 / L) < 5 * math.sqrt((1 / L) * (1 - 1 / L) / n1)
+    hist = np.bincount(k_star, minlength=L)
+    chi2 = (((hist - n1 / L) ** 2) / (n1 / L)).sum()
+    assert chi2 < 30          # 5 dof; p ~ 2e-5
+
+
 def test_relu_beaver_identity():
     """Alg. relu: reconstruct(ReLU shares) = x * (DReLU' xor t) mod 2^l
     exactly (Beaver identity), and equals max(x, 0) on in-domain inputs."""
