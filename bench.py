@@ -269,12 +269,14 @@ def main():
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), dev)
         line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
+        line["linear_layer_truncation"] = linear_trunc_table(ctx, dev)
         if world == 1:
             rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
             line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
                                     "kind": "oracle",
                                     "sample": f"first {m2} elements of the workload, full step "
                                               f"(share, product, both truncations, ReLU), {dt:.1f} s"}
+        line["party_separated"] = parties_bench(ctx, prm, buf, n, relu_avg)
         line["config1"] = config1_check(ctx, dev)
         line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
         line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
@@ -320,7 +322,7 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, dev):
     return {"value": n * steps / dt, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
             "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
             "api": f"bc_linear_relu_host (pinned host buffers, chunks of 2^{best[0]}, "
-                   f"three streams)"}
+                   f"four streams)"}
 
 
 def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):
@@ -410,6 +412,67 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "persistent_best_ms": b_persist_ms(ctx, items),
             "status": b.status(), "identical_to_plain": identical}
+
+
+def linear_trunc_table(ctx, dev, n=1 << 22):
+    """Sec. 4 on synthetic products: x, y ~ N(0, 4^2) with f fractional bits
+    in Z_{2^64} (5 integer bits), their product truncated by f:
+      mult-then-trc, ABY3, random r     (e1 expected: sum |x y| / 2^64)
+      mult-then-trc, ABY3, r = 2^f fixed (the shortcut that hides e1)
+      mult-then-trc, SecureML
+      trc-then-mult (Alg. linear)        (inputs truncated by f/2 first)
+    Failures counted against floor(x y / 2^f) (more than one away)."""
+    import torch
+    from paper_2309_04909_gb300 import workloads as W
+    out = {}
+    for f in (13, 20, 26):
+        X = W.gaussian_reals(n, 4.0, seed=40 + f, stream=0)
+        Y = W.gaussian_reals(n, 4.0, seed=40 + f, stream=1)
+        xi = np.rint(np.ldexp(X, f)).astype(np.int64)
+        yi = np.rint(np.ldexp(Y, f)).astype(np.int64)
+        prod = xi * yi                      # |x y| < 2^62 for these inputs: exact in int64
+        x0, x1 = ctx.share(64, torch.from_numpy(xi).to(dev), tensor_id=500 + f)
+        y0, y1 = ctx.share(64, torch.from_numpy(yi).to(dev), tensor_id=600 + f)
+        p0, p1 = ctx.mul_beaver(64, x0, x1, y0, y1, tensor_id=700 + f)
+        pg = torch.from_numpy(prod).to(dev)
+        row = {"expected_e1_random_r": float(np.abs(prod.astype(np.float64)).sum() / 2.0 ** 64)}
+        a0, a1 = ctx.trunc_aby3(64, f, p0, p1, tensor_id=800 + f)
+        row["mult_then_trc_aby3_random_r"] = ctx.count_trunc_failures(64, f, pg, a0, a1)
+        a0, a1 = ctx.trunc_aby3(64, f, p0, p1, tensor_id=800 + f, fixed_r=1 << f)
+        row["mult_then_trc_aby3_fixed_r"] = ctx.count_trunc_failures(64, f, pg, a0, a1)
+        s0, s1 = ctx.trunc_prob(64, f, p0, p1)
+        row["mult_then_trc_secureml"] = ctx.count_trunc_failures(64, f, pg, s0, s1)
+        t0, t1 = ctx.trunc_then_mul(64, f // 2, f - f // 2, x0, x1, y0, y1, tensor_id=900 + f)
+        # trc-then-mult loses up to (|x| + |y|) / 2^(f/2) + 1 by design; count e1-scale misses
+        rec = (t0.view(torch.int64) + t1.view(torch.int64)) - (pg >> f)
+        row["trc_then_mult_e1_scale_errors"] = int((rec.abs() > (1 << 20)).sum().item())
+        out[f"f={f}"] = row
+    return out
+
+
+def parties_bench(ctx, prm, buf, n, fused_ms):
+    """The same ReLU with each party's work in its own kernel and every
+    message in a device buffer (bit-packed w at lx+1 bits per value): the
+    communication path the fused kernel keeps in registers."""
+    import torch
+    msgs = ctx.party_buffers(prm, n)
+    out = (torch.empty_like(buf["relu0"]), torch.empty_like(buf["relu1"]))
+    for _ in range(3):
+        ctx.relu_parties(prm, buf["trc0"], buf["trc1"], 4, out=out, msgs=msgs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        ctx.relu_parties(prm, buf["trc0"], buf["trc1"], 4, out=out, msgs=msgs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    same = bool(torch.equal(out[0], buf["relu0"]) and torch.equal(out[1], buf["relu1"]))
+    msg_bytes = sum(t.numel() * t.element_size() for t in msgs.values())
+    return {"kernel_ms": ms, "elems_per_s": n / (ms / 1e3), "vs_fused": fused_ms / ms,
+            "message_bytes_per_element": msg_bytes / n,
+            "protocol_bits_per_element_p0_to_p2": (prm.lx + 1) ** 2,
+            "identical_to_fused": same, "launches": 3}
 
 
 def config1_check(ctx, dev):

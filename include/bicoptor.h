@@ -72,6 +72,8 @@ typedef struct {
   uint64_t rounds;               /* online communication rounds                        */
   uint64_t elements;             /* elements processed by interactive protocols        */
   uint64_t calls;                /* protocol calls                                     */
+  uint64_t pre_p2_to_p0;         /* preprocessing: [s]_0 of the RSS protocol           */
+  uint64_t rss_reshare;          /* replicated-product reshares P_i -> P_(i-1), all 3  */
 } bc_comm;
 
 /* Optional materialised messages of the next DReLU/ReLU calls (device
@@ -130,6 +132,24 @@ int bc_trunc_det(bc_ctx *ctx, int ring_bits, int k1, int k2, const void *sh0, co
 int bc_mod_switch(bc_ctx *ctx, int lp, uint32_t p, const void *sh0, const void *sh1, size_t n,
                   uint32_t *o0, uint32_t *o1);
 
+/* Alg. aby3trc (ABY3 probabilistic truncation, Sec. 2.4) between P0 and P1
+ * with P2 dealing (r, r' = r / 2^k): [r]_0, [r']_0 from seed02, [r]_1 from
+ * seed12, [r']_1 = r' - [r']_0 sent by P2 to P1; P0 and P1 open
+ * alpha = x + r; P0 outputs alpha / 2^k - [r']_0, P1 outputs -[r']_1.  "/ 2^k"
+ * is floor division of the two's-complement value.  fixed_r != 0 uses the
+ * constant r = fixed_r (random shares) -- the implementation shortcut Sec. 4.1
+ * shows hides e1.  Outputs in Z_{2^l}; 0 <= k < l. */
+int bc_trunc_aby3(bc_ctx *ctx, int ring_bits, int k, const void *sh0, const void *sh1, size_t n,
+                  uint32_t tensor_id, uint64_t fixed_r, void *o0, void *o1);
+
+/* Alg. linear (truncate-then-multiply, Sec. 4.2): Alg. smltrc removes kx bits
+ * from x and ky bits from y (kx + ky = the fractional bits; kx != ky for an odd
+ * count), then the Beaver product of the truncated shares (triple as in
+ * bc_mul_beaver for the same tensor_id).  One fused elementwise kernel. */
+int bc_trunc_then_mul(bc_ctx *ctx, int ring_bits, int kx, int ky, const void *x0, const void *x1,
+                      const void *y0, const void *y1, size_t n, uint32_t tensor_id, void *o0,
+                      void *o1);
+
 /* Beaver multiplication (Table "notation", Alg. relu preprocessing): the
  * triple comes from seed02/seed12, P2 sends [c]_1 to P1, d = x - a and
  * e = y - b are opened; [xy] = de + d[b] + e[a] + [c].  Exact in Z_{2^l}. */
@@ -149,6 +169,51 @@ int bc_relu(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void
 /* Materialise the messages of subsequent DReLU/ReLU calls into `bufs`
  * (NULL turns auditing off).  The buffers must hold the call's n elements. */
 int bc_set_audit(bc_ctx *ctx, const bc_audit *bufs);
+
+/* ---- RSS DReLU / ReLU (Alg. drelu2) ------------------------------------- */
+
+/* 2-of-3 replicated shares in Z_{2^l}: component arrays x0, x1, x2 with
+ * x = x0 + x1 + x2; P0 holds (x0, x1), P1 (x1, x2), P2 (x2, x0).  Outputs the
+ * three components of [DReLU(x)] (bc_rss_drelu) or of [ReLU(x)] (bc_rss_relu,
+ * the replicated product [x][DReLU]).  Preprocessing (replicated sharings of
+ * t and of P2's bit s, [s xor t] by one replicated product) and Alg. drelu
+ * between P0 ([x]_0 + [x]_1) and P1 ([x]_2) run in one fused kernel; P2
+ * publishes d'' = s xor DReLU'. */
+int bc_rss_drelu(bc_ctx *ctx, const bc_drelu_params *prm, const void *x0, const void *x1,
+                 const void *x2, size_t n, uint32_t tensor_id, void *y0, void *y1, void *y2);
+int bc_rss_relu(bc_ctx *ctx, const bc_drelu_params *prm, const void *x0, const void *x1,
+                const void *x2, size_t n, uint32_t tensor_id, void *y0, void *y1, void *y2);
+
+/* ---- party-separated DReLU / ReLU --------------------------------------- */
+
+/* The message buffers of one party-separated call (device memory owned by
+ * the caller).  Every message of Alg. drelu / Alg. relu lives here between
+ * the sender's kernel and the receiver's:
+ *   w0, w1      P0 -> P2 and P1 -> P2 (step 8), bc_party_msg_words(lx, n)
+ *               uint32 words each: the lx+1 values of lx+1 bits per element,
+ *               packed (groups of 32 elements; slot k of group g occupies the
+ *               lx+1 words at (k * ceil(n/32) + g) * (lx+1), element 32g+l at
+ *               bits [l (lx+1), (l+1)(lx+1)))
+ *   reply       lanes [n]: [DReLU']_1 to P1 (DReLU) / e = DReLU' - b (ReLU)
+ *   open0/1     lanes [n]: P0 -> P1 and P1 -> P0 shares of d = x - a (ReLU)
+ *   pre_c1      lanes [n]: P2 -> P1 preprocessing [c]_1 (ReLU)              */
+typedef struct {
+  uint32_t *w0, *w1;
+  void *reply, *open0, *open1, *pre_c1;
+} bc_party_msgs;
+
+/* uint32 words of one packed w buffer for n elements (ceil(n/32)*32*(lx+1)^2 bits). */
+size_t bc_party_msg_words(int lx, size_t n);
+
+/* Alg. drelu / Alg. relu with each party's local work in its own kernel and
+ * every message in `msgs`: P0 and P1 (steps 1-8, each expanding seed01
+ * itself, + ReLU openings), then P2 (step 9, reply, [c]_1), then P0 and P1
+ * finish.  Same outputs as bc_drelu / bc_relu and the same messages as their
+ * audit buffers (unpacked). */
+int bc_drelu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+                     size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
+int bc_relu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+                    size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
 
 int bc_get_comm(bc_ctx *ctx, bc_comm *out);
 int bc_reset_comm(bc_ctx *ctx);
@@ -248,13 +313,13 @@ typedef struct {
 int bc_linear_relu(bc_ctx *ctx, const bc_linear_relu_args *a);
 /* Same with HOST pointers for x0,x1,y0,y1 (input) and relu0,relu1,det0,det1
  * (output); prod/trc fields are ignored.  Staged through device buffers
- * reserved by bc_reserve in chunks of its `chunk` elements, three chunks in
- * flight on three streams so that host-to-device copies, kernels and
+ * reserved by bc_reserve in chunks of its `chunk` elements, four chunks in
+ * flight on four streams so that host-to-device copies, kernels and
  * device-to-host copies of different chunks overlap (pinned host memory
  * needed for the overlap).  Returns after the results are in host memory. */
 int bc_linear_relu_host(bc_ctx *ctx, const bc_linear_relu_args *a);
 /* Set the chunk of bc_linear_relu_host to `chunk` elements, growing the
- * device staging (3 sets of 12 arrays of `chunk` 64-bit lanes) if needed. */
+ * device staging (4 sets of 12 arrays of `chunk` 64-bit lanes) if needed. */
 int bc_reserve(bc_ctx *ctx, size_t chunk);
 
 /* ---- truncation-failure statistics (evaluation only) --------------------- */

@@ -26,8 +26,9 @@ _LIB_PATH = (os.path.join(os.path.dirname(os.path.abspath(_SRC)), "_build", "lib
 _lock = threading.Lock()
 _lib = None
 
-PAIR_01, PAIR_02, PAIR_12, PAIR_DEALER = 0x01, 0x02, 0x12, 0xDE
-PUR_SHARE, PUR_PERM, PUR_MASK, PUR_REPLY, PUR_RELU_TRIPLE, PUR_MUL_TRIPLE = 1, 2, 3, 4, 5, 6
+PAIR_01, PAIR_02, PAIR_12, PAIR_DEALER, PAIR_012, PAIR_2 = 0x01, 0x02, 0x12, 0xDE, 0x03, 0x20
+PUR_SHARE, PUR_PERM, PUR_MASK, PUR_REPLY, PUR_RELU_TRIPLE, PUR_MUL_TRIPLE, PUR_ABY3 = (
+    1, 2, 3, 4, 5, 6, 7)
 
 
 def build(force: bool = False) -> str:
@@ -239,3 +240,48 @@ def drelu_core_many(P: _Params, s0, s1, t, fy, r, z):
     if rc != 0:
         raise ValueError("oracle rejected the parameters")
     return out
+
+
+def aby3_core(ell, k, s0, s1, r0, r1, rp0):
+    """One element of Alg. aby3trc with explicit preprocessing randomness."""
+    o0, o1 = ctypes.c_uint64(), ctypes.c_uint64()
+    u = ctypes.c_uint64
+    lib().orc_aby3_core(ell, k, u(s0), u(s1), u(r0), u(r1), u(rp0), ctypes.byref(o0),
+                        ctypes.byref(o1))
+    return o0.value, o1.value
+
+
+def trunc_aby3(ell, k, s0, s1, seed, tid, fixed_r=0, idx=None):
+    s0, s1 = _u64(s0), _u64(s1)
+    idx = None if idx is None else _u64(idx)
+    o0, o1 = np.empty_like(s0), np.empty_like(s1)
+    lib().orc_trunc_aby3(ell, k, _p(s0), _p(s1), _p(idx), ctypes.c_size_t(s0.size),
+                         ctypes.c_uint64(seed), ctypes.c_uint32(tid), ctypes.c_uint64(fixed_r),
+                         _p(o0), _p(o1))
+    return o0, o1
+
+
+def trunc_then_mul(ell, kx, ky, x0, x1, y0, y1, seed, tid, idx=None):
+    x0, x1, y0, y1 = map(_u64, (x0, x1, y0, y1))
+    idx = None if idx is None else _u64(idx)
+    o0, o1 = np.empty_like(x0), np.empty_like(x0)
+    lib().orc_trunc_then_mul(ell, kx, ky, _p(x0), _p(x1), _p(y0), _p(y1), _p(idx),
+                             ctypes.c_size_t(x0.size), ctypes.c_uint64(seed),
+                             ctypes.c_uint32(tid), _p(o0), _p(o1))
+    return o0, o1
+
+
+def rss_drelu(P, x0, x1, x2, seed, tid, relu=False, idx=None, threads=1):
+    """Alg. drelu2 (relu=False) or the RSS ReLU on replicated components;
+    returns (y0, y1, y2, DReLU')."""
+    x0, x1, x2 = map(_u64, (x0, x1, x2))
+    n = x0.size
+    idx = None if idx is None else _u64(idx)
+    y0, y1, y2 = (np.empty_like(x0) for _ in range(3))
+    dp = np.empty(n, np.uint8)
+    rc = lib().orc_rss_drelu(ctypes.byref(P), _p(x0), _p(x1), _p(x2), _p(idx), ctypes.c_size_t(n),
+                             ctypes.c_uint64(seed), ctypes.c_uint32(tid), int(relu), _p(y0),
+                             _p(y1), _p(y2), _p(dp), threads)
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters")
+    return y0, y1, y2, dp

@@ -99,14 +99,20 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Word j of a stream is word j % 4 of block j / 4.                          */
 /* ------------------------------------------------------------------------- */
 
-enum { PAIR_01 = 0x01, PAIR_02 = 0x02, PAIR_12 = 0x12, PAIR_DEALER = 0xDE };
+enum { PAIR_01 = 0x01, PAIR_02 = 0x02, PAIR_12 = 0x12, PAIR_DEALER = 0xDE,
+       PAIR_012 = 0x03 /* seed012, all three parties */, PAIR_2 = 0x20 /* seed2, P2 alone */ };
 enum {
     PUR_SHARE = 1,      /* dealer's R for the 2-of-2 sharing            */
     PUR_PERM = 2,       /* seed01: flip bit t and the shuffle           */
     PUR_MASK = 3,       /* seed01: r_k, z_k of message slot k           */
     PUR_REPLY = 4,      /* seed02: P0's share of DReLU'                 */
     PUR_RELU_TRIPLE = 5,/* seed02: a0,b0,c0 / seed12: a1,b1 (ReLU)      */
-    PUR_MUL_TRIPLE = 6  /* seed02: a0,b0,c0 / seed12: a1,b1 (product)   */
+    PUR_MUL_TRIPLE = 6, /* seed02: a0,b0,c0 / seed12: a1,b1 (product)   */
+    PUR_ABY3 = 7,       /* seed02: [r]_0, [r']_0 / seed12: [r]_1         */
+    PUR_RSS_T = 8,      /* seed012: alpha_0..2 (sharing of t)            */
+    PUR_RSS_S = 9,      /* seed2: s / seed012: [s]_1 / seed12: [s]_2     */
+    PUR_RSS_Z = 10,     /* seed012: gamma_0..2, zero sharing of [s][t]   */
+    PUR_RSS_ZR = 11     /* seed012: zero sharing of the ReLU product     */
 };
 
 uint32_t orc_stream_word(uint64_t seed, int pair, int purpose, uint32_t tensor_id,
@@ -287,6 +293,55 @@ void orc_mod_switch(int lp, uint32_t p, const uint64_t *s0, const uint64_t *s1, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Alg. aby3trc (ABY3 probabilistic truncation) between P0 and P1, with P2  */
+/* dealing the pair (r, r' = r / 2^k): [r]_0 and [r']_0 from seed02, [r]_1  */
+/* from seed12; P2 sends [r']_1 = r' - [r']_0 to P1 (preprocessing).         */
+/* Online both open alpha = x + r; P0 sets alpha / 2^k - [r']_0 and P1 sets  */
+/* -[r']_1 (the public alpha / 2^k is added by P0 alone).                    */
+/* READING: / 2^k is floor division of the two's-complement (signed) value. */
+/* Sec. 4.1's claim that a fixed r = 2^26 never triggers e1 for 62-bit      */
+/* inputs holds for negative inputs only under this reading.                 */
+/* ------------------------------------------------------------------------- */
+
+static uint64_t floor_div_pow2_signed(uint64_t a, int ell, int k)
+{
+    __int128 v = (__int128)rmod(a, ell);
+    if (ell < 128 && (v >> (ell - 1)) & 1) v -= ((__int128)1 << ell);   /* signed value */
+    __int128 d = (__int128)1 << k;
+    __int128 q = v >= 0 ? v / d : -((-v + d - 1) / d);                  /* floor */
+    return rmod((uint64_t)q, ell);
+}
+
+/* One element of Alg. aby3trc with the preprocessing randomness passed in:
+ * r0 = [r]_0, r1 = [r]_1 (r = r0 + r1), rp0 = [r']_0.  Returns the shares. */
+void orc_aby3_core(int ell, int k, uint64_t s0, uint64_t s1, uint64_t r0, uint64_t r1,
+                   uint64_t rp0, uint64_t *o0, uint64_t *o1)
+{
+    uint64_t r = rmod(r0 + r1, ell);                       /* known to P2 */
+    uint64_t rp = floor_div_pow2_signed(r, ell, k);        /* r' = r / 2^k */
+    uint64_t rp1 = rmod(rp - rp0, ell);                    /* P2 -> P1 */
+    uint64_t alpha = rmod((s0 + r0) + (s1 + r1), ell);     /* opened */
+    *o0 = rmod(floor_div_pow2_signed(alpha, ell, k) - rp0, ell);
+    *o1 = rneg(rp1, ell);
+}
+
+/* fixed_r != 0 reproduces the implementation shortcut of Sec. 4.1: r is
+ * the constant fixed_r (its shares stay random: [r]_1 = fixed_r - [r]_0). */
+void orc_trunc_aby3(int ell, int k, const uint64_t *s0, const uint64_t *s1, const uint64_t *idx,
+                    size_t n, uint64_t seed, uint32_t tid, uint64_t fixed_r, uint64_t *o0,
+                    uint64_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t elem = elem_index(idx, i);
+        uint64_t r0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 0, ell);
+        uint64_t rp0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 1, ell);
+        uint64_t r1 = stream_ring(seed, PAIR_12, PUR_ABY3, tid, elem, 0, ell);
+        if (fixed_r) r1 = rmod(fixed_r - r0, ell);
+        orc_aby3_core(ell, k, s0[i], s1[i], r0, r1, rp0, &o0[i], &o1[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Beaver multiplication (Table notation, Sec. 2.3; Alg. relu pre-          */
 /* processing): the triple comes from the pre-shared seeds, P2 completes     */
 /* [c]_1 = (a0 + a1)(b0 + b1) - [c]_0 and sends it to P1.  d = x - a and     */
@@ -319,6 +374,22 @@ void orc_mul_beaver(int ell, const uint64_t *x0, const uint64_t *x1, const uint6
         uint64_t e = rmod((y0[i] - T.b0) + (y1[i] - T.b1), ell);
         o0[i] = rmod(d * e + d * T.b0 + e * T.a0 + T.c0, ell);
         o1[i] = rmod(d * T.b1 + e * T.a1 + T.c1, ell);
+    }
+}
+
+/* Alg. linear (truncate-then-multiply): P_i truncates its shares of x by
+ * kx bits and of y by ky bits with Alg. smltrc (kx + ky = l_x^frac; for an
+ * odd precision one input loses one bit more), then the Beaver product of
+ * the truncated shares gives shares of trc(x y, l_x^frac). */
+void orc_trunc_then_mul(int ell, int kx, int ky, const uint64_t *x0, const uint64_t *x1,
+                        const uint64_t *y0, const uint64_t *y1, const uint64_t *idx, size_t n,
+                        uint64_t seed, uint32_t tid, uint64_t *o0, uint64_t *o1)
+{
+    for (size_t i = 0; i < n; i++) {
+        uint64_t tx0 = smltrc_p0(x0[i], ell, kx), tx1 = smltrc_p1(x1[i], ell, kx);
+        uint64_t ty0 = smltrc_p0(y0[i], ell, ky), ty1 = smltrc_p1(y1[i], ell, ky);
+        uint64_t e = elem_index(idx, i);
+        orc_mul_beaver(ell, &tx0, &tx1, &ty0, &ty1, &e, 1, seed, tid, &o0[i], &o1[i]);
     }
 }
 
@@ -549,6 +620,83 @@ int orc_relu(const orc_params *P, const uint64_t *s0, const uint64_t *s1, const 
             if (audit->t) audit->t[i] = (uint8_t)t;
             if (audit->dprime) audit->dprime[i] = (uint8_t)dprime;
         }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. drelu2 (RSS Bicoptor 2.0 DReLU) and the RSS ReLU.  2-of-3 replicated */
+/* sharing: x = x0 + x1 + x2, P0 holds (x0, x1), P1 (x1, x2), P2 (x2, x0);  */
+/* component arrays x0, x1, x2 in and y0, y1, y2 out.                         */
+/* Preprocessing: t from seed01; alpha_i from seed012, beta_i = alpha_i -   */
+/* alpha_(i-1), [t] = (beta_0, beta_1 + t, beta_2); s a bit from seed2,      */
+/* [s]_1 from seed012, [s]_2 from seed12, [s]_0 = s - [s]_1 - [s]_2 (P2 ->   */
+/* P0); [s xor t] = [s] + [t] - 2 [s][t].                                     */
+/* READING: [s][t] is the replicated product (each P_i forms                  */
+/* s_i t_i + s_i t_(i+1) + s_(i+1) t_i plus a zero sharing                    */
+/* gamma_i - gamma_(i+1) and sends it to P_(i-1)); the paper names the       */
+/* product but not its protocol.                                              */
+/* Online: P0 runs Alg. drelu on [x]_0 + [x]_1, P1 on [x]_2 (steps 1-8 with  */
+/* the same seed01 draws); P2 gets DReLU', sends d'' = s xor DReLU' to P0    */
+/* and P1; all set [DReLU] = d'' + [s xor t] - 2 d'' [s xor t] (the public  */
+/* d'' added to component 0).  RSS ReLU: the replicated product              */
+/* [x] [DReLU] with its own zero sharing (Sec. "How to construct the RSS     */
+/* ... protocols").                                                          */
+/* ------------------------------------------------------------------------- */
+
+static void rss_mul(int ell, const uint64_t a[3], const uint64_t b[3], const uint64_t g[3],
+                    uint64_t out[3])
+{
+    for (int i = 0; i < 3; i++) {
+        int j = (i + 1) % 3;
+        out[i] = rmod(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] - g[j], ell);
+    }
+}
+
+int orc_rss_drelu(const orc_params *P, const uint64_t *x0, const uint64_t *x1, const uint64_t *x2,
+                  const uint64_t *idx, size_t n, uint64_t seed, uint32_t tid, int relu,
+                  uint64_t *y0, uint64_t *y1, uint64_t *y2, uint8_t *dprime_out, int threads)
+{
+    if (check_params(P)) return -1;
+    const int ell = P->ell;
+    const uint32_t inv32 = inv_two32_mod_p(P->p);
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (long long ii = 0; ii < (long long)n; ii++) {
+        size_t i = (size_t)ii;
+        uint64_t elem = elem_index(idx, i);
+        int t;
+        uint32_t fy[MAXL], r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
+        draw_seed01(P, seed, tid, elem, inv32, &t, fy, r, z);
+        /* preprocessing: [t], [s], [s xor t] */
+        uint64_t al[3], T[3], S[3], g[3], ST[3], X[3];
+        for (int j = 0; j < 3; j++) al[j] = stream_ring(seed, PAIR_012, PUR_RSS_T, tid, elem, j, ell);
+        T[0] = rmod(al[0] - al[2], ell);
+        T[1] = rmod(al[1] - al[0] + (uint64_t)t, ell);
+        T[2] = rmod(al[2] - al[1], ell);
+        uint64_t sbit = orc_stream_word(seed, PAIR_2, PUR_RSS_S, tid, elem, 0) & 1u;
+        S[1] = stream_ring(seed, PAIR_012, PUR_RSS_S, tid, elem, 0, ell);
+        S[2] = stream_ring(seed, PAIR_12, PUR_RSS_S, tid, elem, 0, ell);
+        S[0] = rmod(sbit - S[1] - S[2], ell);
+        for (int j = 0; j < 3; j++) g[j] = stream_ring(seed, PAIR_012, PUR_RSS_Z, tid, elem, j, ell);
+        rss_mul(ell, S, T, g, ST);
+        for (int j = 0; j < 3; j++) X[j] = rmod(S[j] + T[j] - 2 * ST[j], ell);
+        /* online: Alg. drelu between P0 ([x]_0 + [x]_1) and P1 ([x]_2) */
+        int dprime = orc_drelu_core(P, rmod(x0[i] + x1[i], ell), x2[i], t, fy, r, z, msg0, msg1);
+        uint64_t dd = (sbit ^ (uint64_t)dprime);            /* d'' = s xor DReLU' */
+        uint64_t Y[3];
+        for (int j = 0; j < 3; j++) Y[j] = rmod(X[j] - 2 * dd * X[j] + (j == 0 ? dd : 0), ell);
+        if (relu) {
+            uint64_t xr[3] = {x0[i], x1[i], x2[i]}, gr[3], Z[3];
+            for (int j = 0; j < 3; j++)
+                gr[j] = stream_ring(seed, PAIR_012, PUR_RSS_ZR, tid, elem, j, ell);
+            rss_mul(ell, xr, Y, gr, Z);
+            for (int j = 0; j < 3; j++) Y[j] = Z[j];
+        }
+        y0[i] = Y[0]; y1[i] = Y[1]; y2[i] = Y[2];
+        if (dprime_out) dprime_out[i] = (uint8_t)dprime;
     }
     return 0;
 }

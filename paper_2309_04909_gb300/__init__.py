@@ -18,7 +18,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 from . import _native
-from ._native import Audit, BatchConfig, Comm, DreluParams, LinearReluArgs, TensorDesc
+from ._native import Audit, BatchConfig, Comm, DreluParams, LinearReluArgs, PartyMsgs, TensorDesc
 
 __all__ = ["Context", "Params", "BicoptorError", "lane_dtype", "prime_above", "build"]
 
@@ -173,6 +173,31 @@ class Context:
                                             _ptr(y1), n, tensor_id, _ptr(o0), _ptr(o1)))
         return o0, o1
 
+    def trunc_aby3(self, ring_bits: int, k: int, s0, s1, tensor_id: int, fixed_r: int = 0,
+                   out=None):
+        """Alg. aby3trc; fixed_r != 0 uses the constant mask of Sec. 4.1."""
+        self._need(s0, ring_bits, "s0")
+        self._need(s1, ring_bits, "s1")
+        n = s0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, ring_bits), self._empty(n, ring_bits))
+        self._sync_stream()
+        self._check(self._lib.bc_trunc_aby3(self._h, ring_bits, k, _ptr(s0), _ptr(s1), n,
+                                            tensor_id, fixed_r, _ptr(o0), _ptr(o1)))
+        return o0, o1
+
+    def trunc_then_mul(self, ring_bits: int, kx: int, ky: int, x0, x1, y0, y1, tensor_id: int,
+                       out=None):
+        """Alg. linear: Alg. smltrc by kx / ky bits, then the Beaver product."""
+        for t, nm in ((x0, "x0"), (x1, "x1"), (y0, "y0"), (y1, "y1")):
+            self._need(t, ring_bits, nm)
+        n = x0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, ring_bits), self._empty(n, ring_bits))
+        self._sync_stream()
+        self._check(self._lib.bc_trunc_then_mul(self._h, ring_bits, kx, ky, _ptr(x0), _ptr(x1),
+                                                _ptr(y0), _ptr(y1), n, tensor_id, _ptr(o0),
+                                                _ptr(o1)))
+        return o0, o1
+
     # -- DReLU / ReLU -------------------------------------------------------------
     def _protocol(self, fn, prm: Params, s0, s1, tensor_id, out, audit):
         self._need(s0, prm.ring_bits, "s0")
@@ -208,6 +233,58 @@ class Context:
 
     def relu(self, prm: Params, s0, s1, tensor_id: int, out=None, audit: bool = False):
         return self._protocol(self._lib.bc_relu, prm, s0, s1, tensor_id, out, audit)
+
+    # -- RSS (Alg. drelu2) -----------------------------------------------------------
+    def _rss(self, fn, prm: Params, x0, x1, x2, tensor_id, out):
+        for t, nm in ((x0, "x0"), (x1, "x1"), (x2, "x2")):
+            self._need(t, prm.ring_bits, nm)
+        n = x0.numel()
+        ys = out if out is not None else tuple(self._empty(n, prm.ring_bits) for _ in range(3))
+        prm_c = prm.c_struct()
+        self._sync_stream()
+        self._check(fn(self._h, ctypes.byref(prm_c), _ptr(x0), _ptr(x1), _ptr(x2), n, tensor_id,
+                       *[_ptr(y) for y in ys]))
+        return ys
+
+    def rss_drelu(self, prm: Params, x0, x1, x2, tensor_id: int, out=None):
+        """Alg. drelu2 on replicated components; returns (y0, y1, y2)."""
+        return self._rss(self._lib.bc_rss_drelu, prm, x0, x1, x2, tensor_id, out)
+
+    def rss_relu(self, prm: Params, x0, x1, x2, tensor_id: int, out=None):
+        return self._rss(self._lib.bc_rss_relu, prm, x0, x1, x2, tensor_id, out)
+
+    # -- party-separated ----------------------------------------------------------
+    def party_buffers(self, prm: Params, n: int) -> Dict[str, torch.Tensor]:
+        """Message buffers of one party-separated call (see bc_party_msgs)."""
+        words = int(self._lib.bc_party_msg_words(prm.lx, n))
+        dev = self.device
+        d = {"w0": torch.empty(words, dtype=torch.int32, device=dev),
+             "w1": torch.empty(words, dtype=torch.int32, device=dev)}
+        for k in ("reply", "open0", "open1", "pre_c1"):
+            d[k] = self._empty(n, prm.ring_bits)
+        return d
+
+    def _parties(self, fn, prm: Params, s0, s1, tensor_id, out, msgs):
+        self._need(s0, prm.ring_bits, "s0")
+        self._need(s1, prm.ring_bits, "s1")
+        n = s0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, prm.ring_bits),
+                                              self._empty(n, prm.ring_bits))
+        m = msgs if msgs is not None else self.party_buffers(prm, n)
+        pm = PartyMsgs(*[_ptr(m[k]) for k in ("w0", "w1", "reply", "open0", "open1", "pre_c1")])
+        prm_c = prm.c_struct()
+        self._sync_stream()
+        self._check(fn(self._h, ctypes.byref(prm_c), _ptr(s0), _ptr(s1), n, tensor_id, _ptr(o0),
+                       _ptr(o1), ctypes.byref(pm)))
+        return o0, o1, m
+
+    def drelu_parties(self, prm: Params, s0, s1, tensor_id: int, out=None, msgs=None):
+        """DReLU with each party's work in its own kernel and the messages in
+        device buffers; returns (o0, o1, message buffers)."""
+        return self._parties(self._lib.bc_drelu_parties, prm, s0, s1, tensor_id, out, msgs)
+
+    def relu_parties(self, prm: Params, s0, s1, tensor_id: int, out=None, msgs=None):
+        return self._parties(self._lib.bc_relu_parties, prm, s0, s1, tensor_id, out, msgs)
 
     # -- batched ------------------------------------------------------------------
     def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0,

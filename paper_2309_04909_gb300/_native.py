@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libbicoptor.so")
-SOURCES = ["bc_relu.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu"]
+SOURCES = ["bc_relu.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu", "bc_parties.cu"]
 HEADERS = ["bc_device.cuh", "bc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -86,7 +86,8 @@ class DreluParams(ctypes.Structure):
 
 class Comm(ctypes.Structure):
     _fields_ = [(n, c_u64) for n in ("p0_to_p2", "p1_to_p2", "p2_to_p0", "p2_to_p1", "p0_to_p1",
-                                     "p1_to_p0", "pre_p2_to_p1", "rounds", "elements", "calls")]
+                                     "p1_to_p0", "pre_p2_to_p1", "rounds", "elements", "calls",
+                                     "pre_p2_to_p0", "rss_reshare")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -101,6 +102,11 @@ class TensorDesc(ctypes.Structure):
     _fields_ = [("sh0", c_void_p), ("sh1", c_void_p), ("o0", c_void_p), ("o1", c_void_p),
                 ("n", c_u64), ("tensor_id", c_u32), ("op", c_int), ("params", DreluParams),
                 ("elem_offset", c_u64)]
+
+
+class PartyMsgs(ctypes.Structure):
+    _fields_ = [("w0", c_void_p), ("w1", c_void_p), ("reply", c_void_p), ("open0", c_void_p),
+                ("open1", c_void_p), ("pre_c1", c_void_p)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -151,6 +157,19 @@ SIGNATURES = {
     "bc_count_trunc_failures": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                         c_size, c_void_p]),
     "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),
+    "bc_party_msg_words": (c_size, [c_int, c_size]),
+    "bc_rss_drelu": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_void_p, c_size, c_u32,
+                             c_void_p, c_void_p, c_void_p]),
+    "bc_rss_relu": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_void_p, c_size, c_u32,
+                            c_void_p, c_void_p, c_void_p]),
+    "bc_trunc_aby3": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_size, c_u32, c_u64,
+                              c_void_p, c_void_p]),
+    "bc_trunc_then_mul": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_size, c_u32, c_void_p, c_void_p]),
+    "bc_drelu_parties": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_size, c_u32,
+                                 c_void_p, c_void_p, P(PartyMsgs)]),
+    "bc_relu_parties": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_size, c_u32,
+                                c_void_p, c_void_p, P(PartyMsgs)]),
 }
 
 

@@ -13,7 +13,7 @@
 struct bc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaStream_t aux[2] = {nullptr, nullptr};   // more streams of the host-staging pipeline
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   // more streams of the host staging
   uint64_t seed = 0;
   bc::RoundKeys rk{};
   int num_sms = 1;
@@ -46,7 +46,7 @@ struct bc_ctx {
   // host staging for bc_linear_relu_host: one set of chunk buffers per stream
   size_t stage_cap = 0;       // allocated elements per array
   size_t stage_chunk = 0;     // elements per chunk (<= stage_cap)
-  void* stage[3] = {nullptr, nullptr, nullptr};
+  void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_start = nullptr;
 };
 
@@ -141,6 +141,8 @@ void add_comm(bc_comm* c, const bc_comm& d) {
   c->rounds += d.rounds;
   c->elements += d.elements;
   c->calls += d.calls;
+  c->pre_p2_to_p0 += d.pre_p2_to_p0;
+  c->rss_reshare += d.rss_reshare;
 }
 
 bc_comm relu_comm(int ell, int lx, uint64_t n, bool relu) {
@@ -223,7 +225,7 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
   ctx->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int) * bc::kMaxBatchGroups);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
@@ -244,7 +246,7 @@ int bc_destroy(bc_ctx* ctx) {
   if (!ctx) return BC_EINVAL;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     if (ctx->aux[i]) {
       cudaStreamSynchronize(ctx->aux[i]);
       cudaStreamDestroy(ctx->aux[i]);
@@ -259,7 +261,7 @@ int bc_destroy(bc_ctx* ctx) {
   }
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_status);
-  for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
+  for (int i = 0; i < 4; ++i) cudaFree(ctx->stage[i]);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   delete ctx;
   return BC_OK;
@@ -332,6 +334,35 @@ int bc_mul_beaver(bc_ctx* ctx, int ring_bits, const void* x0, const void* x1, co
   return BC_OK;
 }
 
+int bc_trunc_aby3(bc_ctx* ctx, int ring_bits, int k, const void* sh0, const void* sh1, size_t n,
+                  uint32_t tensor_id, uint64_t fixed_r, void* o0, void* o1) {
+  if (!ctx || ring_bits < 2 || ring_bits > 64 || k < 0 || k >= ring_bits) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_trunc_aby3(ring_bits, ctx->rk, k, sh0, sh1, n, tensor_id,
+                           fixed_r & ring_mask(ring_bits), o0, o1, ctx->num_sms, ctx->stream));
+  bc_comm d{};
+  d.p0_to_p1 = d.p1_to_p0 = n * (uint64_t)ring_bits;   // shares of alpha = x + r
+  d.pre_p2_to_p1 = n * (uint64_t)ring_bits;            // [r']_1
+  d.rounds = n ? 1 : 0;
+  d.elements = n;
+  d.calls = 1;
+  add_comm(&ctx->comm, d);
+  return BC_OK;
+}
+
+int bc_trunc_then_mul(bc_ctx* ctx, int ring_bits, int kx, int ky, const void* x0, const void* x1,
+                      const void* y0, const void* y1, size_t n, uint32_t tensor_id, void* o0,
+                      void* o1) {
+  if (!ctx || ring_bits < 1 || ring_bits > 64 || kx < 0 || ky < 0 || kx >= ring_bits ||
+      ky >= ring_bits)
+    return BC_EINVAL;
+  if (n && (!x0 || !x1 || !y0 || !y1 || !o0 || !o1)) return BC_EINVAL;
+  CK(bc::launch_trunc_then_mul(ring_bits, ctx->rk, kx, ky, x0, x1, y0, y1, n, tensor_id, o0, o1,
+                               ctx->num_sms, ctx->stream));
+  add_comm(&ctx->comm, mul_comm(ring_bits, n));
+  return BC_OK;
+}
+
 int bc_drelu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
              uint32_t tensor_id, void* o0, void* o1) {
   return run_relu(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, false, 0, ctx ? ctx->stream : nullptr,
@@ -358,6 +389,71 @@ int bc_set_audit(bc_ctx* ctx, const bc_audit* b) {
     ctx->audit.dprime = b->dprime;
   }
   return BC_OK;
+}
+
+static int run_rss(bc_ctx* ctx, const bc_drelu_params* prm, const void* x0, const void* x1,
+                   const void* x2, size_t n, uint32_t tensor_id, void* y0, void* y1, void* y2,
+                   bool relu) {
+  if (!ctx) return BC_EINVAL;
+  if (n && (!x0 || !x1 || !x2 || !y0 || !y1 || !y2)) return BC_EINVAL;
+  bc::ReluConsts k;
+  int rc = make_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  const void* x[3] = {x0, x1, x2};
+  void* y[3] = {y0, y1, y2};
+  if (n) CK(bc::launch_rss(k, relu, x, n, y, ctx->stream));
+  const uint64_t ell = (uint64_t)prm->ring_bits, L = (uint64_t)prm->lx + 1;
+  bc_comm d{};
+  d.p0_to_p2 = d.p1_to_p2 = n * L * L;        // Alg. drelu step 8
+  d.p2_to_p0 = d.p2_to_p1 = n;                // the public bit d''
+  d.pre_p2_to_p0 = n * ell;                   // [s]_0
+  d.rss_reshare = 3 * n * ell * (relu ? 2 : 1);   // [s][t] (and [x][DReLU])
+  d.rounds = n ? (relu ? 3 : 2) : 0;
+  d.elements = n;
+  d.calls = 1;
+  add_comm(&ctx->comm, d);
+  return BC_OK;
+}
+
+int bc_rss_drelu(bc_ctx* ctx, const bc_drelu_params* prm, const void* x0, const void* x1,
+                 const void* x2, size_t n, uint32_t tensor_id, void* y0, void* y1, void* y2) {
+  return run_rss(ctx, prm, x0, x1, x2, n, tensor_id, y0, y1, y2, false);
+}
+
+int bc_rss_relu(bc_ctx* ctx, const bc_drelu_params* prm, const void* x0, const void* x1,
+                const void* x2, size_t n, uint32_t tensor_id, void* y0, void* y1, void* y2) {
+  return run_rss(ctx, prm, x0, x1, x2, n, tensor_id, y0, y1, y2, true);
+}
+
+size_t bc_party_msg_words(int lx, size_t n) {
+  if (lx < 1 || lx > 31) return 0;
+  return (size_t)bc::party_msg_words((uint32_t)lx, n);
+}
+
+static int run_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+                       size_t n, uint32_t tensor_id, void* o0, void* o1,
+                       const bc_party_msgs* m, bool relu) {
+  if (!ctx || !m) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1 || !m->w0 || !m->w1 || !m->reply)) return BC_EINVAL;
+  if (n && relu && (!m->open0 || !m->open1 || !m->pre_c1)) return BC_EINVAL;
+  bc::ReluConsts k;
+  int rc = make_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  if (n)
+    CK(bc::launch_parties(k, relu, sh0, sh1, n, o0, o1, m->w0, m->w1, m->open0, m->open1,
+                          m->reply, m->pre_c1, ctx->stream));
+  add_comm(&ctx->comm, relu_comm(prm->ring_bits, prm->lx, n, relu));
+  return BC_OK;
+}
+
+int bc_drelu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+                     size_t n, uint32_t tensor_id, void* o0, void* o1, const bc_party_msgs* m) {
+  return run_parties(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, m, false);
+}
+
+int bc_relu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+                    size_t n, uint32_t tensor_id, void* o0, void* o1, const bc_party_msgs* m) {
+  return run_parties(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, m, true);
 }
 
 int bc_get_comm(bc_ctx* ctx, bc_comm* out) {
@@ -567,14 +663,14 @@ int bc_reserve(bc_ctx* ctx, size_t max_chunk) {
   if (!ctx || max_chunk == 0) return BC_EINVAL;
   if (max_chunk > ctx->stage_cap) {
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 2; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
+    for (int i = 0; i < 4; ++i) {
       cudaFree(ctx->stage[i]);
       ctx->stage[i] = nullptr;
     }
     ctx->stage_cap = ctx->stage_chunk = 0;
     const size_t per = ((max_chunk * 8 + 255) / 256) * 256;   // one 64-bit array, 256 B aligned
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       if (cudaMalloc(&ctx->stage[i], per * 12) != cudaSuccess) {
         cudaGetLastError();
         return BC_ENOMEM;
@@ -596,11 +692,10 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   const size_t db = lane_bytes(a->ring_bits - a->trunc_bits);
   const size_t per = ((ctx->stage_cap * 8 + 255) / 256) * 256;
   const size_t chunk = ctx->stage_chunk;
-  cudaStream_t st[3] = {ctx->stream, ctx->aux[0], ctx->aux[1]};
+  cudaStream_t st[4] = {ctx->stream, ctx->aux[0], ctx->aux[1], ctx->aux[2]};
   // the other streams start after everything queued on the context stream
   CK(cudaEventRecord(ctx->ev_start, ctx->stream));
-  CK(cudaStreamWaitEvent(ctx->aux[0], ctx->ev_start, 0));
-  CK(cudaStreamWaitEvent(ctx->aux[1], ctx->ev_start, 0));
+  for (int i = 0; i < 3; ++i) CK(cudaStreamWaitEvent(ctx->aux[i], ctx->ev_start, 0));
   const char* hx0 = static_cast<const char*>(a->x0);
   const char* hx1 = static_cast<const char*>(a->x1);
   const char* hy0 = static_cast<const char*>(a->y0);
@@ -609,14 +704,14 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   char* hr1 = static_cast<char*>(a->relu1);
   char* hd0 = static_cast<char*>(a->det0);
   char* hd1 = static_cast<char*>(a->det1);
-  // chunk j runs on stream j % 3 with stage set j % 3: copies in, compute,
-  // copies out; three chunks in flight let the two copy directions and the
+  // chunk j runs on stream j % 4 with stage set j % 4: copies in, compute,
+  // copies out; four chunks in flight let the two copy directions and the
   // kernels of different chunks overlap
   size_t j = 0;
   for (size_t off = 0; off < a->n; off += chunk, ++j) {
     const size_t m = std::min(chunk, a->n - off);
-    cudaStream_t s = st[j % 3];
-    char* base = static_cast<char*>(ctx->stage[j % 3]);
+    cudaStream_t s = st[j % 4];
+    char* base = static_cast<char*>(ctx->stage[j % 4]);
     void* b[12];
     for (int q = 0; q < 12; ++q) b[q] = base + per * q;
     CK(cudaMemcpyAsync(b[0], hx0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
@@ -634,7 +729,7 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
       CK(cudaMemcpyAsync(hd1 + off * db, b[9], m * db, cudaMemcpyDeviceToHost, s));
     }
   }
-  for (int i = 0; i < 2; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
+  for (int i = 0; i < 3; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
   CK(cudaStreamSynchronize(ctx->stream));
   add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
   add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));

@@ -65,7 +65,11 @@ __device__ __forceinline__ U32x4 philox_rounds_2_10(uint32_t c0, uint32_t c1, ui
 
 // Stream tags: which pre-shared seed a draw belongs to, and what it is for.
 // counter = (lo32(elem), tensor_id, block, pair << 24 | purpose << 16 | elem >> 32)
-enum : uint32_t { kPair01 = 0x01, kPair02 = 0x02, kPair12 = 0x12, kPairDealer = 0xDE };
+enum : uint32_t {
+  kPair01 = 0x01, kPair02 = 0x02, kPair12 = 0x12, kPairDealer = 0xDE,
+  kPair012 = 0x03,   // seed012, all three parties (RSS)
+  kPair2 = 0x20      // seed2, P2 alone (RSS)
+};
 enum : uint32_t {
   kPurShare = 1,        // dealer: R of the 2-of-2 sharing
   kPurPerm = 2,         // seed01: flip bit t and the shuffle words
@@ -73,6 +77,11 @@ enum : uint32_t {
   kPurReply = 4,        // seed02: P0's share of DReLU'
   kPurReluTriple = 5,   // seed02: a0,b0,c0 / seed12: a1,b1 of the ReLU product
   kPurMulTriple = 6,    // seed02: a0,b0,c0 / seed12: a1,b1 of a Beaver product
+  kPurAby3 = 7,         // seed02: [r]_0, [r']_0 / seed12: [r]_1 of ABY3 truncation
+  kPurRssT = 8,         // seed012: alpha_0..2, the sharing of t (RSS)
+  kPurRssS = 9,         // seed2: s / seed012: [s]_1 / seed12: [s]_2 (RSS)
+  kPurRssZ = 10,        // seed012: zero sharing of [s][t] (RSS)
+  kPurRssZr = 11,       // seed012: zero sharing of the RSS ReLU product
 };
 
 __device__ __forceinline__ uint32_t stream_tag(uint32_t pair, uint32_t purpose, uint64_t elem) {

@@ -6,6 +6,8 @@
 // These are HBM-bound: each thread moves 16 bytes per array per iteration
 // (one 128-bit load of 2 x uint64 or 4 x uint32 lanes) when every array is
 // 16-byte aligned; grid = SMs x resident CTAs, grid-stride.
+#include <type_traits>
+
 #include "bc_internal.h"
 
 namespace bc {
@@ -168,6 +170,73 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// ---- Alg. aby3trc: open alpha = x + r, P0: alpha / 2^k - [r']_0, P1: -[r']_1 ---
+// floor(signed(a) / 2^k) in Z_{2^l}: sign-extend bit l-1, arithmetic shift.
+template <typename Lane>
+__device__ __forceinline__ Lane sdiv_pow2(Lane a, Lane mask, uint32_t ell, uint32_t k) {
+  using S = typename std::conditional<sizeof(Lane) == 8, int64_t, int32_t>::type;
+  const Lane sign = (Lane)1 << (ell - 1);
+  const S v = (S)((a ^ sign) - sign);   // two's-complement value of the l-bit a
+  return (Lane)(v >> k) & mask;
+}
+
+template <typename Lane>
+__global__ void __launch_bounds__(kBlock)
+    aby3_trunc_kernel(const RoundKeys rk, Lane mask, uint32_t ell, uint32_t k, uint32_t tid,
+                      uint64_t base, Lane fixed_r, const Lane* __restrict__ s0,
+                      const Lane* __restrict__ s1, uint64_t n, Lane* __restrict__ o0,
+                      Lane* __restrict__ o1) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
+    const uint64_t elem = base + i;
+    const U32x4 q02 = draw_block(kPair02, kPurAby3, tid, elem, 0, rk);   // P0 and P2
+    const U32x4 q12 = draw_block(kPair12, kPurAby3, tid, elem, 0, rk);   // P1 and P2
+    const Lane r0 = block_elem<Lane>(q02, 0) & mask;
+    const Lane rp0 = block_elem<Lane>(q02, 1) & mask;
+    Lane r1 = block_elem<Lane>(q12, 0) & mask;
+    if (fixed_r) r1 = (Lane)(fixed_r - r0) & mask;
+    // P2: r' = r / 2^k, [r']_1 = r' - [r']_0 -> P1
+    const Lane rp1 = (Lane)(sdiv_pow2<Lane>((Lane)(r0 + r1) & mask, mask, ell, k) - rp0) & mask;
+    // P0 and P1 open alpha = ([x]_0 + [r]_0) + ([x]_1 + [r]_1)
+    const Lane alpha = (Lane)((s0[i] + r0) + (s1[i] + r1)) & mask;
+    o0[i] = (Lane)(sdiv_pow2<Lane>(alpha, mask, ell, k) - rp0) & mask;
+    o1[i] = ring_neg<Lane>(rp1, mask);
+  }
+}
+
+// ---- Alg. linear: Alg. smltrc on both inputs, then the Beaver product --------
+template <typename Lane>
+__global__ void __launch_bounds__(kBlock)
+    trunc_then_mul_kernel(const RoundKeys rk, Lane mask, uint32_t kx, uint32_t ky, uint32_t tid,
+                          uint64_t base, const Lane* __restrict__ x0, const Lane* __restrict__ x1,
+                          const Lane* __restrict__ y0, const Lane* __restrict__ y1, uint64_t n,
+                          Lane* __restrict__ o0, Lane* __restrict__ o1) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
+    const Lane tx0 = x0[i] >> kx;
+    const Lane tx1 = ring_neg<Lane>((Lane)(ring_neg<Lane>(x1[i], mask) >> kx), mask);
+    const Lane ty0 = y0[i] >> ky;
+    const Lane ty1 = ring_neg<Lane>((Lane)(ring_neg<Lane>(y1[i], mask) >> ky), mask);
+    const uint64_t elem = base + i;
+    const U32x4 q0 = draw_block(kPair02, kPurMulTriple, tid, elem, 0, rk);
+    const U32x4 q1 = draw_block(kPair12, kPurMulTriple, tid, elem, 0, rk);
+    Lane a0, b0, c0;
+    if (sizeof(Lane) == 4) {
+      a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
+    } else {
+      const U32x4 q2 = draw_block(kPair02, kPurMulTriple, tid, elem, 1, rk);
+      a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
+    }
+    const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
+    a0 &= mask; b0 &= mask; c0 &= mask;
+    const Lane c1 = (Lane)((a0 + a1) * (b0 + b1) - c0) & mask;
+    const Lane d = (Lane)((tx0 - a0) + (tx1 - a1)) & mask;
+    const Lane e = (Lane)((ty0 - b0) + (ty1 - b1)) & mask;
+    o0[i] = (Lane)(d * e + d * b0 + e * a0 + c0) & mask;
+    o1[i] = (Lane)(d * b1 + e * a1 + c1) & mask;
+  }
+}
+
 // ---- truncation failures vs the plaintext ---------------------------------
 template <typename Lane>
 __global__ void __launch_bounds__(kBlock)
@@ -284,6 +353,49 @@ cudaError_t launch_mul_beaver(int ring_bits, const RoundKeys& rk, const void* x0
         static_cast<const uint32_t*>(x1), static_cast<const uint32_t*>(y0),
         static_cast<const uint32_t*>(y1), n, static_cast<uint32_t*>(o0),
         static_cast<uint32_t*>(o1));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trunc_aby3(int ring_bits, const RoundKeys& rk, int k, const void* sh0,
+                              const void* sh1, uint64_t n, uint32_t tensor_id, uint64_t fixed_r,
+                              void* o0, void* o1, int num_sms, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (ring_bits > 32) {
+    auto kern = aby3_trunc_kernel<uint64_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(
+        rk, lane_mask<uint64_t>(ring_bits), (uint32_t)ring_bits, (uint32_t)k, tensor_id, 0,
+        (uint64_t)fixed_r, static_cast<const uint64_t*>(sh0), static_cast<const uint64_t*>(sh1), n,
+        static_cast<uint64_t*>(o0), static_cast<uint64_t*>(o1));
+  } else {
+    auto kern = aby3_trunc_kernel<uint32_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(
+        rk, lane_mask<uint32_t>(ring_bits), (uint32_t)ring_bits, (uint32_t)k, tensor_id, 0,
+        (uint32_t)fixed_r, static_cast<const uint32_t*>(sh0), static_cast<const uint32_t*>(sh1), n,
+        static_cast<uint32_t*>(o0), static_cast<uint32_t*>(o1));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trunc_then_mul(int ring_bits, const RoundKeys& rk, int kx, int ky,
+                                  const void* x0, const void* x1, const void* y0, const void* y1,
+                                  uint64_t n, uint32_t tensor_id, void* o0, void* o1, int num_sms,
+                                  cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (ring_bits > 32) {
+    auto kern = trunc_then_mul_kernel<uint64_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(
+        rk, lane_mask<uint64_t>(ring_bits), (uint32_t)kx, (uint32_t)ky, tensor_id, 0,
+        static_cast<const uint64_t*>(x0), static_cast<const uint64_t*>(x1),
+        static_cast<const uint64_t*>(y0), static_cast<const uint64_t*>(y1), n,
+        static_cast<uint64_t*>(o0), static_cast<uint64_t*>(o1));
+  } else {
+    auto kern = trunc_then_mul_kernel<uint32_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(
+        rk, lane_mask<uint32_t>(ring_bits), (uint32_t)kx, (uint32_t)ky, tensor_id, 0,
+        static_cast<const uint32_t*>(x0), static_cast<const uint32_t*>(x1),
+        static_cast<const uint32_t*>(y0), static_cast<const uint32_t*>(y1), n,
+        static_cast<uint32_t*>(o0), static_cast<uint32_t*>(o1));
   }
   return cudaGetLastError();
 }

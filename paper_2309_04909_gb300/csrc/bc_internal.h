@@ -78,6 +78,16 @@ cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles
                               const BatchGroup* groups, int ngroups, unsigned int* counters,
                               int* status, int num_sms, int ctas_per_sm, cudaStream_t s);
 
+// Alg. drelu2 / RSS ReLU on replicated components x[0..2] -> y[0..2].
+cudaError_t launch_rss(const ReluConsts& k, bool relu, const void* const* x, uint64_t n,
+                       void* const* y, cudaStream_t s);
+
+// Party-separated DReLU/ReLU (three launches, messages in device buffers).
+uint64_t party_msg_words(uint32_t lx, uint64_t n);
+cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
+                           uint64_t n, void* o0, void* o1, uint32_t* w0, uint32_t* w1,
+                           void* open0, void* open1, void* reply, void* pre_c1, cudaStream_t s);
+
 cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
                          uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,
                          cudaStream_t s);
@@ -93,6 +103,13 @@ cudaError_t launch_mul_beaver(int ring_bits, const RoundKeys& rk, const void* x0
                               const void* y0, const void* y1, uint64_t n, uint32_t tensor_id,
                               uint64_t elem_base, void* o0, void* o1, int num_sms,
                               cudaStream_t s);
+cudaError_t launch_trunc_aby3(int ring_bits, const RoundKeys& rk, int k, const void* sh0,
+                              const void* sh1, uint64_t n, uint32_t tensor_id, uint64_t fixed_r,
+                              void* o0, void* o1, int num_sms, cudaStream_t s);
+cudaError_t launch_trunc_then_mul(int ring_bits, const RoundKeys& rk, int kx, int ky,
+                                  const void* x0, const void* x1, const void* y0, const void* y1,
+                                  uint64_t n, uint32_t tensor_id, void* o0, void* o1, int num_sms,
+                                  cudaStream_t s);
 cudaError_t launch_count_failures(int out_bits, int k, const int64_t* x, const void* o0,
                                   const void* o1, uint64_t n, unsigned long long* count,
                                   int num_sms, cudaStream_t s);

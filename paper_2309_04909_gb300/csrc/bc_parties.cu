@@ -1,0 +1,291 @@
+// Party-separated Bicoptor 2.0 DReLU / ReLU (Alg. drelu, Alg. relu): each
+// party's local computation is its own kernel, and every message between the
+// parties is a device buffer written by the sender's kernel and read by the
+// receiver's.  Three launches, in protocol order:
+//   1. parties_local   P0 and P1 (blockIdx.y = party), each from its own share
+//                      and its own expansion of the pre-shared seeds: steps 1-8,
+//                      w messages to P2 bit-packed at lx+1 bits per value;
+//                      ReLU: the opening [x]_j - [a]_j to the other party
+//   2. helper          P2: preprocessing [c]_1 -> P1 (ReLU); step 9 on the two
+//                      w messages; step 10 reply [DReLU']_1 -> P1 (DReLU) or
+//                      e = DReLU' - b -> P0, P1 (ReLU)
+//   3. parties_finish  P0 and P1: step 11 / the Beaver finish from the
+//                      messages they received
+// Unlike the fused kernel, P0 and P1 each expand seed01 (t, the shuffle, the
+// masks) themselves, as separate servers would.
+//
+// Packed w layout: elements in groups of 32; for slot k and group g the lx+1
+// words at (k * G + g) * (lx+1) (G = ceil(n / 32)) hold the 32 values of the
+// group, element 32 g + l at bits [l (lx+1), (l+1)(lx+1)).  The buffer is
+// exactly L * G * 32 * (lx+1) bits: the protocol's (lx+1)^2 bits per element
+// and sender, padded only in the last group.
+#include "bc_internal.h"
+
+namespace bc {
+namespace {
+
+constexpr int kPB = kBlock;             // threads per CTA
+constexpr int kWarps = kPB / 32;
+
+template <typename Lane>
+__device__ __forceinline__ Lane lane_at(const void* p, uint64_t i) {
+  return static_cast<const Lane*>(p)[i];
+}
+template <typename Lane>
+__device__ __forceinline__ void lane_put(void* p, uint64_t i, Lane v) {
+  static_cast<Lane*>(p)[i] = v;
+}
+
+// seed01: t and the Fisher-Yates shuffle (steps 1 and 6), into `perm`
+// (this thread's column of the shared table, stride kPB).
+__device__ __forceinline__ uint32_t seed01_shuffle(const ElemPhilox& ep, uint32_t L,
+                                                   uint32_t* perm, const RoundKeys& rk) {
+  for (uint32_t s = 0; s < L; ++s) perm[s * kPB] = s;
+  uint32_t t = 0;
+  const uint32_t nblk = (L + 3) >> 2;
+  for (uint32_t b = 0; b < nblk; ++b) {
+    const U32x4 wb = ep.block_at(kPair01, kPurPerm, b, rk);
+    const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t widx = 4 * b + q;
+      if (widx == 0) {
+        t = ws[0] & 1u;
+      } else if (widx < L) {
+        const uint32_t j = L - widx;
+        const uint32_t partner = __umulhi(ws[q], j + 1);
+        const uint32_t a = perm[j * kPB];
+        const uint32_t c = perm[partner * kPB];
+        perm[j * kPB] = c;
+        perm[partner * kPB] = a;
+      }
+    }
+  }
+  return t;
+}
+
+__device__ __forceinline__ uint32_t seed01_t(const ElemPhilox& ep, const RoundKeys& rk) {
+  return ep.block_at(kPair01, kPurPerm, 0, rk).x & 1u;
+}
+
+// Pack one (lx+1)-bit value per lane of the warp into the group's B words at
+// `dst` (B = lx+1 <= 32).  `stage` is this warp's 32-word shared scratch.
+__device__ __forceinline__ void warp_pack(uint32_t v, bool valid, uint32_t B, uint32_t lane,
+                                          uint32_t* stage, uint32_t* dst) {
+  stage[lane] = 0u;
+  __syncwarp();
+  if (valid) {
+    const uint32_t bit = lane * B;
+    const uint32_t w = bit >> 5, s = bit & 31u;
+    atomicOr(&stage[w], v << s);
+    if (s + B > 32u) atomicOr(&stage[w + 1], v >> (32u - s));
+  }
+  __syncwarp();
+  if (lane < B) dst[lane] = stage[lane];
+  __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t unpack(const uint32_t* src, uint32_t B, uint32_t lane) {
+  const uint32_t bit = lane * B;
+  const uint32_t w = bit >> 5, s = bit & 31u;
+  const uint64_t two = (uint64_t)src[w] | ((s + B > 32u) ? ((uint64_t)src[w + 1] << 32) : 0ull);
+  const uint32_t mask = B >= 32u ? 0xffffffffu : ((1u << B) - 1u);
+  return (uint32_t)(two >> s) & mask;
+}
+
+struct PartyArgs {
+  ReluConsts k;
+  const void* sh[2];        // [x]_0 (P0's input), [x]_1 (P1's input)
+  void* out[2];             // output shares of P0, P1
+  uint32_t* w[2];           // P0 -> P2, P1 -> P2 packed messages
+  void* open[2];            // P0 -> P1, P1 -> P0 openings (ReLU)
+  void* reply;              // P2 -> P1 / P2 -> P0, P1
+  void* pre_c1;             // P2 -> P1 preprocessing (ReLU)
+  uint64_t n;
+  uint64_t groups;          // ceil(n / 32)
+};
+
+// ---- launch 1: P0 and P1, steps 1-8 (+ opening of x - a) --------------------
+template <typename Lane, bool RELU>
+__global__ void __launch_bounds__(kPB)
+    parties_local_kernel(const PartyArgs a) {
+  __shared__ uint32_t perm_s[kMaxSlots * kPB];
+  __shared__ uint32_t stage_s[kWarps][32];
+  const uint32_t party = blockIdx.y;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
+  const bool valid = i < a.n;
+  // a warp past the end owns no group: it must not pack (the group index of
+  // every lane is its warp's, so a partial warp packs its own group only)
+  if (!__any_sync(0xffffffffu, valid)) return;
+  const uint64_t g = ((uint64_t)blockIdx.x * kPB + warp * 32u) >> 5;
+  const ReluConsts& k = a.k;
+  const uint32_t lx = k.lx, L = lx + 1, B = lx + 1;
+  const Lane mask = (Lane)k.ring_mask;
+  const uint64_t elem = k.elem_base + (valid ? i : 0);
+  const ElemPhilox ep(elem, k.tensor_id);
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint32_t t = seed01_shuffle(ep, L, perm, k.rk);
+  const Lane s = valid ? lane_at<Lane>(a.sh[party], i) : (Lane)0;
+  // steps 1-2 and the P1 pre-negation: P0 keeps [x]_0 (flipped), P1 keeps
+  // 2^l - [x]_1 of its flipped share
+  const Lane f = party == 0 ? (t ? ring_neg(s, mask) : s) : (t ? s : ring_neg(s, mask));
+  uint64_t mb = 0;
+  for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
+    const uint32_t ii = perm[slot * kPB];
+    const uint32_t sh = k.c + ii;
+    const uint32_t y = (uint32_t)((uint64_t)f >> sh);
+    const uint32_t next_mask = (ii < lx) ? k.mx : 0u;
+    uint32_t m;
+    if (party == 0) {
+      const uint32_t v = ((y & k.mx) + ((y >> 1) & next_mask) - 1u) & k.mx;   // steps 3-4
+      m = v ? v : k.two_lx;                                                  // step 5
+    } else {
+      const uint32_t v = (0u - (y & k.mx) - ((y >> 1) & next_mask)) & k.mx;
+      m = v + k.p_minus_2lx;
+    }
+    const U32x4 rz = ep.block(kPair01, kPurMask, mb, k.rk);                  // step 7
+    const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+    const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
+    uint32_t w = mont_mul(m, rho, k.mp);
+    w = party == 0 ? add_mod(w, z, k.mp.p) : sub_mod(w, z, k.mp.p);          // step 8
+    warp_pack(w, valid, B, lane, stage_s[warp], a.w[party] + (slot * a.groups + g) * B);
+  }
+  if (RELU && valid) {
+    // opening of d = x - a: P0 draws a0 from seed02, P1 draws a1 from seed12
+    const U32x4 q = ep.block_at(party == 0 ? kPair02 : kPair12, kPurReluTriple, 0, k.rk);
+    const Lane ai = block_elem<Lane>(q, 0) & mask;
+    lane_put<Lane>(a.open[party], i, (Lane)(s - ai) & mask);
+  }
+}
+
+// ---- launch 2: P2 ---------------------------------------------------------------
+template <typename Lane, bool RELU>
+__global__ void __launch_bounds__(kPB)
+    helper_kernel(const PartyArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
+  if (i >= a.n) return;
+  const ReluConsts& k = a.k;
+  const uint32_t L = k.lx + 1, B = k.lx + 1;
+  const Lane mask = (Lane)k.ring_mask;
+  const uint64_t g = i >> 5;
+  uint32_t any_zero = 0;
+  for (uint32_t slot = 0; slot < L; ++slot) {                // step 9
+    const uint64_t off = (slot * a.groups + g) * B;
+    const uint32_t w0 = unpack(a.w[0] + off, B, lane);
+    const uint32_t w1 = unpack(a.w[1] + off, B, lane);
+    any_zero |= (add_mod(w0, w1, k.mp.p) == 0u) ? 1u : 0u;
+  }
+  const ElemPhilox ep(k.elem_base + i, k.tensor_id);
+  if (!RELU) {
+    const Lane d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
+    lane_put<Lane>(a.reply, i, (Lane)((Lane)any_zero - d0) & mask);        // step 10 -> P1
+    return;
+  }
+  // P2 knows seed02 and seed12: the whole triple
+  const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
+  const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
+  Lane a0, b0, c0;
+  if (sizeof(Lane) == 4) {
+    a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
+  } else {
+    const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
+    a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
+  }
+  a0 &= mask; b0 &= mask; c0 &= mask;
+  const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
+  lane_put<Lane>(a.pre_c1, i, (Lane)((a0 + a1) * (b0 + b1) - c0) & mask);  // [c]_1 -> P1
+  lane_put<Lane>(a.reply, i, (Lane)((Lane)any_zero - b0 - b1) & mask);     // e -> P0, P1
+}
+
+// ---- launch 3: P0 and P1 finish --------------------------------------------
+template <typename Lane, bool RELU>
+__global__ void __launch_bounds__(kPB)
+    parties_finish_kernel(const PartyArgs a) {
+  const uint32_t party = blockIdx.y;
+  const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
+  if (i >= a.n) return;
+  const ReluConsts& k = a.k;
+  const Lane mask = (Lane)k.ring_mask;
+  const ElemPhilox ep(k.elem_base + i, k.tensor_id);
+  const Lane t = (Lane)seed01_t(ep, k.rk);
+  if (!RELU) {
+    // step 11: P0 has d0 from seed02, P1 the reply [DReLU']_1
+    if (party == 0) {
+      const Lane d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
+      lane_put<Lane>(a.out[0], i, t ? (Lane)((Lane)1 - d0) & mask : d0);
+    } else {
+      const Lane d1 = lane_at<Lane>(a.reply, i);
+      lane_put<Lane>(a.out[1], i, t ? ring_neg(d1, mask) : d1);
+    }
+    return;
+  }
+  const Lane e = lane_at<Lane>(a.reply, i);
+  const Lane d = (Lane)(lane_at<Lane>(a.open[0], i) + lane_at<Lane>(a.open[1], i)) & mask;
+  const Lane s = lane_at<Lane>(a.sh[party], i);
+  Lane xd;
+  if (party == 0) {
+    const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
+    Lane a0, b0, c0;
+    if (sizeof(Lane) == 4) {
+      a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
+    } else {
+      const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
+      a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
+    }
+    a0 &= mask; b0 &= mask; c0 &= mask;
+    xd = (Lane)(d * (e + b0) + e * a0 + c0) & mask;
+  } else {
+    const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
+    const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
+    xd = (Lane)(d * b1 + e * a1 + lane_at<Lane>(a.pre_c1, i)) & mask;
+  }
+  lane_put<Lane>(a.out[party], i, t ? (Lane)(s - xd) & mask : xd);
+}
+
+template <typename Lane, bool RELU>
+cudaError_t launch_parties_t(const PartyArgs& a, cudaStream_t s) {
+  const uint64_t blocks = (a.n + kPB - 1) / kPB;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+  parties_local_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  parties_finish_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint64_t party_msg_words(uint32_t lx, uint64_t n) {
+  const uint64_t groups = (n + 31) / 32;
+  return (uint64_t)(lx + 1) * groups * (lx + 1);
+}
+
+cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
+                           uint64_t n, void* o0, void* o1, uint32_t* w0, uint32_t* w1,
+                           void* open0, void* open1, void* reply, void* pre_c1, cudaStream_t s) {
+  PartyArgs a;
+  a.k = k;
+  a.sh[0] = sh0;
+  a.sh[1] = sh1;
+  a.out[0] = o0;
+  a.out[1] = o1;
+  a.w[0] = w0;
+  a.w[1] = w1;
+  a.open[0] = open0;
+  a.open[1] = open1;
+  a.reply = reply;
+  a.pre_c1 = pre_c1;
+  a.n = n;
+  a.groups = (n + 31) / 32;
+  if (k.ring_bits > 32)
+    return relu ? launch_parties_t<uint64_t, true>(a, s) : launch_parties_t<uint64_t, false>(a, s);
+  return relu ? launch_parties_t<uint32_t, true>(a, s) : launch_parties_t<uint32_t, false>(a, s);
+}
+
+}  // namespace bc

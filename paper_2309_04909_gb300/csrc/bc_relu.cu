@@ -19,8 +19,20 @@
 // element and used by both simulated parties.
 #include "bc_internal.h"
 
+// Tuning knobs of the fused kernel (compile-time): unroll of the message-slot
+// loop and the minimum resident CTAs per SM requested from the register
+// allocator (0 = let it choose).
+#ifndef BC_SLOT_UNROLL
+#define BC_SLOT_UNROLL 2
+#endif
+#ifndef BC_RELU_MIN_CTAS
+#define BC_RELU_MIN_CTAS 0
+#endif
+
 namespace bc {
 namespace {
+
+constexpr int kSlotUnroll = BC_SLOT_UNROLL;
 
 template <int LX, bool WIDE>
 struct SlotMath;
@@ -96,7 +108,9 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
 
 // Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
 // column of the shared-memory shuffle table (stride kBlock words).
-template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
+// DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
+// (the RSS protocol finishes differently).
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false>
 __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
                                                  uint32_t tensor_id, Lane s0, Lane s1,
                                                  uint64_t elem, uint32_t* perm, Lane& out0,
@@ -146,7 +160,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
   // ---- steps 3-9 over message slots k ----------------------------------------
   uint32_t any_zero = 0;
   uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
-#pragma unroll 2
+#pragma unroll kSlotUnroll
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     const uint32_t i = perm[slot * kBlock];
     const uint32_t sh = k.c + i;
@@ -177,6 +191,11 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
     any_zero |= (M::add(w0, w1, p) == 0u) ? 1u : 0u;
   }
   const uint32_t dprime = any_zero;
+  if (DPONLY) {
+    out0 = (Lane)dprime;
+    out1 = (Lane)t;
+    return;
+  }
 
   if (!RELU) {
     // step 10: [DReLU']_0 = d0 from seed02 (P0 derives it), [DReLU']_1 to P1
@@ -214,7 +233,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
 // One element per thread; the grid covers the tensor once, so the CTA
 // scheduler hands out work as CTAs retire (no static tail).
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
     relu_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
                 uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, const AuditPtrs aud) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
@@ -370,7 +389,120 @@ cudaError_t launch_group(const BatchGroup& g, const BatchTensor* tensors, const 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Alg. drelu2 (RSS DReLU) and the RSS ReLU: replicated components x0, x1, x2
+// (P0 holds 0 and 1, P1 holds 1 and 2, P2 holds 2 and 0).  Per element:
+// preprocessing [t] (zero sharing from seed012 plus t), [s] (s from seed2),
+// [s xor t] via the replicated product; Alg. drelu steps 1-9 between P0
+// ([x]_0 + [x]_1) and P1 ([x]_2); P2's d'' = s xor DReLU'; the local finish
+// and, for ReLU, the replicated product [x][DReLU].
+// ---------------------------------------------------------------------------
+
+template <typename Lane>
+__device__ __forceinline__ void draw3(const ElemPhilox& ep, uint32_t pair, uint32_t purpose,
+                                      Lane mask, const RoundKeys& rk, Lane out[3]) {
+  const U32x4 q0 = ep.block_at(pair, purpose, 0, rk);
+  if (sizeof(Lane) == 4) {
+    out[0] = (Lane)q0.x & mask;
+    out[1] = (Lane)q0.y & mask;
+    out[2] = (Lane)q0.z & mask;
+  } else {
+    const U32x4 q1 = ep.block_at(pair, purpose, 1, rk);
+    out[0] = block_elem<Lane>(q0, 0) & mask;
+    out[1] = block_elem<Lane>(q0, 1) & mask;
+    out[2] = block_elem<Lane>(q1, 0) & mask;
+  }
+}
+
+template <typename Lane>
+__device__ __forceinline__ void rss_mul3(const Lane a[3], const Lane b[3], const Lane g[3],
+                                         Lane mask, Lane out[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = i == 2 ? 0 : i + 1;
+    out[i] = (Lane)(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] - g[j]) & mask;
+  }
+}
+
+template <typename Lane, int LX, bool SHORT, bool RELU>
+__global__ void __launch_bounds__(kBlock)
+    rss_kernel(const ReluConsts k, const Lane* __restrict__ x0, const Lane* __restrict__ x1,
+               const Lane* __restrict__ x2, uint64_t n, Lane* __restrict__ y0,
+               Lane* __restrict__ y1, Lane* __restrict__ y2) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const Lane mask = (Lane)k.ring_mask;
+  const uint64_t elem = k.elem_base + i;
+  const Lane X[3] = {x0[i], x1[i], x2[i]};
+  Lane dp, t;
+  const AuditPtrs none{};
+  bicoptor_element<Lane, LX, SHORT, false, false, true>(k, k.rk, k.tensor_id,
+                                                        (Lane)(X[0] + X[1]) & mask, X[2], elem,
+                                                        perm, dp, t, none, i);
+  const ElemPhilox ep(elem, k.tensor_id);
+  Lane al[3], S[3], T[3], g[3], ST[3], Xs[3], Y[3];
+  draw3<Lane>(ep, kPair012, kPurRssT, mask, k.rk, al);
+  T[0] = (Lane)(al[0] - al[2]) & mask;
+  T[1] = (Lane)(al[1] - al[0] + t) & mask;
+  T[2] = (Lane)(al[2] - al[1]) & mask;
+  const Lane sbit = (Lane)(ep.block_at(kPair2, kPurRssS, 0, k.rk).x & 1u);
+  S[1] = block_elem<Lane>(ep.block_at(kPair012, kPurRssS, 0, k.rk), 0) & mask;
+  S[2] = block_elem<Lane>(ep.block_at(kPair12, kPurRssS, 0, k.rk), 0) & mask;
+  S[0] = (Lane)(sbit - S[1] - S[2]) & mask;                          // P2 -> P0
+  draw3<Lane>(ep, kPair012, kPurRssZ, mask, k.rk, g);
+  rss_mul3<Lane>(S, T, g, mask, ST);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Xs[j] = (Lane)(S[j] + T[j] - 2 * ST[j]) & mask;   // [s xor t]
+  const Lane dd = sbit ^ dp;                                         // d'' (P2 -> P0, P1)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Y[j] = (Lane)(Xs[j] - 2 * dd * Xs[j] + (j == 0 ? dd : 0)) & mask;
+  if (RELU) {
+    Lane gr[3], Z[3];
+    draw3<Lane>(ep, kPair012, kPurRssZr, mask, k.rk, gr);
+    rss_mul3<Lane>(X, Y, gr, mask, Z);
+    y0[i] = Z[0];
+    y1[i] = Z[1];
+    y2[i] = Z[2];
+  } else {
+    y0[i] = Y[0];
+    y1[i] = Y[1];
+    y2[i] = Y[2];
+  }
+}
+
+template <typename Lane, int LX, bool SHORT, bool RELU>
+cudaError_t launch_rss_t(const ReluConsts& k, const void* const* x, uint64_t n, void* const* y,
+                         cudaStream_t s) {
+  const uint64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid == 0) return cudaSuccess;
+  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  rss_kernel<Lane, LX, SHORT, RELU><<<(unsigned)grid, kBlock, 0, s>>>(
+      k, static_cast<const Lane*>(x[0]), static_cast<const Lane*>(x[1]),
+      static_cast<const Lane*>(x[2]), n, static_cast<Lane*>(y[0]), static_cast<Lane*>(y[1]),
+      static_cast<Lane*>(y[2]));
+  return cudaGetLastError();
+}
+
+template <typename Lane, bool RELU>
+cudaError_t launch_rss_lx(const ReluConsts& k, const void* const* x, uint64_t n, void* const* y,
+                          cudaStream_t s) {
+  if (k.lx == 24 && sizeof(Lane) == 8 && k.c + k.lx < 32)
+    return launch_rss_t<Lane, 24, true, RELU>(k, x, n, y, s);
+  return launch_rss_t<Lane, 0, false, RELU>(k, x, n, y, s);
+}
+
 }  // namespace
+
+cudaError_t launch_rss(const ReluConsts& k, bool relu, const void* const* x, uint64_t n,
+                       void* const* y, cudaStream_t s) {
+  if (k.ring_bits > 32)
+    return relu ? launch_rss_lx<uint64_t, true>(k, x, n, y, s)
+                : launch_rss_lx<uint64_t, false>(k, x, n, y, s);
+  return relu ? launch_rss_lx<uint32_t, true>(k, x, n, y, s)
+              : launch_rss_lx<uint32_t, false>(k, x, n, y, s);
+}
 
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,

@@ -300,3 +300,47 @@ def test_full_size_config2_sampled(ctx):
     ok = (rel == trc) | (rel == 0)
     assert ok.all()
     assert ((rel == np.maximum(trc, 0)).mean()) > 0.9999
+
+
+@pytest.mark.parametrize("bits,k,fixed", [(64, 16, 0), (64, 26, 1 << 26), (32, 12, 0), (16, 4, 0)])
+def test_trunc_aby3(ctx, bits, k, fixed):
+    n = 60_013
+    x = W.magnitude_bounded_ints(n, bits - 3, seed=bits + k)
+    s0, s1 = _shares(ctx, bits, x, 70)
+    o0, o1 = ctx.trunc_aby3(bits, k, s0, s1, tensor_id=71, fixed_r=fixed)
+    es0, es1 = O.share(bits, masked(x, bits), SEED, 70)
+    e0, e1 = O.trunc_aby3(bits, k, es0, es1, SEED, 71, fixed_r=fixed)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+@pytest.mark.parametrize("bits,kx,ky", [(64, 13, 13), (64, 3, 4), (32, 6, 6)])
+def test_trunc_then_mul(ctx, bits, kx, ky):
+    n = 50_021
+    x = W.magnitude_bounded_ints(n, bits // 2 - 3, seed=kx)
+    y = W.magnitude_bounded_ints(n, bits // 2 - 3, seed=ky + 100)
+    x0, x1 = _shares(ctx, bits, x, 80)
+    y0, y1 = _shares(ctx, bits, y, 81)
+    o0, o1 = ctx.trunc_then_mul(bits, kx, ky, x0, x1, y0, y1, tensor_id=82)
+    ex0, ex1 = O.share(bits, masked(x, bits), SEED, 80)
+    ey0, ey1 = O.share(bits, masked(y, bits), SEED, 81)
+    e0, e1 = O.trunc_then_mul(bits, kx, ky, ex0, ex1, ey0, ey1, SEED, 82)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+@pytest.mark.parametrize("ring,lx,c,mag,n", [(64, 24, 0, 23, 20_011), (32, 14, 4, 17, 9_999),
+                                            (32, 9, 14, 22, 4_096), (16, 5, 2, 6, 777)])
+def test_rss_parity(ctx, op, ring, lx, c, mag, n):
+    x = W.magnitude_bounded_ints(n, mag, seed=n)
+    rng = np.random.default_rng(n)
+    mk = np.uint64((1 << ring) - 1) if ring < 64 else np.uint64(2**64 - 1)
+    x0 = rng.integers(0, 2**63, n, dtype=np.uint64) & mk
+    x1 = rng.integers(0, 2**63, n, dtype=np.uint64) & mk
+    x2 = (x.astype(np.uint64) - x0 - x1) & mk
+    fn = ctx.rss_drelu if op == "drelu" else ctx.rss_relu
+    ys = fn(Params(ring, lx, c), to_dev(x0, ring), to_dev(x1, ring), to_dev(x2, ring), tensor_id=9)
+    e = O.rss_drelu(O.params(ring, lx, c), x0, x1, x2, SEED, 9, relu=(op == "relu"), threads=8)
+    for g, w in zip(ys, e[:3]):
+        assert np.array_equal(to_np(g).astype(np.uint64), w)

@@ -39,6 +39,12 @@ MUTANTS = {
     "philox_key_bump_order": ("if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }",
                               "{ k0 += PHILOX_W0; k1 += PHILOX_W1; }"),
     "share_sign": ("*s1 = rneg(r, ell);", "*s1 = rmod(r, ell);"),
+    "rss_xor_dropped_product": ("X[j] = rmod(S[j] + T[j] - 2 * ST[j], ell);",
+                                "X[j] = rmod(S[j] + T[j], ell);"),
+    "rss_zero_sharing_sign": ("out[i] = rmod(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] - g[j], ell);",
+                              "out[i] = rmod(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] + g[j], ell);"),
+    "aby3_signed_division": ("if (ell < 128 && (v >> (ell - 1)) & 1) v -= ((__int128)1 << ell);",
+                             "if (0) v -= ((__int128)1 << ell);"),
 }
 
 

@@ -437,3 +437,124 @@ def test_stream_layout():
     for j in range(9):
         ctr = [elem & 0xFFFFFFFF, tid, j // 4, (pair << 24) | (pur << 16) | (elem >> 32)]
         assert O.stream_word(seed, pair, pur, tid, elem, j) == O.philox(ctr, key)[j % 4]
+
+
+# --------------------------------------------------------------------------
+# Alg. aby3trc and Alg. linear (Sec. 2.4, Sec. 4)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_aby3_failure_law_exhaustive_l8(k):
+    """Sec. 3: ABY3 truncation fails (e1) exactly when alpha = x + r leaves
+    the signed range, i.e. for |x| of the 2^l values of r."""
+    for x in range(-100, 101):
+        fails = 0
+        for r in range(256):
+            r0 = (r * 37 + 11) & 255           # any split of r works
+            s0, s1 = O.share_with_r(8, x & 255, (r * 91 + 5) & 255)
+            o0, o1 = O.aby3_core(8, k, s0, s1, r0, (r - r0) & 255, (r * 13) & 255)
+            res = (o0 + o1) & 255
+            res = res - 256 if res >= 128 else res
+            fails += abs(res - (x >> k)) > 1
+        assert fails == abs(x), (x, k, fails)
+
+
+def test_aby3_fixed_r_hides_e1_and_random_r_does_not():
+    """Sec. 4.1: with r fixed to 2^26 no e1 occurs for |x| < 2^62 (the
+    implementation shortcut that hid the error); with uniform r the failure
+    count matches sum |x| / 2^64 (within 5 sigma)."""
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(1 << 18, 62, seed=26)
+    x = xs.astype(np.uint64)
+    s0, s1 = O.share(64, x, seed=3, tid=1)
+    want = xs >> 26
+    for fixed, expect_zero in ((1 << 26, True), (0, False)):
+        o0, o1 = O.trunc_aby3(64, 26, s0, s1, seed=4, tid=2, fixed_r=fixed)
+        res = O.to_signed(O.reconstruct(64, o0, o1), 64)
+        fails = int((np.abs(res.astype(object) - want.astype(object)) > 1).sum())
+        if expect_zero:
+            assert fails == 0
+        else:
+            p = np.abs(xs).astype(np.float64) / 2.0 ** 64
+            assert abs(fails - p.sum()) < 5 * math.sqrt((p * (1 - p)).sum()) + 1
+            assert fails > 1000
+
+
+def test_truncate_then_multiply_exact_composition():
+    """Alg. linear: shares reconstruct to trc(x, kx) * trc(y, ky) where each
+    truncation is Alg. smltrc's (the Beaver product is exact), and the result
+    stays within (|x| + |y|) / 2^(f/2) + 1 of x y / 2^f for in-range inputs,
+    where multiply-then-truncate at l = 64 with f = 26 fails often."""
+    from paper_2309_04909_gb300 import workloads as W
+    f = 26
+    X = W.gaussian_reals(20000, 4.0, seed=5, stream=0)
+    Y = W.gaussian_reals(20000, 4.0, seed=5, stream=1)
+    xi = np.rint(np.ldexp(X, f)).astype(np.int64)
+    yi = np.rint(np.ldexp(Y, f)).astype(np.int64)
+    x0, x1 = O.share(64, xi.astype(np.uint64), seed=6, tid=1)
+    y0, y1 = O.share(64, yi.astype(np.uint64), seed=6, tid=2)
+    kx, ky = f // 2, f - f // 2
+    o0, o1 = O.trunc_then_mul(64, kx, ky, x0, x1, y0, y1, seed=7, tid=3)
+    tx0, tx1 = O.trunc_prob(64, kx, x0, x1)
+    ty0, ty1 = O.trunc_prob(64, ky, y0, y1)
+    tx = O.to_signed(O.reconstruct(64, tx0, tx1), 64).astype(object)
+    ty = O.to_signed(O.reconstruct(64, ty0, ty1), 64).astype(object)
+    got = O.to_signed(O.reconstruct(64, o0, o1), 64).astype(object)
+    assert (got == (tx * ty)).all() or all(((g - a * b) % 2**64) == 0 for g, a, b in zip(got, tx, ty))
+    exact = [(int(a) * int(b)) / 2.0 ** f for a, b in zip(xi, yi)]
+    bound = [(abs(int(a)) + abs(int(b))) / 2.0 ** (f // 2) + 2 for a, b in zip(xi, yi)]
+    assert all(abs(float(g) - e) <= bd for g, e, bd in zip(got, exact, bound))
+
+
+# --------------------------------------------------------------------------
+# Alg. drelu2 (RSS) and the RSS ReLU
+# --------------------------------------------------------------------------
+
+def test_rss_drelu_bruteforce_l8():
+    """Every x in Z_{2^8}, 24 replicated splits each: the three output
+    components reconstruct to DReLU' xor t, DReLU' is Thm. newtrc2's closed
+    form on x = x0 + x1 + x2 split as (x0 + x1, x2), and the sign is right
+    outside the exception set (lx = 4, c = 0: xi* = 10)."""
+    ell, lx, c, m = 8, 4, 0, 255
+    P = O.params(ell, lx, c)
+    rng = np.random.default_rng(9)
+    X = np.repeat(np.arange(256, dtype=np.uint64), 24)
+    a = rng.integers(0, 256, X.size, dtype=np.uint64)
+    b = rng.integers(0, 256, X.size, dtype=np.uint64)
+    x0, x1, x2 = a, b, (X - a - b) & np.uint64(m)
+    seed, tid = 11, 3
+    y0, y1, y2, dp = O.rss_drelu(P, x0, x1, x2, seed, tid)
+    t = np.array([O.stream_word(seed, O.PAIR_01, O.PUR_PERM, tid, e, 0) & 1 for e in range(X.size)],
+                 dtype=np.uint64)
+    rec = (y0 + y1 + y2) & np.uint64(m)
+    assert (rec == (dp.astype(np.uint64) ^ t)).all()
+    # DReLU' on the 2-of-2 split (x0 + x1, x2) after the flip by t
+    s0 = (x0 + x1) & np.uint64(m)
+    neg = lambda v: (np.uint64(0) - v) & np.uint64(m)
+    fs0, fs1 = np.where(t == 1, neg(s0), s0), np.where(t == 1, neg(x2), x2)
+    assert (dp.astype(bool) == _closed_form_dprime(ell, lx, c, fs0, fs1)).all()
+    xs = np.where(X >= 128, X.astype(np.int64) - 256, X.astype(np.int64))
+    dom = (np.abs(xs) < 16) & (xs != 0)
+    bad = dom & (rec != (xs >= 0))
+    assert set(np.abs(xs[bad]).tolist()) <= _c0_exceptions(lx)
+
+
+def test_rss_relu_exact_product():
+    from paper_2309_04909_gb300 import workloads as W
+    for ell, lx, c, bits in ((64, 24, 0, 23), (32, 14, 4, 17)):
+        P = O.params(ell, lx, c)
+        mk = np.uint64((1 << ell) - 1)
+        xs = W.magnitude_bounded_ints(4000, bits, seed=ell)
+        rng = np.random.default_rng(ell)
+        x0 = rng.integers(0, 2**63, xs.size, dtype=np.uint64) & mk
+        x1 = rng.integers(0, 2**63, xs.size, dtype=np.uint64) & mk
+        x2 = (xs.astype(np.uint64) - x0 - x1) & mk
+        d0, d1, d2, dp = O.rss_drelu(P, x0, x1, x2, 4, 5)
+        r0, r1, r2, dp2 = O.rss_drelu(P, x0, x1, x2, 4, 5, relu=True)
+        assert (dp == dp2).all()
+        b = ((d0 + d1 + d2) & mk).astype(object)
+        rec = ((r0 + r1 + r2) & mk).astype(object)
+        assert (rec == (xs.astype(object) * b) % (1 << ell)).all()
+        signed = O.to_signed((r0 + r1 + r2) & mk, ell)
+        miss = np.abs(xs[signed != np.maximum(xs, 0)])
+        assert all(_predicted_miss(int(v), lx, c) for v in miss)
