@@ -204,7 +204,11 @@ def main():
         if ev is not None:
             ev[0].record()
         ctx.mul_beaver(RING, x0, x1, y0, y1, 3, out=(buf["prod0"], buf["prod1"]))
+        if ev is not None:
+            ev[3].record()
         ctx.trunc_prob(RING, K_TRUNC, buf["prod0"], buf["prod1"], out=(buf["trc0"], buf["trc1"]))
+        if ev is not None:
+            ev[4].record()
         ctx.trunc_det(RING, K_TRUNC, 0, buf["prod0"], buf["prod1"], out=(buf["det0"], buf["det1"]))
         if ev is not None:
             ev[1].record()
@@ -215,7 +219,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
@@ -234,6 +238,16 @@ def main():
     relu_ms = [e[1].elapsed_time(e[2]) for e in evs]
     pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
     relu_avg = sum(relu_ms) / len(relu_ms)
+    mean = lambda xs: sum(xs) / len(xs)
+    mul_ms = mean([e[0].elapsed_time(e[3]) for e in evs])
+    tp_ms = mean([e[3].elapsed_time(e[4]) for e in evs])
+    td_ms = mean([e[4].elapsed_time(e[1]) for e in evs])
+    hbm_peak = 6793.4   # GB/s, measured STREAM-style copy on the GB300s
+
+    def hbm(ms, bytes_per_elem):
+        gbs = bytes_per_elem * n / (ms / 1e3) / 1e9
+        return {"ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
+                "bytes_per_element": bytes_per_elem}
     value = n * args.steps * world / (total_ms / 1e3)
     ops = costmodel.int_ops_per_element(LX, RING, relu=True)
     muls = costmodel.mul_ops_per_element(LX, RING, relu=True)
@@ -252,7 +266,10 @@ def main():
                    "l2": "working set 384 MB per step > 129 MB L2; no flush"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
-                     "traffic": None,
+                     # DRAM bytes per launch: ncu dram__bytes_read+write of this kernel at
+                     # 2^21 elements (profiles/relu_kernel_config2_full.md), 16.14 B per
+                     # element, scaled to this launch's n
+                     "traffic": 16.14 * n,
                      "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
                      "mul_ops_per_element": muls, "kernel_ms": relu_avg,
                      "peak_basis": "integer multiplier: 152 SM x 4 x 16-lane FMA-heavy pipe "
@@ -264,6 +281,8 @@ def main():
         "clocks": ck,
         "step_breakdown_ms": {"product_and_truncations": sum(pre_ms) / len(pre_ms),
                               "relu": relu_avg},
+        "hbm_kernels": {"mul_beaver": hbm(mul_ms, 48), "trunc_prob": hbm(tp_ms, 32),
+                        "trunc_det": hbm(td_ms, 32)},
     }
 
     if rank == 0 and not args.no_extras:
@@ -277,6 +296,7 @@ def main():
                                     "sample": f"first {m2} elements of the workload, full step "
                                               f"(share, product, both truncations, ReLU), {dt:.1f} s"}
         line["party_separated"] = parties_bench(ctx, prm, buf, n, relu_avg)
+        line["rss_relu"] = rss_bench(ctx, prm, buf, n)
         line["config1"] = config1_check(ctx, dev)
         line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
         line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
@@ -448,6 +468,25 @@ def linear_trunc_table(ctx, dev, n=1 << 22):
         row["trc_then_mult_e1_scale_errors"] = int((rec.abs() > (1 << 20)).sum().item())
         out[f"f={f}"] = row
     return out
+
+
+def rss_bench(ctx, prm, buf, n):
+    """Alg. drelu2 + the replicated ReLU product on 2-of-3 replicated shares
+    of the same truncated product (components trc0, 0, trc1)."""
+    import torch
+    z = torch.zeros_like(buf["trc0"])
+    ys = tuple(torch.empty_like(buf["trc0"]) for _ in range(3))
+    for _ in range(3):
+        ctx.rss_relu(prm, buf["trc0"], z, buf["trc1"], 4, out=ys)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        ctx.rss_relu(prm, buf["trc0"], z, buf["trc1"], 4, out=ys)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    return {"kernel_ms": ms, "elems_per_s": n / (ms / 1e3)}
 
 
 def parties_bench(ctx, prm, buf, n, fused_ms):
