@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window of each serving run (60 s in the full trace)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving trace at the offered 2,000 req/s and print it")
     return ap.parse_args()
 
 
@@ -183,6 +185,9 @@ def main():
     from paper_2309_04909_gb300 import Context, Params, costmodel
     from paper_2309_04909_gb300.replicas import max_over_ranks, rank_seed
 
+    if args.serving_only:
+        serving_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -273,7 +278,7 @@ def main():
                      "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
                      "mul_ops_per_element": muls, "kernel_ms": relu_avg,
                      "peak_basis": "integer multiplier: 152 SM x 4 x 16-lane FMA-heavy pipe "
-                                   "x 2070 MHz (derived, see DESIGN.md)",
+                                   "x 2070 MHz (maximum SM clock)",
                      "int_ops_per_element": ops,
                      "issue_frac": issue_frac,
                      "hbm_bytes_per_element": costmodel.hbm_bytes_per_element_relu(RING)},
@@ -297,7 +302,7 @@ def main():
                                               f"(share, product, both truncations, ReLU), {dt:.1f} s"}
         line["party_separated"] = parties_bench(ctx, prm, buf, n, relu_avg)
         line["rss_relu"] = rss_bench(ctx, prm, buf, n)
-        line["config1"] = config1_check(ctx, dev)
+        line["drelu_l32_uniform"] = uniform_l32_drelu_check(ctx, dev)
         line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
         line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
         line["serving"] = serving_bench(ctx, dev, bvp["batched_elems_per_s"],
@@ -381,7 +386,7 @@ def b_persist_ms(ctx, items):
 
 
 def vgg16_batched_vs_plain(ctx, dev, batch=128):
-    """Config-3 shape: the 13 ReLU tensors of a VGG-16 on 32x32 inputs for
+    """The 13 ReLU tensors of a VGG-16 on 32x32 inputs for
     `batch` images (1,664 tensors, 35,389,440 elements at batch 128), l = 64,
     f = 16, per-layer sigma in [0.5, 8].  Plain = one launch per tensor
     (eager, and replayed from a CUDA graph); batched = one persistent launch
@@ -514,8 +519,8 @@ def parties_bench(ctx, prm, buf, n, fused_ms):
             "identical_to_fused": same, "launches": 3}
 
 
-def config1_check(ctx, dev):
-    """Config 1: DReLU of 65,536 uniform reals in [-1000, 1000] (f = 12) in
+def uniform_l32_drelu_check(ctx, dev):
+    """DReLU of 65,536 uniform reals in [-1000, 1000] (f = 12) in
     Z_{2^32}, (lx, c) = (9, 14).  Checks every element against the oracle
     (bit-exact shares) and the reconstructed sign against the plaintext; every
     mismatch must lie in the predicted set |x| < 2^c or the band around
@@ -558,7 +563,7 @@ def config1_check(ctx, dev):
 
 
 def resnet18_batched(ctx, dev, batch=32):
-    """Config-4 shape: ResNet-18 224x224 ReLU set for `batch` images, once at
+    """The ResNet-18 224x224 ReLU set for `batch` images, once at
     l = 64 (f = 16, lx = 24) and once at l = 32 (f = 12, (lx, c) = (14, 4)),
     Laplace(0, 2) activations: 1,088 tensors, 147,718,144 elements.  One
     CUDA-graph-captured batched run (one launch per parameter group) vs one
@@ -611,6 +616,28 @@ def resnet18_batched(ctx, dev, batch=32):
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "status": b.status(), "identical_to_plain": bool(identical)}
+
+
+def serving_only(args):
+    """The serving workload alone: Poisson 2,000 req/s for --serve-seconds,
+    1-64 images per request, 50/50 LeNet / VGG-16 ReLU sets, l = 64, f = 16,
+    40 GB admission budget, seed 4."""
+    import torch
+    from paper_2309_04909_gb300 import Context, Params, workloads as W
+    from paper_2309_04909_gb300.serve import Engine, ServingSetup
+    dev = torch.device("cuda", 0)
+    ctx = Context(0xB1C0_5E12, device=0)
+    budget = 40 << 30
+    setup = ServingSetup(ctx, Params(64, 24, 0), budget, seed=4, pool_images=64)
+    trace = W.serving_trace(2000.0, args.serve_seconds, seed=4)
+    reqs = setup.requests_from_trace(trace)
+    st = Engine(setup.executor(schedule=1), budget, max_iter_elems=1 << 24).run(reqs)
+    s = st.summary()
+    s.update({"metric": METRIC, "workload": f"serving: Poisson 2000 req/s x {args.serve_seconds} s, "
+                                            "1-64 images, LeNet/VGG-16 50/50, l=64 f=16",
+              "offered_elems_per_s": sum(r.elements for r in reqs) / args.serve_seconds})
+    print(json.dumps(s), flush=True)
+    ctx.close()
 
 
 def serving_bench(ctx, dev, capacity, seconds, bvp, budget=40 << 30):

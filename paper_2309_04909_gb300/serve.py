@@ -92,6 +92,11 @@ class ServeRequest:
     retired: int = 0                    # elements whose iteration finished
     admitted_s: Optional[float] = None
     finished_s: Optional[float] = None
+    # optional client limits on the engine clock (seconds): a request not
+    # finished by its deadline expires, one past cancel_at_s is cancelled
+    deadline_s: Optional[float] = None
+    cancel_at_s: Optional[float] = None
+    dropped: Optional[str] = None       # "expired" or "cancelled"
 
     @property
     def latency_s(self) -> Optional[float]:
@@ -139,6 +144,8 @@ class ServeStats:
     peak_bytes: int
     max_waiting: int
     rejected: int = 0
+    expired: int = 0
+    cancelled: int = 0
 
     def summary(self) -> Dict[str, float]:
         lat = sorted(self.latencies_s)
@@ -155,7 +162,8 @@ class ServeStats:
                 "p99_ms": None if not lat else 1e3 * pct(0.99),
                 "max_ms": None if not lat else 1e3 * lat[-1],
                 "iterations": self.iterations, "peak_bytes": self.peak_bytes,
-                "max_waiting": self.max_waiting, "rejected": self.rejected}
+                "max_waiting": self.max_waiting, "rejected": self.rejected,
+                "expired": self.expired, "cancelled": self.cancelled}
 
 
 class Engine:
@@ -175,7 +183,7 @@ class Engine:
         left: each gets an equal quantum of the iteration (small requests
         finish in their first iteration); what the quanta leave unused goes
         to the oldest requests first."""
-        live = [r for r in active if r.elements > r.done][:self.max_share]
+        live = [r for r in active if r.elements > r.done and r.dropped is None][:self.max_share]
         if not live:
             return []
         budget = self.max_iter_elems
@@ -224,6 +232,16 @@ class Engine:
                 else:
                     waiting.append(r)
             max_waiting = max(max_waiting, len(waiting))
+            # client limits: drop queued requests at once; an admitted one
+            # stops getting chunks and is freed when its chunks in flight retire
+            for r in list(waiting) + active:
+                if r.dropped is None:
+                    if r.cancel_at_s is not None and now >= r.cancel_at_s:
+                        r.dropped = "cancelled"
+                    elif r.deadline_s is not None and now >= r.deadline_s:
+                        r.dropped = "expired"
+            if any(r.dropped for r in waiting):
+                waiting = collections.deque(r for r in waiting if r.dropped is None)
             # admission: FIFO while the output shares fit in the budget
             while waiting:
                 r = waiting[0]
@@ -246,7 +264,16 @@ class Engine:
                             on_complete(c.req)
                         self.arena.free(c.req.offset, c.req.elements * out_b)
                 progressed = True
-            active = [r for r in active if r.retired < r.elements]
+            # a dropped request leaves once nothing of it is in flight
+            keep = []
+            for r in active:
+                if r.dropped is not None and r.retired == r.done and r.finished_s is None:
+                    self.arena.free(r.offset, r.elements * out_b)
+                    r.offset = None
+                    progressed = True
+                elif r.retired < r.elements and not (r.dropped is not None and r.offset is None):
+                    keep.append(r)
+            active = keep
             # launch the next iteration over the admitted requests' next chunks
             if len(inflight) < self.max_inflight:
                 chunks = self._plan_iteration(active)
@@ -261,8 +288,10 @@ class Engine:
                     self.ex.sleep_until(t0 + pending[0].arrival_s)
         wall = self.ex.now() - t0
         lat = [r.latency_s for r in requests if r.latency_s is not None]
+        expired = sum(1 for r in requests if r.dropped == "expired" and r.finished_s is None)
+        cancelled = sum(1 for r in requests if r.dropped == "cancelled" and r.finished_s is None)
         return ServeStats(len(requests), len(lat), done_elems, wall, lat, iterations,
-                          self.arena.peak, max_waiting, rejected)
+                          self.arena.peak, max_waiting, rejected, expired, cancelled)
 
 
 # ---------------------------------------------------------------------------

@@ -214,7 +214,7 @@ def test_count_trunc_failures(ctx):
 
 
 def test_linear_relu_chain(ctx):
-    """Config-2-shaped chain at reduced size: product, both truncations and
+    """Product -> truncation -> ReLU chain at reduced size: product, both truncations and
     the ReLU of the prob-truncated product, device and host-buffer paths."""
     n, f, k = 50_021, 16, 16
     X = W.gaussian_reals(n, 4.0, seed=1, stream=0)

@@ -100,3 +100,31 @@ def test_summary_percentiles():
     s = st.summary()
     assert s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
     assert s["completed"] == 50
+
+
+def test_engine_cancellation_and_deadlines():
+    """Requests cancelled by the client or past their deadline are dropped:
+    queued ones at once, admitted ones once their chunks in flight retire;
+    their memory returns to the arena and every other request completes."""
+    rng = random.Random(3)
+    reqs = []
+    for i in range(200):
+        r = ServeRequest(i, 1e-4 * i, rng.randrange(500_000, 3_000_000))
+        if i % 10 == 3:
+            r.cancel_at_s = r.arrival_s + 2e-4
+        if i % 10 == 7:
+            r.deadline_s = r.arrival_s + 1e-3
+        reqs.append(r)
+    ex = FakeExecutor(rate_elems_per_s=2e9)          # overloaded: deadlines bite
+    eng = Engine(ex, 2 << 30, max_iter_elems=1 << 22)
+    st = eng.run(reqs)
+    assert eng.arena.used == 0
+    dropped = [r for r in reqs if r.dropped and r.finished_s is None]
+    assert st.cancelled + st.expired == len(dropped) > 0
+    assert st.completed + len(dropped) == len(reqs)
+    assert all(r.finished_s is not None for r in reqs if r.dropped is None)
+    for r in reqs:
+        if r.dropped == "expired" and r.finished_s is None:
+            assert r.deadline_s is not None
+    # no chunk of a dropped request was launched after it was dropped
+    assert all(r.done <= r.elements for r in reqs)
