@@ -290,16 +290,17 @@ def main():
                         "trunc_det": hbm(td_ms, 32)},
     }
 
-    if rank == 0 and not args.no_extras:
+    # the long extras run in the single-GPU run only (N > 1 runs measure the
+    # scaled step; every rank's GPU would otherwise be held for minutes)
+    if rank == 0 and world == 1 and not args.no_extras:
         line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), dev)
         line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
         line["linear_layer_truncation"] = linear_trunc_table(ctx, dev)
-        if world == 1:
-            rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
-            line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
-                                    "kind": "oracle",
-                                    "sample": f"first {m2} elements of the workload, full step "
-                                              f"(share, product, both truncations, ReLU), {dt:.1f} s"}
+        rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
+        line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
+                                "kind": "oracle",
+                                "sample": f"first {m2} elements of the workload, full step "
+                                          f"(share, product, both truncations, ReLU), {dt:.1f} s"}
         line["party_separated"] = parties_bench(ctx, prm, buf, n, relu_avg)
         line["rss_relu"] = rss_bench(ctx, prm, buf, n)
         line["drelu_l32_uniform"] = uniform_l32_drelu_check(ctx, dev)
