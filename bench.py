@@ -31,6 +31,9 @@ WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs ->
 N_DEFAULT = 1 << 22
 RING, FRAC, K_TRUNC, LX, KEY_OFF = 64, 16, 16, 24, 0
 SEED = 1
+# DRAM bytes per element of the fused step kernel: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one 2^21-element launch (90.39 MB) / its elements
+TRAFFIC_PER_ELEM = 43.10
 
 
 def parse():
@@ -87,6 +90,50 @@ def cpu_rate(n_target_s: float, xi, yi, threads):
     oracle_chain(xi[:m2], yi[:m2], 77, threads)
     dt = time.perf_counter() - t0
     return m2 / dt, m2, dt
+
+
+def cpu_configs(threads: int, min_elems: int = 10_000_000):
+    """The oracle's ReLU (OpenMP over `threads` cores) on at least `min_elems`
+    elements of the batched workloads, extrapolated linearly to their full
+    size: the VGG-16 32x32 set of 128 images (l = 64, lx = 24, c = 0) and both
+    rings of the ResNet-18 224x224 set of 32 images (l = 64; l = 32 with
+    lx = 14, c = 4)."""
+    import oracle as O
+    from paper_2309_04909_gb300 import workloads as W
+    out = {}
+
+    def sample(ts, ring, frac, full):
+        xs, m = [], 0
+        for r, rb in zip(ts.reals, ts.ring_bits):
+            if rb != ring:
+                continue
+            xs.append(np.rint(np.ldexp(r, frac)).astype(np.int64))
+            m += r.size
+            if m >= min_elems:
+                break
+        x = np.concatenate(xs)
+        return x, full
+
+    # the first images of each set are the same as in the full batch (per-image
+    # streams), so only as many images as the sample needs are generated
+    per_vgg, per_res = sum(W.VGG16_32_LAYERS), sum(W.RESNET18_224_LAYERS)
+    vgg = W.vgg16_batch(-(-min_elems // per_vgg), seed=2)
+    res = W.resnet18_mixed_batch(-(-min_elems // per_res), seed=3)
+    for name, ts, ring, frac, lx, c, full in (
+            ("vgg16_l64", vgg, 64, 16, 24, 0, 128 * per_vgg),
+            ("resnet18_l64", res, 64, 16, 24, 0, 32 * per_res),
+            ("resnet18_l32", res, 32, 12, 14, 4, 32 * per_res)):
+        x, full = sample(ts, ring, frac, full)
+        idx = np.arange(x.size, dtype=np.uint64)
+        s0, s1 = O.share(ring, (x.astype(np.uint64) & np.uint64((1 << ring) - 1)
+                                if ring < 64 else x.astype(np.uint64)), 9, 1, idx=idx)
+        t0 = time.perf_counter()
+        O.relu(O.params(ring, lx, c), s0, s1, 9, 2, idx=idx, threads=threads)
+        dt = time.perf_counter() - t0
+        out[name] = {"elems_per_s": x.size / dt, "sample_elems": int(x.size), "seconds": dt,
+                     "full_elems": int(full), "full_seconds_extrapolated": full * dt / x.size}
+    out["cores"] = threads
+    return out
 
 
 def run_reference(args):
@@ -203,28 +250,18 @@ def main():
     y0, y1 = ctx.share(RING, torch.from_numpy(yi).to(dev), tensor_id=2)
     prm = Params(RING, LX, KEY_OFF)
     buf = ctx.linear_relu_buffers(RING, K_TRUNC, n)
+    # the step's outputs: the ReLU of the SecureML-truncated product and the
+    # deterministic truncation; product and truncated shares stay in registers
+    work = {nm: buf[nm] for nm in ("det0", "det1", "relu0", "relu1")}
     torch.cuda.synchronize()
 
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record()
-        ctx.mul_beaver(RING, x0, x1, y0, y1, 3, out=(buf["prod0"], buf["prod1"]))
-        if ev is not None:
-            ev[3].record()
-        ctx.trunc_prob(RING, K_TRUNC, buf["prod0"], buf["prod1"], out=(buf["trc0"], buf["trc1"]))
-        if ev is not None:
-            ev[4].record()
-        ctx.trunc_det(RING, K_TRUNC, 0, buf["prod0"], buf["prod1"], out=(buf["det0"], buf["det1"]))
-        if ev is not None:
-            ev[1].record()
-        ctx.relu(prm, buf["trc0"], buf["trc1"], 4, out=(buf["relu0"], buf["relu1"]))
-        if ev is not None:
-            ev[2].record()
+    def step():
+        ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=work)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
@@ -233,32 +270,22 @@ def main():
     torch.cuda.synchronize()
     start.record()
     for s in range(args.steps):
-        step(evs[s])
+        evs[s][0].record()
+        step()
+        evs[s][1].record()
     end.record()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ck = clocks.stop() if clocks else None
     total_ms = max_over_ranks(start.elapsed_time(end), device=dev)
-    relu_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    relu_avg = sum(relu_ms) / len(relu_ms)
-    mean = lambda xs: sum(xs) / len(xs)
-    mul_ms = mean([e[0].elapsed_time(e[3]) for e in evs])
-    tp_ms = mean([e[3].elapsed_time(e[4]) for e in evs])
-    td_ms = mean([e[4].elapsed_time(e[1]) for e in evs])
-    hbm_peak = 6793.4   # GB/s, measured STREAM-style copy on the GB300s
-
-    def hbm(ms, bytes_per_elem):
-        gbs = bytes_per_elem * n / (ms / 1e3) / 1e9
-        return {"ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
-                "bytes_per_element": bytes_per_elem}
+    kern_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / len(evs)
     value = n * args.steps * world / (total_ms / 1e3)
-    ops = costmodel.int_ops_per_element(LX, RING, relu=True)
-    muls = costmodel.mul_ops_per_element(LX, RING, relu=True)
+    ops = costmodel.linear_relu_int_ops_per_element(LX, RING)
+    muls = costmodel.linear_relu_mul_ops_per_element(LX, RING)
     peak = costmodel.int_mul_peak_ops()
-    achieved = muls * n / (relu_avg / 1e3)
-    issue_frac = ops * n / (relu_avg / 1e3) / costmodel.int_issue_peak_ops()
+    achieved = muls * n / (kern_ms / 1e3)
+    issue_frac = ops * n / (kern_ms / 1e3) / costmodel.int_issue_peak_ops()
 
     line = {
         "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
@@ -268,40 +295,43 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "ring_bits": RING, "frac_bits": FRAC,
                    "trunc_bits": K_TRUNC, "lx": LX, "key_off": KEY_OFF, "p": 16777259,
                    "parallelism": f"replicas x{world}",
-                   "l2": "working set 384 MB per step > 129 MB L2; no flush"},
+                   "l2": "working set 268 MB per step > 129 MB L2; no flush"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
-                     # DRAM bytes per launch: ncu dram__bytes_read+write of this kernel at
-                     # 2^21 elements (profiles/relu_kernel_config2_full.md), 16.14 B per
-                     # element, scaled to this launch's n
-                     "traffic": 16.14 * n,
-                     "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
-                     "mul_ops_per_element": muls, "kernel_ms": relu_avg,
+                     # DRAM bytes per launch: ncu dram__bytes_read+write of this kernel
+                     # per element, scaled to this launch's n
+                     "traffic": TRAFFIC_PER_ELEM * n if TRAFFIC_PER_ELEM else None,
+                     "kernel": "linear_relu_kernel<uint64_t,24,SHORT>",
+                     "mul_ops_per_element": muls, "kernel_ms": kern_ms,
                      "peak_basis": "integer multiplier: 152 SM x 4 x 16-lane FMA-heavy pipe "
                                    "x 2070 MHz (maximum SM clock)",
                      "int_ops_per_element": ops,
                      "issue_frac": issue_frac,
-                     "hbm_bytes_per_element": costmodel.hbm_bytes_per_element_relu(RING)},
-        "gpu_launches": 4 * args.steps,
+                     "hbm_bytes_per_element": costmodel.hbm_bytes_per_element_linear_relu(RING)},
+        "gpu_launches": args.steps,
         "clocks": ck,
-        "step_breakdown_ms": {"product_and_truncations": sum(pre_ms) / len(pre_ms),
-                              "relu": relu_avg},
-        "hbm_kernels": {"mul_beaver": hbm(mul_ms, 48), "trunc_prob": hbm(tp_ms, 32),
-                        "trunc_det": hbm(td_ms, 32)},
     }
 
     # the long extras run in the single-GPU run only (N > 1 runs measure the
     # scaled step; every rank's GPU would otherwise be held for minutes)
     if rank == 0 and world == 1 and not args.no_extras:
-        line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), dev)
+        # every intermediate of the step, for the extras that read them
+        ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
+        line["unfused_chain"] = chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms)
+        line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf)
         line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
         line["linear_layer_truncation"] = linear_trunc_table(ctx, dev)
         rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
+        rate1, m1, dt1 = cpu_rate(max(2.0, args.cpu_seconds / 5), xi, yi, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
                                 "kind": "oracle",
                                 "sample": f"first {m2} elements of the workload, full step "
-                                          f"(share, product, both truncations, ReLU), {dt:.1f} s"}
-        line["party_separated"] = parties_bench(ctx, prm, buf, n, relu_avg)
+                                          f"(share, product, both truncations, ReLU), {dt:.1f} s",
+                                "single_thread": {"value": rate1, "sample_elems": m1,
+                                                  "seconds": dt1}}
+        line["cpu_baseline_batched_configs"] = cpu_configs(_threads())
+        line["party_separated"] = parties_bench(ctx, prm, buf, n,
+                                                line["unfused_chain"]["relu_ms"])
         line["rss_relu"] = rss_bench(ctx, prm, buf, n)
         line["drelu_l32_uniform"] = uniform_l32_drelu_check(ctx, dev)
         line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
@@ -320,35 +350,87 @@ def _threads():
     return O.max_threads()
 
 
-def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, dev):
-    """The same step through the host-buffer entry point: pinned host inputs,
-    copies in, compute, copies out, inside the timed region."""
+def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms):
+    """The step as four separate launches (Beaver product, the two
+    truncations, ReLU) through HBM, each kernel timed with CUDA events, and
+    checked bit for bit against the fused kernel's outputs."""
+    import torch
+    hbm_peak = 6793.4   # GB/s, measured STREAM-style copy on this pool's GB300s
+    q = {nm: torch.empty_like(t) for nm, t in buf.items()}
+
+    def run(ev=None):
+        rec = (lambda j: ev[j].record()) if ev else (lambda j: None)
+        rec(0)
+        ctx.mul_beaver(RING, x0, x1, y0, y1, 3, out=(q["prod0"], q["prod1"]))
+        rec(1)
+        ctx.trunc_prob(RING, K_TRUNC, q["prod0"], q["prod1"], out=(q["trc0"], q["trc1"]))
+        rec(2)
+        ctx.trunc_det(RING, K_TRUNC, 0, q["prod0"], q["prod1"], out=(q["det0"], q["det1"]))
+        rec(3)
+        ctx.relu(prm, q["trc0"], q["trc1"], 4, out=(q["relu0"], q["relu1"]))
+        rec(4)
+
+    for _ in range(3):
+        run()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(20)]
+    for ev in evs:
+        run(ev)
+    torch.cuda.synchronize()
+    ms = [sum(ev[j].elapsed_time(ev[j + 1]) for ev in evs) / len(evs) for j in range(4)]
+    same = all(torch.equal(q[nm], buf[nm]) for nm in buf)
+
+    def hbm(t, bytes_per_elem):
+        gbs = bytes_per_elem * n / (t / 1e3) / 1e9
+        return {"ms": t, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
+                "bytes_per_element": bytes_per_elem}
+    return {"ms": sum(ms), "fused_ms": fused_ms, "speedup_of_fusion": sum(ms) / fused_ms,
+            "relu_ms": ms[3], "equal_to_fused": same,
+            "hbm_kernels": {"mul_beaver": hbm(ms[0], 48), "trunc_prob": hbm(ms[1], 32),
+                            "trunc_det": hbm(ms[2], 32)}}
+
+
+def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, buf):
+    """The same step through the host-buffer entry point with pinned host
+    inputs and outputs, host<->device transfers inside the timed region.  The
+    default (direct) path has the fused kernel load and store the pinned
+    buffers across the host link; the staged path copies chunks through
+    device buffers on four streams.  Both are checked against the device
+    step's outputs."""
     import torch
     hx = [t.cpu().pin_memory() for t in (x0, x1, y0, y1)]
-    out = {k: torch.empty(n, dtype=torch.int64).pin_memory() for k in ("relu0", "relu1")}
-    out["det0"] = torch.empty(n, dtype=torch.int64).pin_memory()
-    out["det1"] = torch.empty(n, dtype=torch.int64).pin_memory()
-    best = None
-    for chunk_log2 in (18, 19, 20):         # pick the staging chunk, then time
-        ctx.reserve(1 << chunk_log2)
-        for _ in range(2):
-            ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
-        t0 = time.perf_counter()
-        for _ in range(5):
-            ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
-        dt = time.perf_counter() - t0
-        if best is None or dt < best[1]:
-            best = (chunk_log2, dt)
-    ctx.reserve(1 << best[0])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    names = ("relu0", "relu1", "det0", "det1")
+    out = {k: torch.empty(n, dtype=torch.int64).pin_memory() for k in names}
+
+    def timed(reps):
         ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
-    dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+        return n * reps / (time.perf_counter() - t0)
+
+    def same():
+        return all(torch.equal(out[k], buf[k].cpu()) for k in names)
+
+    paths = {}
+    ctx.set_host_path(ctx.HOST_STAGED)
+    best = None
+    for chunk_log2 in (18, 19, 20):         # pick the staging chunk
+        ctx.reserve(1 << chunk_log2)
+        r = timed(5)
+        if best is None or r > best[1]:
+            best = (chunk_log2, r)
+    ctx.reserve(1 << best[0])
+    paths["staged"] = {"elems_per_s": timed(steps), "chunk": 1 << best[0], "equal": same()}
+    ctx.set_host_path(ctx.HOST_DIRECT)
+    paths["direct"] = {"elems_per_s": timed(steps), "equal": same()}
+    ctx.set_host_path(ctx.HOST_AUTO)
+    value = timed(steps)
+    return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
             "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
-            "api": f"bc_linear_relu_host (pinned host buffers, chunks of 2^{best[0]}, "
-                   f"four streams)"}
+            "api": "bc_linear_relu_host, pinned host buffers, default path (direct: the fused "
+                   "kernel loads and stores them across the host link)",
+            "paths": paths}
 
 
 def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):

@@ -303,23 +303,42 @@ typedef struct {
   const void *x0, *x1, *y0, *y1;
   size_t n;
   uint32_t tensor_id;       /* product uses tensor_id, ReLU tensor_id + 1     */
-  void *prod0, *prod1;      /* product shares (workspace, l-bit lanes)        */
-  void *trc0, *trc1;        /* Alg. smltrc output (l-bit lanes)               */
-  void *det0, *det1;        /* Alg. newtrc output in Z_{2^(l-k)}              */
+  void *prod0, *prod1;      /* product shares (l-bit lanes; optional)         */
+  void *trc0, *trc1;        /* Alg. smltrc output (l-bit lanes; optional)     */
+  void *det0, *det1;        /* Alg. newtrc output in Z_{2^(l-k)} (optional)   */
   void *relu0, *relu1;      /* ReLU of the probabilistically truncated product */
 } bc_linear_relu_args;
 
-/* All device pointers: product, both truncations, ReLU, back to back. */
+/* One fused kernel per element: the Beaver product (Sec. 2.2) with the triple
+ * of `tensor_id`, Alg. smltrc and Alg. newtrc (k1 = trunc_bits, k2 = 0) of the
+ * product, and Alg. relu (tensor id tensor_id + 1) of the Alg. smltrc output.
+ * Results equal bc_mul_beaver, bc_trunc_prob, bc_trunc_det and bc_relu called
+ * in turn.  All pointers are device pointers.  x, y, relu are required;
+ * prod, trc and det are optional in pairs (both NULL: not written; one NULL:
+ * BC_EINVAL).  Communication is counted as for the product plus the ReLU. */
 int bc_linear_relu(bc_ctx *ctx, const bc_linear_relu_args *a);
-/* Same with HOST pointers for x0,x1,y0,y1 (input) and relu0,relu1,det0,det1
- * (output); prod/trc fields are ignored.  Staged through device buffers
- * reserved by bc_reserve in chunks of its `chunk` elements, four chunks in
- * flight on four streams so that host-to-device copies, kernels and
- * device-to-host copies of different chunks overlap (pinned host memory
- * needed for the overlap).  Returns after the results are in host memory. */
+
+/* The same step with HOST pointers: x0,x1,y0,y1 in; relu0,relu1 and
+ * optionally det0,det1 out (prod/trc fields are ignored).  Two paths:
+ *   direct  every buffer is page-locked memory mapped for the device (from
+ *           cudaHostAlloc/cudaMallocHost or cudaHostRegister): the fused
+ *           kernel loads and stores it across the host link, one launch.
+ *   staged  otherwise: chunks of bc_reserve's `chunk` elements are copied to
+ *           device buffers, run and copied back, four chunks in flight on
+ *           four streams so that both copy directions and the kernels of
+ *           different chunks overlap (needs bc_reserve first, else BC_EINVAL).
+ * bc_set_host_path chooses: BC_HOST_AUTO (direct when every buffer is mapped),
+ * BC_HOST_DIRECT (BC_EINVAL if one is not), BC_HOST_STAGED.  Each host array
+ * must hold n lanes: the direct path cannot check extents, and a short buffer
+ * is an out-of-range device access.  Returns after the results are in host
+ * memory. */
+#define BC_HOST_AUTO 0
+#define BC_HOST_DIRECT 1
+#define BC_HOST_STAGED 2
 int bc_linear_relu_host(bc_ctx *ctx, const bc_linear_relu_args *a);
-/* Set the chunk of bc_linear_relu_host to `chunk` elements, growing the
- * device staging (4 sets of 12 arrays of `chunk` 64-bit lanes) if needed. */
+int bc_set_host_path(bc_ctx *ctx, int path);
+/* Set the chunk of the staged path to `chunk` elements, growing the device
+ * staging (4 sets of 8 arrays of `chunk` 64-bit lanes) if needed. */
 int bc_reserve(bc_ctx *ctx, size_t chunk);
 
 /* ---- truncation-failure statistics (evaluation only) --------------------- */

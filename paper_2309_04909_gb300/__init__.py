@@ -324,35 +324,48 @@ class Context:
     def linear_relu(self, ring_bits: int, k: int, prm: Params, x0, x1, y0, y1, tensor_id: int,
                     work=None):
         """Beaver product, Alg. smltrc and Alg. newtrc by k bits, ReLU of the
-        probabilistically truncated product.  Returns dict of device tensors."""
+        probabilistically truncated product, in one fused kernel.  `work` maps
+        output names to device tensors; "relu0"/"relu1" are required, the pairs
+        "prod", "trc" and "det" are written only when present.  Returns `work`
+        (all eight outputs when it is None)."""
         n = x0.numel()
         w = work or self.linear_relu_buffers(ring_bits, k, n)
+        ptr = lambda nm: w[nm].data_ptr() if nm in w else None
         a = LinearReluArgs(ring_bits, k, prm.c_struct(), x0.data_ptr(), x1.data_ptr(),
                            y0.data_ptr(), y1.data_ptr(), n, tensor_id,
-                           *[w[nm].data_ptr() for nm in ("prod0", "prod1", "trc0", "trc1", "det0",
-                                                         "det1", "relu0", "relu1")])
+                           *[ptr(nm) for nm in ("prod0", "prod1", "trc0", "trc1", "det0",
+                                                "det1", "relu0", "relu1")])
         self._sync_stream()
         self._check(self._lib.bc_linear_relu(self._h, ctypes.byref(a)))
         return w
 
-    def linear_relu_buffers(self, ring_bits: int, k: int, n: int) -> Dict[str, torch.Tensor]:
-        d = {nm: self._empty(n, ring_bits) for nm in ("prod0", "prod1", "trc0", "trc1", "relu0",
-                                                       "relu1")}
-        d["det0"] = self._empty(n, ring_bits - k)
-        d["det1"] = self._empty(n, ring_bits - k)
-        return d
+    def linear_relu_buffers(self, ring_bits: int, k: int, n: int,
+                            names=("prod0", "prod1", "trc0", "trc1", "det0", "det1", "relu0",
+                                   "relu1")) -> Dict[str, torch.Tensor]:
+        return {nm: self._empty(n, ring_bits - k if nm.startswith("det") else ring_bits)
+                for nm in names}
+
+    HOST_AUTO, HOST_DIRECT, HOST_STAGED = 0, 1, 2
+
+    def set_host_path(self, path: int):
+        """Path of linear_relu_host: HOST_AUTO (direct when every buffer is
+        pinned), HOST_DIRECT, HOST_STAGED."""
+        self._check(self._lib.bc_set_host_path(self._h, path))
 
     def reserve(self, max_chunk: int):
         self._check(self._lib.bc_reserve(self._h, max_chunk))
 
     def linear_relu_host(self, ring_bits: int, k: int, prm: Params, x0, x1, y0, y1,
                          tensor_id: int, out: Dict[str, torch.Tensor]):
-        """Host (CPU, ideally pinned) tensors in and out; copies happen inside."""
+        """Host tensors in and out ("relu0"/"relu1" required, "det0"/"det1"
+        optional).  Pinned tensors take the direct path (the kernel reads and
+        writes them across the host link); others are staged in chunks, which
+        needs reserve() first."""
         n = x0.numel()
+        det = [out[nm].data_ptr() if nm in out else None for nm in ("det0", "det1")]
         a = LinearReluArgs(ring_bits, k, prm.c_struct(), x0.data_ptr(), x1.data_ptr(),
                            y0.data_ptr(), y1.data_ptr(), n, tensor_id, None, None, None, None,
-                           out["det0"].data_ptr(), out["det1"].data_ptr(),
-                           out["relu0"].data_ptr(), out["relu1"].data_ptr())
+                           *det, out["relu0"].data_ptr(), out["relu1"].data_ptr())
         self._sync_stream()
         self._check(self._lib.bc_linear_relu_host(self._h, ctypes.byref(a)))
         return out

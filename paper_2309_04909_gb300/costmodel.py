@@ -59,6 +59,39 @@ def mul_ops_per_element(lx: int, ring_bits: int, relu: bool = True) -> int:
     return philox_blocks(lx, ring_bits, relu) * PHILOX_BLOCK_MUL + L * SLOT_MUL + lx + finish
 
 
+# The fused step of a linear layer followed by a ReLU adds, per element:
+#   Beaver product    Philox blocks of the triple: 3 (l > 32; a0 b0 | c0 | a1 b1)
+#                     or 2 (l <= 32); 6 ring products (c1, d e, d b0, e a0, d b1,
+#                     e a1), each 4 multiplier ops at l > 32 (a 64-bit low product)
+#                     or 1; 14 ring adds/subtracts/masks (2 ops each at l > 32)
+#   truncations       2 shifts, 3 negations, 2 masks (2 ops each at l > 32)
+def product_mul_ops_per_element(ring_bits: int) -> int:
+    wide = ring_bits > 32
+    return (3 if wide else 2) * PHILOX_BLOCK_MUL + 6 * (4 if wide else 1)
+
+
+def product_int_ops_per_element(ring_bits: int) -> int:
+    wide = ring_bits > 32
+    w = 2 if wide else 1
+    return ((3 if wide else 2) * PHILOX_BLOCK_OPS + 6 * (4 if wide else 1) + 14 * w + 7 * w)
+
+
+def linear_relu_mul_ops_per_element(lx: int, ring_bits: int) -> int:
+    return product_mul_ops_per_element(ring_bits) + mul_ops_per_element(lx, ring_bits, True)
+
+
+def linear_relu_int_ops_per_element(lx: int, ring_bits: int) -> int:
+    return product_int_ops_per_element(ring_bits) + int_ops_per_element(lx, ring_bits, True)
+
+
+def hbm_bytes_per_element_linear_relu(ring_bits: int, det_bits: int = 48) -> int:
+    """Fused step: read x0, x1, y0, y1; write the ReLU and the deterministic
+    truncation shares (det lanes 8 bytes when l - k > 32)."""
+    lane = 8 if ring_bits > 32 else 4
+    det = 8 if det_bits > 32 else 4
+    return 6 * lane + 2 * det
+
+
 def hbm_bytes_per_element_relu(ring_bits: int) -> int:
     lane = 8 if ring_bits > 32 else 4
     return 4 * lane            # read [x]_0, [x]_1; write two output shares

@@ -48,6 +48,7 @@ struct bc_ctx {
   size_t stage_chunk = 0;     // elements per chunk (<= stage_cap)
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_start = nullptr;
+  int host_path = BC_HOST_AUTO;
 };
 
 namespace {
@@ -628,18 +629,32 @@ int check_linear(const bc_linear_relu_args* a) {
   return BC_OK;
 }
 
-int linear_relu_device(bc_ctx* ctx, const bc_linear_relu_args* a, const void* x0, const void* x1,
-                       const void* y0, const void* y1, void* prod0, void* prod1, void* trc0,
-                       void* trc1, void* det0, void* det1, void* relu0, void* relu1, size_t n,
-                       uint64_t base, cudaStream_t s) {
-  const int ell = a->ring_bits, k = a->trunc_bits;
-  CK(bc::launch_mul_beaver(ell, ctx->rk, x0, x1, y0, y1, n, a->tensor_id, base, prod0, prod1,
-                           ctx->num_sms, s));
-  CK(bc::launch_trunc_prob(ell, k, prod0, prod1, n, trc0, trc1, ctx->num_sms, s));
-  if (det0 && det1)
-    CK(bc::launch_trunc_det(ell, k, 0, prod0, prod1, n, det0, det1, ctx->num_sms, s));
-  return run_relu(ctx, &a->relu, trc0, trc1, n, a->tensor_id + 1, relu0, relu1, true, base, s,
-                  false);
+// The fused step kernel over n elements starting at element `base`; prod/trc/
+// det pointers may be NULL (not written).
+int linear_relu_device(bc_ctx* ctx, const bc_linear_relu_args* a, const bc::LinearIo& io,
+                       size_t n, uint64_t base, cudaStream_t s) {
+  bc::LinearConsts c;
+  int rc = make_consts(ctx, &a->relu, a->tensor_id + 1, &c.k);
+  if (rc) return rc;
+  c.k.elem_base = base;
+  c.mul_tid = a->tensor_id;
+  c.trunc = (uint32_t)a->trunc_bits;
+  c.det_mask = ring_mask(a->ring_bits - a->trunc_bits);
+  c.det_wide = a->ring_bits - a->trunc_bits > 32 ? 1u : 0u;
+  if (n) CK(bc::launch_linear_relu(c, io, n, s));
+  return BC_OK;
+}
+
+// Device address of a host pointer that the GPU can load from and store to
+// (page-locked memory of the CUDA allocator or registered with it), else NULL.
+void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 }  // namespace
@@ -648,14 +663,20 @@ int bc_linear_relu(bc_ctx* ctx, const bc_linear_relu_args* a) {
   if (!ctx) return BC_EINVAL;
   int rc = check_linear(a);
   if (rc) return rc;
-  if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->prod0 || !a->prod1 || !a->trc0 ||
-               !a->trc1 || !a->relu0 || !a->relu1))
-    return BC_EINVAL;
-  rc = linear_relu_device(ctx, a, a->x0, a->x1, a->y0, a->y1, a->prod0, a->prod1, a->trc0,
-                          a->trc1, a->det0, a->det1, a->relu0, a->relu1, a->n, 0, ctx->stream);
+  if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->relu0 || !a->relu1)) return BC_EINVAL;
+  if (!a->prod0 != !a->prod1 || !a->trc0 != !a->trc1 || !a->det0 != !a->det1) return BC_EINVAL;
+  const bc::LinearIo io{a->x0, a->x1, a->y0, a->y1, a->prod0, a->prod1, a->trc0,
+                        a->trc1, a->det0, a->det1, a->relu0, a->relu1};
+  rc = linear_relu_device(ctx, a, io, a->n, 0, ctx->stream);
   if (rc) return rc;
   add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
   add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));
+  return BC_OK;
+}
+
+int bc_set_host_path(bc_ctx* ctx, int path) {
+  if (!ctx || path < BC_HOST_AUTO || path > BC_HOST_STAGED) return BC_EINVAL;
+  ctx->host_path = path;
   return BC_OK;
 }
 
@@ -671,7 +692,7 @@ int bc_reserve(bc_ctx* ctx, size_t max_chunk) {
     ctx->stage_cap = ctx->stage_chunk = 0;
     const size_t per = ((max_chunk * 8 + 255) / 256) * 256;   // one 64-bit array, 256 B aligned
     for (int i = 0; i < 4; ++i) {
-      if (cudaMalloc(&ctx->stage[i], per * 12) != cudaSuccess) {
+      if (cudaMalloc(&ctx->stage[i], per * 8) != cudaSuccess) {
         cudaGetLastError();
         return BC_ENOMEM;
       }
@@ -687,49 +708,56 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   int rc = check_linear(a);
   if (rc) return rc;
   if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->relu0 || !a->relu1)) return BC_EINVAL;
-  if (a->n && ctx->stage_chunk == 0) return BC_EINVAL;
-  const size_t lb = lane_bytes(a->ring_bits);
-  const size_t db = lane_bytes(a->ring_bits - a->trunc_bits);
-  const size_t per = ((ctx->stage_cap * 8 + 255) / 256) * 256;
-  const size_t chunk = ctx->stage_chunk;
-  cudaStream_t st[4] = {ctx->stream, ctx->aux[0], ctx->aux[1], ctx->aux[2]};
-  // the other streams start after everything queued on the context stream
-  CK(cudaEventRecord(ctx->ev_start, ctx->stream));
-  for (int i = 0; i < 3; ++i) CK(cudaStreamWaitEvent(ctx->aux[i], ctx->ev_start, 0));
-  const char* hx0 = static_cast<const char*>(a->x0);
-  const char* hx1 = static_cast<const char*>(a->x1);
-  const char* hy0 = static_cast<const char*>(a->y0);
-  const char* hy1 = static_cast<const char*>(a->y1);
-  char* hr0 = static_cast<char*>(a->relu0);
-  char* hr1 = static_cast<char*>(a->relu1);
-  char* hd0 = static_cast<char*>(a->det0);
-  char* hd1 = static_cast<char*>(a->det1);
-  // chunk j runs on stream j % 4 with stage set j % 4: copies in, compute,
-  // copies out; four chunks in flight let the two copy directions and the
-  // kernels of different chunks overlap
-  size_t j = 0;
-  for (size_t off = 0; off < a->n; off += chunk, ++j) {
-    const size_t m = std::min(chunk, a->n - off);
-    cudaStream_t s = st[j % 4];
-    char* base = static_cast<char*>(ctx->stage[j % 4]);
-    void* b[12];
-    for (int q = 0; q < 12; ++q) b[q] = base + per * q;
-    CK(cudaMemcpyAsync(b[0], hx0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(b[1], hx1 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(b[2], hy0 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(b[3], hy1 + off * lb, m * lb, cudaMemcpyHostToDevice, s));
-    const bool det = hd0 && hd1;
-    rc = linear_relu_device(ctx, a, b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7],
-                            det ? b[8] : nullptr, det ? b[9] : nullptr, b[10], b[11], m, off, s);
+  if (!a->det0 != !a->det1) return BC_EINVAL;
+  const bool det = a->det0 != nullptr;
+  if (a->n == 0) return BC_OK;
+  // direct path: every buffer is mapped page-locked memory, so the fused
+  // kernel loads the inputs and stores the outputs across the host link
+  const void* hp[8] = {a->x0, a->x1, a->y0, a->y1, a->relu0, a->relu1, a->det0, a->det1};
+  void* dp[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool direct = ctx->host_path != BC_HOST_STAGED;
+  for (int q = 0; q < (det ? 8 : 6) && direct; ++q) direct = (dp[q] = mapped_host(hp[q])) != nullptr;
+  if (direct) {
+    const bc::LinearIo io{dp[0], dp[1], dp[2], dp[3], nullptr, nullptr, nullptr,
+                          nullptr, dp[6], dp[7], dp[4], dp[5]};
+    rc = linear_relu_device(ctx, a, io, a->n, 0, ctx->stream);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(hr0 + off * lb, b[10], m * lb, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hr1 + off * lb, b[11], m * lb, cudaMemcpyDeviceToHost, s));
-    if (det) {
-      CK(cudaMemcpyAsync(hd0 + off * db, b[8], m * db, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(hd1 + off * db, b[9], m * db, cudaMemcpyDeviceToHost, s));
+  } else {
+    if (ctx->host_path == BC_HOST_DIRECT) return BC_EINVAL;   // some buffer is not mapped
+    if (ctx->stage_chunk == 0) return BC_EINVAL;
+    const size_t lb = lane_bytes(a->ring_bits);
+    const size_t db = lane_bytes(a->ring_bits - a->trunc_bits);
+    const size_t per = ((ctx->stage_cap * 8 + 255) / 256) * 256;
+    const size_t chunk = ctx->stage_chunk;
+    cudaStream_t st[4] = {ctx->stream, ctx->aux[0], ctx->aux[1], ctx->aux[2]};
+    // the other streams start after everything queued on the context stream
+    CK(cudaEventRecord(ctx->ev_start, ctx->stream));
+    for (int i = 0; i < 3; ++i) CK(cudaStreamWaitEvent(ctx->aux[i], ctx->ev_start, 0));
+    // chunk j runs on stream j % 4 with stage set j % 4: copies in, the fused
+    // kernel, copies out; four chunks in flight let the two copy directions
+    // and the kernels of different chunks overlap
+    size_t j = 0;
+    for (size_t off = 0; off < a->n; off += chunk, ++j) {
+      const size_t m = std::min(chunk, a->n - off);
+      cudaStream_t s = st[j % 4];
+      char* base = static_cast<char*>(ctx->stage[j % 4]);
+      void* b[8];
+      for (int q = 0; q < 8; ++q) b[q] = base + per * q;
+      for (int q = 0; q < 4; ++q)
+        CK(cudaMemcpyAsync(b[q], static_cast<const char*>(hp[q]) + off * lb, m * lb,
+                           cudaMemcpyHostToDevice, s));
+      const bc::LinearIo io{b[0], b[1], b[2], b[3], nullptr, nullptr, nullptr,
+                            nullptr, det ? b[6] : nullptr, det ? b[7] : nullptr, b[4], b[5]};
+      rc = linear_relu_device(ctx, a, io, m, off, s);
+      if (rc) return rc;
+      for (int q = 4; q < (det ? 8 : 6); ++q) {
+        const size_t w = q < 6 ? lb : db;
+        CK(cudaMemcpyAsync(static_cast<char*>(const_cast<void*>(hp[q])) + off * w, b[q], m * w,
+                           cudaMemcpyDeviceToHost, s));
+      }
     }
+    for (int i = 0; i < 3; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
   }
-  for (int i = 0; i < 3; ++i) CK(cudaStreamSynchronize(ctx->aux[i]));
   CK(cudaStreamSynchronize(ctx->stream));
   add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
   add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));

@@ -141,6 +141,32 @@ __device__ __forceinline__ uint64_t block_elem<uint64_t>(const U32x4& b, int j) 
   return j == 0 ? ((uint64_t)b.y << 32 | b.x) : ((uint64_t)b.w << 32 | b.z);
 }
 
+// Beaver product of one element (Sec. 2.2, the multiplication of the linear
+// layers): the triple a0, b0, c0 comes from seed02 and a1, b1 from seed12
+// (purpose kPurMulTriple), P2 completes it with c1 = (a0 + a1)(b0 + b1) - c0;
+// P0 and P1 open d = x - a and e = y - b, and P0 adds the public d e.
+template <typename Lane>
+__device__ __forceinline__ void beaver_mul(const ElemPhilox& ep, const RoundKeys& rk, Lane mask,
+                                           Lane x0, Lane x1, Lane y0, Lane y1, Lane& o0,
+                                           Lane& o1) {
+  const U32x4 q0 = ep.block_at(kPair02, kPurMulTriple, 0, rk);
+  const U32x4 q1 = ep.block_at(kPair12, kPurMulTriple, 0, rk);
+  Lane a0, b0, c0;
+  if (sizeof(Lane) == 4) {
+    a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
+  } else {
+    const U32x4 q2 = ep.block_at(kPair02, kPurMulTriple, 1, rk);
+    a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
+  }
+  const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
+  a0 &= mask; b0 &= mask; c0 &= mask;
+  const Lane c1 = (Lane)((a0 + a1) * (b0 + b1) - c0) & mask;   // P2 -> P1
+  const Lane d = (Lane)((x0 - a0) + (x1 - a1)) & mask;           // opened x - a
+  const Lane e = (Lane)((y0 - b0) + (y1 - b1)) & mask;           // opened y - b
+  o0 = (Lane)(d * e + d * b0 + e * a0 + c0) & mask;
+  o1 = (Lane)(d * b1 + e * a1 + c1) & mask;
+}
+
 // low 32 bits of (a >> sh) for 0 <= sh < 64
 __device__ __forceinline__ uint32_t lo32_shr(uint64_t a, uint32_t sh) { return (uint32_t)(a >> sh); }
 __device__ __forceinline__ uint32_t lo32_shr(uint32_t a, uint32_t sh) { return a >> sh; }

@@ -150,23 +150,10 @@ __global__ void __launch_bounds__(kBlock)
                       Lane* __restrict__ o1) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
-    const uint64_t elem = base + i;
-    const U32x4 q0 = draw_block(kPair02, kPurMulTriple, tid, elem, 0, rk);
-    const U32x4 q1 = draw_block(kPair12, kPurMulTriple, tid, elem, 0, rk);
-    Lane a0, b0, c0;
-    if (sizeof(Lane) == 4) {
-      a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
-    } else {
-      const U32x4 q2 = draw_block(kPair02, kPurMulTriple, tid, elem, 1, rk);
-      a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
-    }
-    const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
-    a0 &= mask; b0 &= mask; c0 &= mask;
-    const Lane c1 = (Lane)((a0 + a1) * (b0 + b1) - c0) & mask;       // P2 -> P1
-    const Lane d = (Lane)((x0[i] - a0) + (x1[i] - a1)) & mask;         // opened x - a
-    const Lane e = (Lane)((y0[i] - b0) + (y1[i] - b1)) & mask;         // opened y - b
-    o0[i] = (Lane)(d * e + d * b0 + e * a0 + c0) & mask;
-    o1[i] = (Lane)(d * b1 + e * a1 + c1) & mask;
+    Lane p0, p1;
+    beaver_mul<Lane>(ElemPhilox(base + i, tid), rk, mask, x0[i], x1[i], y0[i], y1[i], p0, p1);
+    o0[i] = p0;
+    o1[i] = p1;
   }
 }
 

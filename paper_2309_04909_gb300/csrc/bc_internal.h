@@ -78,6 +78,27 @@ cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles
                               const BatchGroup* groups, int ngroups, unsigned int* counters,
                               int* status, int num_sms, int ctas_per_sm, cudaStream_t s);
 
+// The fused step of a linear layer followed by a ReLU: Beaver product of
+// [x][y], Alg. smltrc and Alg. newtrc2 of the product by `trunc` bits, and
+// Alg. relu of the probabilistically truncated product.
+struct LinearConsts {
+  ReluConsts k;         // ReLU constants; k.tensor_id is the ReLU's id, k.elem_base the
+                        // element index of the launch's first element (product and ReLU)
+  uint32_t mul_tid;     // tensor id of the product's triple
+  uint32_t trunc;       // truncation bits
+  uint64_t det_mask;    // 2^(l - trunc) - 1
+  uint32_t det_wide;    // l - trunc > 32: 64-bit lanes for the deterministic truncation
+};
+struct LinearIo {
+  const void *x0, *x1, *y0, *y1;   // input shares
+  void *prod0, *prod1;             // product shares (optional)
+  void *trc0, *trc1;               // probabilistic truncation (optional)
+  void *det0, *det1;               // deterministic truncation (optional)
+  void *relu0, *relu1;             // ReLU shares
+};
+cudaError_t launch_linear_relu(const LinearConsts& c, const LinearIo& io, uint64_t n,
+                               cudaStream_t s);
+
 // Alg. drelu2 / RSS ReLU on replicated components x[0..2] -> y[0..2].
 cudaError_t launch_rss(const ReluConsts& k, bool relu, const void* const* x, uint64_t n,
                        void* const* y, cudaStream_t s);

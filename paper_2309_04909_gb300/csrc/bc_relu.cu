@@ -277,6 +277,70 @@ cudaError_t launch_lx(const ReluConsts& k, const void* sh0, const void* sh1, uin
 }
 
 // ---------------------------------------------------------------------------
+// Fused step: Beaver product -> both truncations -> ReLU, one element per
+// thread.  The product and the truncated shares never leave registers unless
+// the caller asks for them, so the step moves 32 bytes in and 32 bytes out per
+// element (l = 64) instead of the 176 of four separate kernels.  The input and
+// output pointers may also be mapped pinned host memory: the loads and stores
+// then cross the host link inside the kernel while the multiplier-bound body
+// of other warps hides their latency.
+// ---------------------------------------------------------------------------
+template <typename Lane, int LX, bool SHORT>
+__global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
+    linear_relu_kernel(const LinearConsts c, const LinearIo io, uint64_t n) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t elem = c.k.elem_base + i;
+  const Lane mask = (Lane)c.k.ring_mask;
+  Lane p0, p1;
+  beaver_mul<Lane>(ElemPhilox(elem, c.mul_tid), c.k.rk, mask,
+                   static_cast<const Lane*>(io.x0)[i], static_cast<const Lane*>(io.x1)[i],
+                   static_cast<const Lane*>(io.y0)[i], static_cast<const Lane*>(io.y1)[i], p0, p1);
+  // Alg. smltrc: P0 cut([z]_0, k); P1 2^l - cut(2^l - [z]_1, k)
+  const Lane hi0 = p0 >> c.trunc;
+  const Lane hi1 = ring_neg<Lane>(p1, mask) >> c.trunc;
+  const Lane t0 = hi0;
+  const Lane t1 = ring_neg<Lane>(hi1, mask);
+  if (io.prod0) {
+    static_cast<Lane*>(io.prod0)[i] = p0;
+    static_cast<Lane*>(io.prod1)[i] = p1;
+  }
+  if (io.trc0) {
+    static_cast<Lane*>(io.trc0)[i] = t0;
+    static_cast<Lane*>(io.trc1)[i] = t1;
+  }
+  // Alg. newtrc2 with k1 = k, k2 = 0: the same cuts, reduced mod 2^(l-k)
+  if (io.det0) {
+    const uint64_t dm = c.det_mask;
+    const uint64_t d0 = (uint64_t)hi0 & dm, d1 = (0ull - (uint64_t)hi1) & dm;
+    if (c.det_wide) {
+      static_cast<uint64_t*>(io.det0)[i] = d0;
+      static_cast<uint64_t*>(io.det1)[i] = d1;
+    } else {
+      static_cast<uint32_t*>(io.det0)[i] = (uint32_t)d0;
+      static_cast<uint32_t*>(io.det1)[i] = (uint32_t)d1;
+    }
+  }
+  Lane r0, r1;
+  bicoptor_element<Lane, LX, SHORT, true, false>(c.k, c.k.rk, c.k.tensor_id, t0, t1, elem, perm,
+                                                 r0, r1, AuditPtrs{}, i);
+  static_cast<Lane*>(io.relu0)[i] = r0;
+  static_cast<Lane*>(io.relu1)[i] = r1;
+}
+
+template <typename Lane, int LX, bool SHORT>
+cudaError_t launch_linear_t(const LinearConsts& c, const LinearIo& io, uint64_t n,
+                            cudaStream_t s) {
+  const uint64_t grid = (n + kBlock - 1) / kBlock;
+  if (grid == 0) return cudaSuccess;
+  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  linear_relu_kernel<Lane, LX, SHORT><<<(unsigned)grid, kBlock, 0, s>>>(c, io, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Batched form: one persistent launch per (lane width, key bits) class over
 // that class's range of a tile table of many tensors.  Every warp takes the
 // next tile from the class's atomic counter on its own (no block barrier, no
@@ -524,6 +588,25 @@ cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const v
   }
   return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, s)
                : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, s);
+}
+
+cudaError_t launch_linear_relu(const LinearConsts& c, const LinearIo& io, uint64_t n,
+                               cudaStream_t s) {
+  const ReluConsts& k = c.k;
+  if (k.ring_bits > 32) {
+    const bool shrt = k.c + k.lx < 32;
+    switch (k.lx) {
+      case 24:
+        return shrt ? launch_linear_t<uint64_t, 24, true>(c, io, n, s)
+                    : launch_linear_t<uint64_t, 24, false>(c, io, n, s);
+      default: return launch_linear_t<uint64_t, 0, false>(c, io, n, s);
+    }
+  }
+  switch (k.lx) {
+    case 14: return launch_linear_t<uint32_t, 14, false>(c, io, n, s);
+    case 9: return launch_linear_t<uint32_t, 9, false>(c, io, n, s);
+    default: return launch_linear_t<uint32_t, 0, false>(c, io, n, s);
+  }
 }
 
 cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
