@@ -181,15 +181,20 @@ struct ModP {
   uint32_t pm1;    // p - 1
 };
 
-// Montgomery product a * b * 2^-32 mod p for a, b < p.  t + m p is a
-// multiple of 2^32 and below 2^64 for p < 2^32 with a, b < p; the quotient
-// is below 2p, so one conditional subtraction lands in [0, p).
+// Montgomery product a * b * 2^-32 mod p for a, b < p < 2^32.  With
+// t = a b and q = -t p^-1 mod 2^32, t + q p is a multiple of 2^32 and
+// (t + q p) / 2^32 < 2p, so one conditional subtraction lands in [0, p).
+// t + q p < p^2 + 2^32 p exceeds 64 bits once p > 0.618 * 2^32 (possible for
+// key width lx = 31), so WIDE keeps the carry out of the 64-bit sum; for
+// p < 2^31 the sum always fits.
+template <bool WIDE = true>
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const ModP& m) {
   const uint64_t t = (uint64_t)a * b;
   const uint32_t q = (uint32_t)t * m.pinv;
   const uint64_t u = t + (uint64_t)q * m.p;
   const uint32_t r = (uint32_t)(u >> 32);
-  return r >= m.p ? r - m.p : r;
+  const bool carry = WIDE && u < t;      // the quotient is r + 2^32
+  return (carry || r >= m.p) ? r - m.p : r;
 }
 
 // a + b mod p and a - b mod p for a, b < p (p < 2^32 so the sum may wrap
@@ -202,7 +207,8 @@ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p) 
   return a >= b ? a - b : a + (p - b);
 }
 
-// floor(w * q / 2^64) for a 64-bit w given as (hi, lo) and a 32-bit q.
+// floor(w * q / 2^64) for a 64-bit w given as (hi, lo) and a 32-bit q:
+// floor((hi q + floor(lo q / 2^32)) / 2^32).
 __device__ __forceinline__ uint32_t mulhi_64x32(uint32_t lo, uint32_t hi, uint32_t q) {
   const uint64_t a = (uint64_t)lo * q;
   const uint64_t b = (uint64_t)hi * q + (a >> 32);

@@ -178,8 +178,8 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
     const U32x4 rz = ep.block(kPair01, kPurMask, mb, rk);
     const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
-    uint32_t w0 = mont_mul(m0, rho, k.mp);
-    uint32_t w1 = mont_mul(m1, rho, k.mp);
+    uint32_t w0 = mont_mul<kWide>(m0, rho, k.mp);
+    uint32_t w1 = mont_mul<kWide>(m1, rho, k.mp);
     // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
     w0 = M::add(w0, z, p);
     w1 = M::sub(w1, z, p);

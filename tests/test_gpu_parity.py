@@ -154,6 +154,51 @@ def test_protocol_parity_no_audit(ctx, op, ring, lx, c, mag, n):
     assert np.array_equal(to_np(o1).astype(np.uint64), e1)
 
 
+# The largest prime below 2^32, a valid p for lx = 31 (2^31 < p < 2^32).  The
+# Montgomery quotient of the masking then needs 33 bits.
+P_MAX32 = 4294967291
+
+
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+def test_largest_prime_parity(ctx, op):
+    """lx = 31 with a caller-chosen p near 2^32: outputs and every masked
+    message equal the oracle's, in the fused kernel and the party-separated
+    launches."""
+    ring, lx, c, n = 64, 31, 2, 20_011
+    x = W.magnitude_bounded_ints(n, 32, seed=77)
+    s0, s1 = _shares(ctx, ring, x, 60)
+    prm = Params(ring, lx, c, p=P_MAX32)
+    P = O.params(ring, lx, c, p=P_MAX32)
+    fn = ctx.drelu if op == "drelu" else ctx.relu
+    o0, o1, aud = fn(prm, s0, s1, tensor_id=61, audit=True)
+    es0, es1 = O.share(ring, masked(x, ring), SEED, 60)
+    ofn = O.drelu if op == "drelu" else O.relu
+    e0, e1, eaud = ofn(P, es0, es1, SEED, 61, audit=True, threads=8)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+    assert np.array_equal(to_np(aud["w0"]).reshape(n, lx + 1), eaud["w0"])
+    assert np.array_equal(to_np(aud["w1"]).reshape(n, lx + 1), eaud["w1"])
+    parties = ctx.drelu_parties if op == "drelu" else ctx.relu_parties
+    p0, p1, _ = parties(prm, s0, s1, tensor_id=61)
+    assert np.array_equal(to_np(p0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(p1).astype(np.uint64), e1)
+
+
+def test_largest_prime_rss(ctx):
+    ring, lx, c, n = 64, 31, 2, 9_001
+    x = W.magnitude_bounded_ints(n, 32, seed=78)
+    rng = np.random.default_rng(78)
+    x0 = rng.integers(0, 2**63, n, dtype=np.uint64)
+    x1 = rng.integers(0, 2**63, n, dtype=np.uint64)
+    x2 = x.astype(np.uint64) - x0 - x1
+    ys = ctx.rss_relu(Params(ring, lx, c, p=P_MAX32), to_dev(x0, ring), to_dev(x1, ring),
+                      to_dev(x2, ring), tensor_id=62)
+    e = O.rss_drelu(O.params(ring, lx, c, p=P_MAX32), x0, x1, x2, SEED, 62, relu=True,
+                    threads=8)
+    for g, w in zip(ys, e[:3]):
+        assert np.array_equal(to_np(g).astype(np.uint64), w)
+
+
 def test_protocol_empty_and_single(ctx):
     prm = Params(64, 24, 0)
     z = torch.empty(0, dtype=torch.int64, device="cuda")

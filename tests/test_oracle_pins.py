@@ -374,6 +374,39 @@ def test_drelu_output_shares_and_messages():
     assert all(int(b) == (int(d) * s) % 2**64 for b, d, s in zip(o1, d1, sgn))
 
 
+@pytest.mark.parametrize("lx,c,p", [(31, 2, 4294967291), (31, 0, 2**31 + 11), (24, 0, 2**24 + 43)])
+def test_drelu_messages_from_definition(lx, c, p):
+    """Steps 1-8 of Alg. drelu recomputed with Python integers from their
+    definitions (flip, windows, pair sums, modulo switch, mask, reshare) for
+    explicit randomness and the identity shuffle (every Fisher-Yates word
+    2^32 - 1 keeps each slot in place).  Includes p near 2^32, where the
+    masked products need more than 64 bits before reduction."""
+    ell = 64
+    P = O.params(ell, lx, c, p=p)
+    rng = np.random.default_rng(lx + c)
+    M = 2**ell
+    L = lx + 1
+    for trial in range(40):
+        x = int(rng.integers(-2**(lx + c - 1), 2**(lx + c - 1)))
+        R = int(rng.integers(0, 2**63)) * 2 + trial % 2
+        s0, s1 = (x + R) % M, (-R) % M
+        t = trial % 2
+        r = [int(v) for v in rng.integers(1, p, size=L)]
+        z = [int(v) for v in rng.integers(0, p, size=L)]
+        dprime, m0, m1 = O.drelu_core(P, s0, s1, t, [2**32 - 1] * lx, r, z)
+        f0, f1 = ((-s0) % M, (-s1) % M) if t else (s0, s1)
+        u0 = [(f0 >> (c + i)) % 2**lx for i in range(L)]
+        u1 = [(-(((-f1) % M) >> (c + i))) % 2**lx for i in range(L)]
+        v0 = [(u0[i] + (u0[i + 1] if i < lx else 0) - 1) % 2**lx for i in range(L)]
+        v1 = [(u1[i] + (u1[i + 1] if i < lx else 0)) % 2**lx for i in range(L)]
+        n0 = [a if a else 2**lx for a in v0]
+        n1 = [(p + a - 2**lx) % p for a in v1]
+        want0 = [(n0[k] * r[k] + z[k]) % p for k in range(L)]
+        want1 = [(n1[k] * r[k] - z[k]) % p for k in range(L)]
+        assert list(m0) == want0 and list(m1) == want1
+        assert dprime == int(any((a + b) % p == 0 for a, b in zip(want0, want1)))
+
+
 def test_beaver_mul_exact():
     from paper_2309_04909_gb300 import workloads as W
     for ell in (64, 32, 8):
