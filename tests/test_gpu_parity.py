@@ -338,6 +338,14 @@ def test_full_size_config2_sampled(ctx):
     p0, p1 = O.mul_beaver(64, ex0, ex1, ey0, ey1, SEED, 3, idx=idx)
     assert np.array_equal(to_np(w["prod0"])[idx], p0)
     assert np.array_equal(to_np(w["prod1"])[idx], p1)
+    d0, d1 = O.trunc_det(64, 16, 0, p0, p1)
+    assert np.array_equal(to_np(w["det0"])[idx], d0)
+    assert np.array_equal(to_np(w["det1"])[idx], d1)
+    # the benchmark's call writes only the ReLU and the deterministic truncation
+    only = ctx.linear_relu_buffers(64, 16, n, names=("det0", "det1", "relu0", "relu1"))
+    ctx.linear_relu(64, 16, prm, x0, x1, y0, y1, tensor_id=3, work=only)
+    for nm, t in only.items():
+        assert torch.equal(t, w[nm]), nm
     # property at any size: reconstructed ReLU = product * DReLU bit, and it
     # equals max(prod_trunc, 0) up to the exception set and e0
     rel = O.to_signed(O.reconstruct(64, to_np(w["relu0"]), to_np(w["relu1"])), 64)
