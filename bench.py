@@ -426,8 +426,12 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, buf):
     paths["direct"] = {"elems_per_s": timed(steps), "equal": same()}
     ctx.set_host_path(ctx.HOST_AUTO)
     value = timed(steps)
+    link = 333.0   # GB/s both directions at once, measured on this machine's GB300 host link
     return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
             "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
+            "link_roofline": {"bytes_per_element": 64, "link_GBps": link,
+                              "bound_elems_per_s": link * 1e9 / 64,
+                              "frac": value / (link * 1e9 / 64)},
             "api": "bc_linear_relu_host, pinned host buffers, default path (direct: the fused "
                    "kernel loads and stores them across the host link)",
             "paths": paths}

@@ -15,11 +15,14 @@
  *    entry point's name ends in _host.  A ring element of Z_{2^l} is stored in
  *    a uint32_t lane when l <= 32 and a uint64_t lane when 32 < l <= 64, in
  *    canonical form (bits >= l are zero).  Inputs that are not canonical give
- *    undefined (but memory-safe) results.
+ *    undefined (but memory-safe) results; bc_set_checked makes calls refuse
+ *    them.
  *  - Calls are asynchronous and ordered on the context's stream.  They return
  *    BC_OK (0) or a negative BC_E* code; on an error nothing is launched.
  *  - Hot calls allocate nothing: device workspace is reserved by bc_create
  *    and by bc_reserve.
+ *  - Every entry point that launches work opens an NVTX range named after
+ *    itself, so that a profiler timeline shows the calls.
  *  - Randomness: every pseudorandom value is Philox-4x32-10 keyed by the
  *    context seed, with the counter (element index, tensor_id, block,
  *    pair/purpose tag).  Results therefore depend only on (seed, tensor_id,
@@ -98,6 +101,13 @@ int bc_create(bc_ctx **out, uint64_t seed, int device, void *cuda_stream);
 int bc_destroy(bc_ctx *ctx);
 int bc_set_stream(bc_ctx *ctx, void *cuda_stream);
 int bc_synchronize(bc_ctx *ctx);
+/* Checked mode (off by default; a debugging aid).  When on, every call that
+ * takes device share arrays (and bc_relu_batch_plan, per tensor) first counts
+ * on the GPU the input lanes that are not canonical (a bit at or above l set;
+ * l = 32 and l = 64 lanes always are), waits for the count, and returns
+ * BC_EINVAL without launching the operation if any lane fails.  The wait
+ * makes every checked call synchronous with the context stream. */
+int bc_set_checked(bc_ctx *ctx, int on);
 const char *bc_strerror(int code);
 /* Text of the last CUDA error seen by this context (empty if none). */
 const char *bc_last_cuda_error(bc_ctx *ctx);

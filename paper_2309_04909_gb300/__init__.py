@@ -345,6 +345,12 @@ class Context:
         return {nm: self._empty(n, ring_bits - k if nm.startswith("det") else ring_bits)
                 for nm in names}
 
+    def set_checked(self, on: bool = True):
+        """Checked mode: calls verify that their input lanes are canonical
+        (no bits at or above l) and raise instead of running if not; each
+        checked call waits for its check."""
+        self._check(self._lib.bc_set_checked(self._h, 1 if on else 0))
+
     HOST_AUTO, HOST_DIRECT, HOST_STAGED = 0, 1, 2
 
     def set_host_path(self, path: int):

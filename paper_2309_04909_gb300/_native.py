@@ -155,6 +155,7 @@ SIGNATURES = {
     "bc_linear_relu_host": (c_int, [c_void_p, P(LinearReluArgs)]),
     "bc_reserve": (c_int, [c_void_p, c_size]),
     "bc_set_host_path": (c_int, [c_void_p, c_int]),
+    "bc_set_checked": (c_int, [c_void_p, c_int]),
     "bc_count_trunc_failures": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                         c_size, c_void_p]),
     "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),

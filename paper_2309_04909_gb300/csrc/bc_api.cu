@@ -8,6 +8,10 @@
 #include <algorithm>
 #include <vector>
 
+#include <initializer_list>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "bc_internal.h"
 
 struct bc_ctx {
@@ -49,6 +53,9 @@ struct bc_ctx {
   void* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_start = nullptr;
   int host_path = BC_HOST_AUTO;
+  // checked mode: canonical-form check of every input before a call
+  bool checked = false;
+  unsigned long long* d_check = nullptr;
 };
 
 namespace {
@@ -57,6 +64,14 @@ int cuda_fail(bc_ctx* ctx, cudaError_t e, const char* where) {
   if (ctx) snprintf(ctx->last_err, sizeof(ctx->last_err), "%s: %s", where, cudaGetErrorString(e));
   return BC_ECUDA;
 }
+// A named range on the NVTX timeline for the duration of an entry point
+// (free when no profiler is attached).
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+};
+#define BC_TRACE() Trace bc_trace_(__func__)
+
 #define CK(call)                                              \
   do {                                                        \
     cudaError_t e_ = (call);                                  \
@@ -98,6 +113,21 @@ bc::ModP make_modp(uint32_t p) {
 }
 
 uint64_t ring_mask(int bits) { return bits >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1); }
+
+// Checked mode: count, on the context stream, the lanes of the given arrays
+// that have bits at or above ring_bits, wait, and refuse the call if any do.
+int check_canonical(bc_ctx* ctx, int ring_bits, std::initializer_list<const void*> arrays,
+                    size_t n) {
+  if (!ctx->checked || n == 0 || ring_bits == 32 || ring_bits == 64) return BC_OK;
+  CK(cudaMemsetAsync(ctx->d_check, 0, sizeof(unsigned long long), ctx->stream));
+  for (const void* a : arrays)
+    if (a) CK(bc::launch_count_noncanonical(ring_bits, a, n, ctx->d_check, ctx->num_sms,
+                                            ctx->stream));
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_check, sizeof bad, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return bad ? BC_EINVAL : BC_OK;
+}
 
 // Checks of Alg. drelu's parameters; fills the kernel constants.
 int make_consts(bc_ctx* ctx, const bc_drelu_params* prm, uint32_t tensor_id,
@@ -185,6 +215,7 @@ int run_relu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const voi
   bc::ReluConsts k;
   int rc = make_consts(ctx, prm, tensor_id, &k);
   if (rc) return rc;
+  if (s == ctx->stream && (rc = check_canonical(ctx, prm->ring_bits, {sh0, sh1}, n))) return rc;
   k.elem_base = elem_base;
   if (n) CK(bc::launch_relu(k, relu, sh0, sh1, n, o0, o1, ctx->audit, ctx->num_sms, s));
   if (count) add_comm(&ctx->comm, relu_comm(prm->ring_bits, prm->lx, n, relu));
@@ -230,6 +261,7 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
     e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int) * bc::kMaxBatchGroups);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_check, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
@@ -262,6 +294,7 @@ int bc_destroy(bc_ctx* ctx) {
   }
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_status);
+  cudaFree(ctx->d_check);
   for (int i = 0; i < 4; ++i) cudaFree(ctx->stage[i]);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   delete ctx;
@@ -284,6 +317,7 @@ int bc_share(bc_ctx* ctx, int ring_bits, const int64_t* x, size_t n, uint32_t te
              void* sh0, void* sh1) {
   if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
   if (n && (!x || !sh0 || !sh1)) return BC_EINVAL;
+  BC_TRACE();
   CK(bc::launch_share(ring_bits, ctx->rk, x, n, tensor_id, 0, sh0, sh1, ctx->num_sms, ctx->stream));
   return BC_OK;
 }
@@ -292,6 +326,8 @@ int bc_reconstruct(bc_ctx* ctx, int ring_bits, const void* sh0, const void* sh1,
                    void* x_out) {
   if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !x_out)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {sh0, sh1}, n)) return rc;
   CK(bc::launch_reconstruct(ring_bits, sh0, sh1, n, x_out, ctx->num_sms, ctx->stream));
   return BC_OK;
 }
@@ -300,6 +336,8 @@ int bc_trunc_prob(bc_ctx* ctx, int ring_bits, int k, const void* sh0, const void
                   void* o0, void* o1) {
   if (!ctx || ring_bits < 1 || ring_bits > 64 || k < 0 || k >= ring_bits) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {sh0, sh1}, n)) return rc;
   CK(bc::launch_trunc_prob(ring_bits, k, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
   return BC_OK;
 }
@@ -312,6 +350,8 @@ int bc_trunc_det(bc_ctx* ctx, int ring_bits, int k1, int k2, const void* sh0, co
   // outputs of a narrower lane than the inputs must not alias them
   if (lane_bytes(ring_bits) != lane_bytes(ring_bits - k1 - k2) && (o0 == sh0 || o1 == sh1))
     return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {sh0, sh1}, n)) return rc;
   CK(bc::launch_trunc_det(ring_bits, k1, k2, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
   return BC_OK;
 }
@@ -321,6 +361,8 @@ int bc_mod_switch(bc_ctx* ctx, int lp, uint32_t p, const void* sh0, const void* 
   if (!ctx || lp < 1 || lp > 31) return BC_EINVAL;
   if ((uint64_t)p <= ((uint64_t)1 << lp) || !is_prime32(p)) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, lp, {sh0, sh1}, n)) return rc;
   CK(bc::launch_mod_switch(lp, p, sh0, sh1, n, o0, o1, ctx->num_sms, ctx->stream));
   return BC_OK;
 }
@@ -329,6 +371,8 @@ int bc_mul_beaver(bc_ctx* ctx, int ring_bits, const void* x0, const void* x1, co
                   const void* y1, size_t n, uint32_t tensor_id, void* o0, void* o1) {
   if (!ctx || ring_bits < 1 || ring_bits > 64) return BC_EINVAL;
   if (n && (!x0 || !x1 || !y0 || !y1 || !o0 || !o1)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {x0, x1, y0, y1}, n)) return rc;
   CK(bc::launch_mul_beaver(ring_bits, ctx->rk, x0, x1, y0, y1, n, tensor_id, 0, o0, o1,
                            ctx->num_sms, ctx->stream));
   add_comm(&ctx->comm, mul_comm(ring_bits, n));
@@ -339,6 +383,8 @@ int bc_trunc_aby3(bc_ctx* ctx, int ring_bits, int k, const void* sh0, const void
                   uint32_t tensor_id, uint64_t fixed_r, void* o0, void* o1) {
   if (!ctx || ring_bits < 2 || ring_bits > 64 || k < 0 || k >= ring_bits) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {sh0, sh1}, n)) return rc;
   CK(bc::launch_trunc_aby3(ring_bits, ctx->rk, k, sh0, sh1, n, tensor_id,
                            fixed_r & ring_mask(ring_bits), o0, o1, ctx->num_sms, ctx->stream));
   bc_comm d{};
@@ -358,6 +404,8 @@ int bc_trunc_then_mul(bc_ctx* ctx, int ring_bits, int kx, int ky, const void* x0
       ky >= ring_bits)
     return BC_EINVAL;
   if (n && (!x0 || !x1 || !y0 || !y1 || !o0 || !o1)) return BC_EINVAL;
+  BC_TRACE();
+  if (int rc = check_canonical(ctx, ring_bits, {x0, x1, y0, y1}, n)) return rc;
   CK(bc::launch_trunc_then_mul(ring_bits, ctx->rk, kx, ky, x0, x1, y0, y1, n, tensor_id, o0, o1,
                                ctx->num_sms, ctx->stream));
   add_comm(&ctx->comm, mul_comm(ring_bits, n));
@@ -366,12 +414,14 @@ int bc_trunc_then_mul(bc_ctx* ctx, int ring_bits, int kx, int ky, const void* x0
 
 int bc_drelu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
              uint32_t tensor_id, void* o0, void* o1) {
+  BC_TRACE();
   return run_relu(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, false, 0, ctx ? ctx->stream : nullptr,
                   true);
 }
 
 int bc_relu(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1, size_t n,
             uint32_t tensor_id, void* o0, void* o1) {
+  BC_TRACE();
   return run_relu(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, true, 0, ctx ? ctx->stream : nullptr,
                   true);
 }
@@ -400,6 +450,8 @@ static int run_rss(bc_ctx* ctx, const bc_drelu_params* prm, const void* x0, cons
   bc::ReluConsts k;
   int rc = make_consts(ctx, prm, tensor_id, &k);
   if (rc) return rc;
+  BC_TRACE();
+  if ((rc = check_canonical(ctx, prm->ring_bits, {x0, x1, x2}, n))) return rc;
   const void* x[3] = {x0, x1, x2};
   void* y[3] = {y0, y1, y2};
   if (n) CK(bc::launch_rss(k, relu, x, n, y, ctx->stream));
@@ -440,6 +492,8 @@ static int run_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0,
   bc::ReluConsts k;
   int rc = make_consts(ctx, prm, tensor_id, &k);
   if (rc) return rc;
+  BC_TRACE();
+  if ((rc = check_canonical(ctx, prm->ring_bits, {sh0, sh1}, n))) return rc;
   if (n)
     CK(bc::launch_parties(k, relu, sh0, sh1, n, o0, o1, m->w0, m->w1, m->open0, m->open1,
                           m->reply, m->pre_c1, ctx->stream));
@@ -494,6 +548,7 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
     bc::ReluConsts k;
     int rc = make_consts(ctx, &d.params, 0, &k);
     if (rc) return rc;
+    if ((rc = check_canonical(ctx, d.params.ring_bits, {d.sh0, d.sh1}, d.n))) return rc;
     int g = 0;
     while (g < ngroups && !(groups[g].k.ring_bits == k.ring_bits && groups[g].k.lx == k.lx &&
                             groups[g].k.c == k.c && groups[g].k.mp.p == k.mp.p))
@@ -596,6 +651,7 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
 
 int bc_relu_batch_run(bc_ctx* ctx) {
   if (!ctx || !ctx->planned) return BC_EINVAL;
+  BC_TRACE();
   CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int) * bc::kMaxBatchGroups, ctx->stream));
   CK(bc::launch_relu_batch(ctx->d_tensors, ctx->d_tiles, ctx->groups, ctx->ngroups,
                            ctx->d_counter, ctx->d_status, ctx->num_sms, ctx->batch_ctas_per_sm,
@@ -665,12 +721,20 @@ int bc_linear_relu(bc_ctx* ctx, const bc_linear_relu_args* a) {
   if (rc) return rc;
   if (a->n && (!a->x0 || !a->x1 || !a->y0 || !a->y1 || !a->relu0 || !a->relu1)) return BC_EINVAL;
   if (!a->prod0 != !a->prod1 || !a->trc0 != !a->trc1 || !a->det0 != !a->det1) return BC_EINVAL;
+  BC_TRACE();
+  if ((rc = check_canonical(ctx, a->ring_bits, {a->x0, a->x1, a->y0, a->y1}, a->n))) return rc;
   const bc::LinearIo io{a->x0, a->x1, a->y0, a->y1, a->prod0, a->prod1, a->trc0,
                         a->trc1, a->det0, a->det1, a->relu0, a->relu1};
   rc = linear_relu_device(ctx, a, io, a->n, 0, ctx->stream);
   if (rc) return rc;
   add_comm(&ctx->comm, mul_comm(a->ring_bits, a->n));
   add_comm(&ctx->comm, relu_comm(a->ring_bits, a->relu.lx, a->n, true));
+  return BC_OK;
+}
+
+int bc_set_checked(bc_ctx* ctx, int on) {
+  if (!ctx) return BC_EINVAL;
+  ctx->checked = on != 0;
   return BC_OK;
 }
 
@@ -711,6 +775,7 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   if (!a->det0 != !a->det1) return BC_EINVAL;
   const bool det = a->det0 != nullptr;
   if (a->n == 0) return BC_OK;
+  BC_TRACE();
   // direct path: every buffer is mapped page-locked memory, so the fused
   // kernel loads the inputs and stores the outputs across the host link
   const void* hp[8] = {a->x0, a->x1, a->y0, a->y1, a->relu0, a->relu1, a->det0, a->det1};

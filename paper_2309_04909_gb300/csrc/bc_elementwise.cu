@@ -321,6 +321,35 @@ cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, u
   return cudaGetLastError();
 }
 
+// Lanes of a share array with bits at or above l set (checked mode).
+template <typename Lane>
+__global__ void __launch_bounds__(kBlock)
+    noncanonical_kernel(const Lane* __restrict__ a, uint64_t n, uint32_t ell,
+                        unsigned long long* __restrict__ count) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  unsigned int bad = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride)
+    bad += (a[i] >> ell) != 0 ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, (unsigned long long)bad);
+}
+
+cudaError_t launch_count_noncanonical(int ring_bits, const void* a, uint64_t n,
+                                      unsigned long long* count, int num_sms, cudaStream_t s) {
+  if (n == 0 || ring_bits == 32 || ring_bits == 64) return cudaSuccess;   // every lane fits
+  if (ring_bits > 32) {
+    auto kern = noncanonical_kernel<uint64_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(static_cast<const uint64_t*>(a), n,
+                                                          (uint32_t)ring_bits, count);
+  } else {
+    auto kern = noncanonical_kernel<uint32_t>;
+    kern<<<simple_grid(kern, n, num_sms), kBlock, 0, s>>>(static_cast<const uint32_t*>(a), n,
+                                                          (uint32_t)ring_bits, count);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mul_beaver(int ring_bits, const RoundKeys& rk, const void* x0, const void* x1,
                               const void* y0, const void* y1, uint64_t n, uint32_t tensor_id,
                               uint64_t elem_base, void* o0, void* o1, int num_sms,

@@ -131,6 +131,8 @@ cudaError_t launch_trunc_then_mul(int ring_bits, const RoundKeys& rk, int kx, in
                                   const void* x0, const void* x1, const void* y0, const void* y1,
                                   uint64_t n, uint32_t tensor_id, void* o0, void* o1, int num_sms,
                                   cudaStream_t s);
+cudaError_t launch_count_noncanonical(int ring_bits, const void* a, uint64_t n,
+                                      unsigned long long* count, int num_sms, cudaStream_t s);
 cudaError_t launch_count_failures(int out_bits, int k, const int64_t* x, const void* o0,
                                   const void* o1, uint64_t n, unsigned long long* count,
                                   int num_sms, cudaStream_t s);
