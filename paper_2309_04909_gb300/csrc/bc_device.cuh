@@ -63,6 +63,23 @@ __device__ __forceinline__ U32x4 philox_rounds_2_10(uint32_t c0, uint32_t c1, ui
   return U32x4{c0, c1, c2, c3};
 }
 
+// Rounds 3..10 of Philox-4x32-10 (rounds 1 and 2 done by the caller).
+__device__ __forceinline__ U32x4 philox_rounds_3_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                    uint32_t c3, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return U32x4{c0, c1, c2, c3};
+}
+
 // Stream tags: which pre-shared seed a draw belongs to, and what it is for.
 // counter = (lo32(elem), tensor_id, block, pair << 24 | purpose << 16 | elem >> 32)
 enum : uint32_t {
@@ -117,6 +134,32 @@ struct ElemPhilox {
   __device__ __forceinline__ U32x4 block_at(uint32_t pair, uint32_t purpose, uint32_t b,
                                             const RoundKeys& rk) const {
     return block(pair, purpose, (uint64_t)kPhiloxM1 * b, rk);
+  }
+};
+
+// The blocks of one (element, pair, purpose) stream, e.g. the lx + 1 mask
+// blocks of an element: after round 1 their counter words 2 and 3 do not
+// depend on the block index, so round 2's product M1 * word2 is the same for
+// all of them and is computed once here.
+struct StreamPhilox {
+  uint32_t q_hi, q_lo;    // round 2: M1 * (hi32(M0 lo32(elem)) ^ tag ^ k1[0])
+  uint32_t e_lo;          // lo32(M0 lo32(elem)), word 3 after round 1
+  uint32_t tensor_id;
+  __device__ __forceinline__ StreamPhilox(const ElemPhilox& ep, uint32_t pair, uint32_t purpose,
+                                          const RoundKeys& rk) {
+    const uint32_t tag = (pair << 24) | (purpose << 16) | ep.elem_hi16;
+    const uint64_t q = (uint64_t)kPhiloxM1 * (ep.e_hi ^ tag ^ rk.k1[0]);
+    q_hi = (uint32_t)(q >> 32);
+    q_lo = (uint32_t)q;
+    e_lo = ep.e_lo;
+    tensor_id = ep.tensor_id;
+  }
+  // block with M1 * block = mb (64-bit); equal to ElemPhilox::block
+  __device__ __forceinline__ U32x4 block(uint64_t mb, const RoundKeys& rk) const {
+    const uint32_t a0 = (uint32_t)(mb >> 32) ^ tensor_id ^ rk.k0[0];
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * a0;
+    return philox_rounds_3_10(q_hi ^ (uint32_t)mb ^ rk.k0[1], q_lo,
+                              (uint32_t)(p0 >> 32) ^ e_lo ^ rk.k1[1], (uint32_t)p0, rk);
   }
 };
 

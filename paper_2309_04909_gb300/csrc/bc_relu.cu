@@ -131,10 +131,11 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
   }
   uint32_t t = 0;
   const uint32_t nblk = (L + 3) >> 2;
+  const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
 #pragma unroll
   for (uint32_t b = 0; b < (LX ? (uint32_t)((LX + 4) >> 2) : 8u); ++b) {
     if (!LX && b >= nblk) break;
-    const U32x4 wb = ep.block_at(kPair01, kPurPerm, b, rk);
+    const U32x4 wb = perm_stream.block((uint64_t)kPhiloxM1 * b, rk);
     const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -159,6 +160,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
 
   // ---- steps 3-9 over message slots k ----------------------------------------
   uint32_t any_zero = 0;
+  const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
   uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
 #pragma unroll kSlotUnroll
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
@@ -175,7 +177,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
     const uint32_t m1 = v1 + k.p_minus_2lx;
     // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
     // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
-    const U32x4 rz = ep.block(kPair01, kPurMask, mb, rk);
+    const U32x4 rz = mask_stream.block(mb, rk);
     const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
     uint32_t w0 = mont_mul<kWide>(m0, rho, k.mp);
