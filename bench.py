@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu extras")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the step alone: skip e2e and the batched/serving/cpu extras")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window of each serving run (60 s in the full trace)")
@@ -313,13 +314,19 @@ def main():
         "clocks": ck,
     }
 
+    # end to end through the host-buffer entry point, every rank at once
+    # (--no-extras, used for profiling the step alone, skips it)
+    if not args.no_extras:
+        line["e2e"] = e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), world,
+                                    dev)
+
     # the long extras run in the single-GPU run only (N > 1 runs measure the
     # scaled step; every rank's GPU would otherwise be held for minutes)
     if rank == 0 and world == 1 and not args.no_extras:
         # every intermediate of the step, for the extras that read them
         ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
         line["unfused_chain"] = chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms)
-        line["e2e"] = e2e_measure(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf)
+        line["e2e"]["paths"] = e2e_paths(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf)
         line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
         line["linear_layer_truncation"] = linear_trunc_table(ctx, dev)
         rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
@@ -390,17 +397,51 @@ def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms):
                             "trunc_det": hbm(ms[2], 32)}}
 
 
-def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, buf):
-    """The same step through the host-buffer entry point with pinned host
-    inputs and outputs, host<->device transfers inside the timed region.  The
-    default (direct) path has the fused kernel load and store the pinned
-    buffers across the host link; the staged path copies chunks through
-    device buffers on four streams.  Both are checked against the device
-    step's outputs."""
+def _host_step_inputs(x0, x1, y0, y1, n):
     import torch
     hx = [t.cpu().pin_memory() for t in (x0, x1, y0, y1)]
-    names = ("relu0", "relu1", "det0", "det1")
-    out = {k: torch.empty(n, dtype=torch.int64).pin_memory() for k in names}
+    out = {k: torch.empty(n, dtype=torch.int64).pin_memory()
+           for k in ("relu0", "relu1", "det0", "det1")}
+    return hx, out
+
+
+def e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, steps, world, dev):
+    """The step through the host-buffer entry point (the call a user with
+    host data makes): pinned host inputs and outputs, host<->device transfers
+    inside the timed region, default path.  Every rank runs its own batch
+    between barriers; the time is the max over ranks."""
+    import torch
+    import torch.distributed as dist
+    from paper_2309_04909_gb300.replicas import max_over_ranks
+    hx, out = _host_step_inputs(x0, x1, y0, y1, n)
+    for _ in range(2):
+        ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
+    dt = max_over_ranks(time.perf_counter() - t0, device=dev)
+    value = n * steps * world / dt
+    link = 333.0   # GB/s both directions at once, measured on this pool's GB300 host link
+    return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n * world,
+            "d2h_bytes_per_step": 4 * 8 * n * world, "steps": steps,
+            "api": "bc_linear_relu_host, pinned host buffers, default path (direct: the fused "
+                   "kernel loads and stores them across the host link)",
+            "link_roofline": {"bytes_per_element": 64, "link_GBps": link,
+                              "bound_elems_per_s": world * link * 1e9 / 64,
+                              "frac": value / (world * link * 1e9 / 64)}}
+
+
+def e2e_paths(ctx, prm, x0, x1, y0, y1, n, steps, buf):
+    """Both host-buffer paths on one GPU: direct (the fused kernel loads and
+    stores the pinned buffers across the host link) and staged (chunks copied
+    through device buffers on four streams, best chunk of three), each
+    checked against the device step's outputs."""
+    import torch
+    hx, out = _host_step_inputs(x0, x1, y0, y1, n)
+    names = tuple(out)
 
     def timed(reps):
         ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
@@ -416,7 +457,7 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, buf):
     paths = {}
     ctx.set_host_path(ctx.HOST_STAGED)
     best = None
-    for chunk_log2 in (18, 19, 20):         # pick the staging chunk
+    for chunk_log2 in (18, 19, 20):
         ctx.reserve(1 << chunk_log2)
         r = timed(5)
         if best is None or r > best[1]:
@@ -426,16 +467,7 @@ def e2e_measure(ctx, prm, x0, x1, y0, y1, n, steps, buf):
     ctx.set_host_path(ctx.HOST_DIRECT)
     paths["direct"] = {"elems_per_s": timed(steps), "equal": same()}
     ctx.set_host_path(ctx.HOST_AUTO)
-    value = timed(steps)
-    link = 333.0   # GB/s both directions at once, measured on this machine's GB300 host link
-    return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n,
-            "d2h_bytes_per_step": 4 * 8 * n, "steps": steps,
-            "link_roofline": {"bytes_per_element": 64, "link_GBps": link,
-                              "bound_elems_per_s": link * 1e9 / 64,
-                              "frac": value / (link * 1e9 / 64)},
-            "api": "bc_linear_relu_host, pinned host buffers, default path (direct: the fused "
-                   "kernel loads and stores them across the host link)",
-            "paths": paths}
+    return paths
 
 
 def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):
