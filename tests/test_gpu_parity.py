@@ -110,6 +110,8 @@ PROTO = [
     (16, 5, 2, 6, 7_001),       # generic-lx kernel
     (8, 3, 0, 2, 4_097),
     (33, 10, 3, 12, 3_001),
+    (2, 1, 0, 1, 1_001),        # smallest ring: l = 2, one key bit, p = 3
+    (4, 1, 1, 2, 999),          # one key bit above the offset
 ]
 
 
