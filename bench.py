@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--step", default="fused", choices=["fused", "chain"],
+                    help="fused: one kernel per step (default); chain: the same step as four "
+                         "launches (product, two truncations, ReLU) through HBM, each timed")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the step alone: skip e2e and the batched/serving/cpu extras")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -259,6 +262,11 @@ def main():
     def step():
         ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=work)
 
+    if args.step == "chain":
+        chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev)
+        ctx.close()
+        return
+
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -358,7 +366,7 @@ def _threads():
     return O.max_threads()
 
 
-def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms):
+def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms, steps=20, warmup=3):
     """The step as four separate launches (Beaver product, the two
     truncations, ReLU) through HBM, each kernel timed with CUDA events, and
     checked bit for bit against the fused kernel's outputs."""
@@ -378,9 +386,9 @@ def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms):
         ctx.relu(prm, q["trc0"], q["trc1"], 4, out=(q["relu0"], q["relu1"]))
         rec(4)
 
-    for _ in range(3):
+    for _ in range(warmup):
         run()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(20)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
     for ev in evs:
         run(ev)
     torch.cuda.synchronize()
@@ -391,10 +399,37 @@ def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms):
         gbs = bytes_per_elem * n / (t / 1e3) / 1e9
         return {"ms": t, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
                 "bytes_per_element": bytes_per_elem}
-    return {"ms": sum(ms), "fused_ms": fused_ms, "speedup_of_fusion": sum(ms) / fused_ms,
-            "relu_ms": ms[3], "equal_to_fused": same,
+    return {"ms": sum(ms), "fused_ms": fused_ms,
+            "speedup_of_fusion": sum(ms) / fused_ms if fused_ms else None,
+            "relu_ms": ms[3], "equal_to_fused": same if fused_ms else None,
             "hbm_kernels": {"mul_beaver": hbm(ms[0], 48), "trunc_prob": hbm(ms[1], 32),
                             "trunc_det": hbm(ms[2], 32)}}
+
+
+def chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev):
+    """`--step chain`: the step as four launches through HBM (the standalone
+    kernels of the C-ABI), each timed with CUDA events on its stream; the
+    ReLU kernel's roofline is reported."""
+    import torch
+    from paper_2309_04909_gb300 import costmodel
+    from paper_2309_04909_gb300.replicas import max_over_ranks
+    r = chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, None, steps=args.steps,
+                    warmup=max(3, args.warmup))
+    total = max_over_ranks(r["ms"], device=dev)
+    muls = costmodel.mul_ops_per_element(LX, RING, relu=True)
+    peak = costmodel.int_mul_peak_ops()
+    achieved = muls * n / (r["relu_ms"] / 1e3)
+    line = {"metric": METRIC, "value": n * world / (total / 1e3), "unit": "elems/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (four launches)", "n": n},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
+                         "mul_ops_per_element": muls, "kernel_ms": r["relu_ms"]},
+            "gpu_launches": 4 * args.steps, "chain": r}
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
 
 
 def _host_step_inputs(x0, x1, y0, y1, n):
