@@ -576,7 +576,8 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
         plain()
     plain_graph_ms = time_ms(g.replay, reps=5, warmup=1)
     best = autotune(ctx, items, reps=2, use_cache=False)
-    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"])
+    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"],
+                  best["elems_per_thread"], best["slot_unroll"])
     batched_ms = time_ms(b.run, reps=5, warmup=1)
     b.capture()
     batched_graph_ms = time_ms(b.run, reps=5, warmup=1)
@@ -590,6 +591,7 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "batched_elems_per_s": total / (batched_graph_ms / 1e3),
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+            "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
             "persistent_best_ms": b_persist_ms(ctx, items),
             "status": b.status(), "identical_to_plain": identical}
 
@@ -758,7 +760,8 @@ def resnet18_batched(ctx, dev, batch=32):
         run_plain()
     plain_ms = time_ms(g.replay, reps=3, warmup=1)
     best = autotune(ctx, items, reps=1, use_cache=False)
-    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"])
+    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"],
+                  best["elems_per_thread"], best["slot_unroll"])
     b.capture()
     batched_ms = time_ms(b.run, reps=3, warmup=1)
     identical = all(torch.equal(a[3], p[3]) and torch.equal(a[4], p[4])
@@ -770,6 +773,7 @@ def resnet18_batched(ctx, dev, batch=32):
             "batched_elems_per_s": total / (batched_ms / 1e3),
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+            "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
             "status": b.status(), "identical_to_plain": bool(identical)}
 
 

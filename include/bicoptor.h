@@ -246,18 +246,28 @@ typedef struct {
 } bc_tensor_desc;
 
 /* Schedule of the batched launch (0 fields = library default).
- *   schedule     BC_SCHED_PERSISTENT: per parameter group, one persistent
- *                grid whose warps take tiles from an atomic work counter;
- *                BC_SCHED_GRID: one CTA per tile of 256 elements (the
- *                hardware CTA scheduler is the queue; tile_elems ignored)
- *   tile_elems   elements per queue tile (persistent schedule; default 512)
- *   ctas_per_sm  resident CTAs per SM of the persistent grid (0 = occupancy) */
+ *   schedule          BC_SCHED_PERSISTENT: per parameter group, one persistent
+ *                     grid whose warps take tiles from an atomic work counter;
+ *                     BC_SCHED_GRID: one CTA per tile of 256 x elems_per_thread
+ *                     elements (the hardware CTA scheduler is the queue;
+ *                     tile_elems ignored)
+ *   tile_elems        elements per queue tile (persistent schedule; default 512)
+ *   ctas_per_sm       resident CTAs per SM of the persistent grid (0 = occupancy)
+ *   elems_per_thread  grid schedule: 1, 2 or 4 elements per thread (default 1)
+ *   slot_unroll       unroll of the per-element key-bit loop over the lx + 1
+ *                     message slots: 1, 2 or 3 (0 = default 2); honoured for
+ *                     lx = 24 at l = 64 and lx = 14, 9 at l <= 32, other key
+ *                     widths use the default
+ * Results do not depend on any of these (randomness is keyed by tensor id and
+ * element index). Values out of range give BC_EINVAL. */
 #define BC_SCHED_PERSISTENT 0
 #define BC_SCHED_GRID 1
 typedef struct {
   int tile_elems;
   int ctas_per_sm;
   int schedule;
+  int elems_per_thread;
+  int slot_unroll;
 } bc_batch_config;
 
 /* Plan a batch: group the tensors by parameters (l, lx, c, p; at most 32

@@ -288,9 +288,11 @@ class Context:
 
     # -- batched ------------------------------------------------------------------
     def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0,
-                        schedule: int = 0):
+                        schedule: int = 0, elems_per_thread: int = 0, slot_unroll: int = 0):
         """items: (prm, s0, s1, o0, o1, tensor_id[, op[, elem_offset]]) per tensor;
-        schedule 0 = persistent tile queue, 1 = one CTA per 256-element tile."""
+        schedule 0 = persistent tile queue, 1 = one CTA per tile of 256 x
+        elems_per_thread elements; slot_unroll = unroll of the key-bit loop
+        (0 = default)."""
         arr = (TensorDesc * max(1, len(items)))()
         self._batch_keep = list(items)
         for i, it in enumerate(items):
@@ -301,15 +303,15 @@ class Context:
                 self._need(t, prm.ring_bits, nm)
             arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
                                 s0.numel(), tid, op, prm.c_struct(), off)
-        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule)
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule, elems_per_thread, slot_unroll)
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_plan(self._h, arr, len(items), ctypes.byref(cfg)))
 
     def relu_batch_plan_descs(self, descs, count: int, tile_elems: int = 0, ctas_per_sm: int = 0,
-                              schedule: int = 0):
+                              schedule: int = 0, elems_per_thread: int = 0, slot_unroll: int = 0):
         """Plan from a prepared ctypes array of TensorDesc (raw device
         pointers; the caller keeps the memory alive)."""
-        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule)
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule, elems_per_thread, slot_unroll)
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_plan(self._h, descs, count, ctypes.byref(cfg)))
 

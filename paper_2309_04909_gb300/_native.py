@@ -18,8 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libbicoptor.so")
-SOURCES = ["bc_relu.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu", "bc_parties.cu"]
-HEADERS = ["bc_device.cuh", "bc_internal.h"]
+SOURCES = ["bc_relu.cu", "bc_batch.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu",
+           "bc_parties.cu"]
+HEADERS = ["bc_device.cuh", "bc_element.cuh", "bc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 _lock = threading.Lock()
@@ -110,7 +111,8 @@ class PartyMsgs(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("tile_elems", c_int), ("ctas_per_sm", c_int), ("schedule", c_int)]
+    _fields_ = [("tile_elems", c_int), ("ctas_per_sm", c_int), ("schedule", c_int),
+                ("elems_per_thread", c_int), ("slot_unroll", c_int)]
 
 
 class LinearReluArgs(ctypes.Structure):

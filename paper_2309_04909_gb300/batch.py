@@ -4,8 +4,10 @@ A network's ReLU layers (and many inferences of uneven size) are planned once
 into a tile table (bc_relu_batch_plan) and run as a single persistent kernel
 (bc_relu_batch_run) whose CTAs pull tiles from an atomic counter.  The run is
 stream-capturable, so a ReluBatch can be replayed through a CUDA graph.
-The autotuner picks the tile size and CTAs per SM by timing the candidates on
-the actual tensors; its choice is cached per (tensor mix, GPU).
+The autotuner picks the schedule, the elements per thread (grid schedule), the
+tile size and CTAs per SM (persistent schedule) and the unroll of the key-bit
+loop by timing the candidates on the actual tensors; its choice is cached per
+(tensor mix, GPU).
 """
 from __future__ import annotations
 
@@ -20,18 +22,23 @@ from . import Context, Params, OP_RELU
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 TILE_CANDIDATES = (128, 256, 512, 1024, 2048)
+EPT_CANDIDATES = (1, 2, 4)
+UNROLL_CANDIDATES = (1, 2, 3)
 
 
 class ReluBatch:
     """items: (Params, s0, s1, o0, o1, tensor_id[, op]) per tensor."""
 
     def __init__(self, ctx: Context, items: Sequence[Tuple], tile_elems: int = 0,
-                 ctas_per_sm: int = 0, schedule: int = 0):
+                 ctas_per_sm: int = 0, schedule: int = 0, elems_per_thread: int = 0,
+                 slot_unroll: int = 0):
         self.ctx = ctx
         self.items = list(items)
         self.tile_elems = tile_elems
         self.ctas_per_sm = ctas_per_sm
         self.schedule = schedule
+        self.elems_per_thread = elems_per_thread
+        self.slot_unroll = slot_unroll
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.plan()
 
@@ -40,7 +47,8 @@ class ReluBatch:
         return int(sum(it[1].numel() for it in self.items))
 
     def plan(self):
-        self.ctx.relu_batch_plan(self.items, self.tile_elems, self.ctas_per_sm, self.schedule)
+        self.ctx.relu_batch_plan(self.items, self.tile_elems, self.ctas_per_sm, self.schedule,
+                                 self.elems_per_thread, self.slot_unroll)
         self.graph = None
 
     def run(self):
@@ -84,15 +92,18 @@ def time_ms(fn, reps: int = 5, warmup: int = 2) -> float:
 def _mix_key(items) -> str:
     rings = sorted({(it[0].ring_bits, it[0].lx) for it in items})
     total = sum(it[1].numel() for it in items)
-    return f"{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}|t{len(items)}"
+    return (f"v2|{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}"
+            f"|t{len(items)}")
 
 
 def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
              use_cache: bool = True) -> Dict[str, float]:
-    """Time the grid schedule and every persistent (tile, ctas_per_sm)
-    candidate on `items`; returns the best {"schedule", "tile_elems",
-    "ctas_per_sm", "ms"}.  Outputs of the tensors are written
-    (the protocol is deterministic, so reruns give identical results)."""
+    """Time the candidates on `items` and return the best {"schedule",
+    "tile_elems", "ctas_per_sm", "elems_per_thread", "slot_unroll", "ms"}:
+    the grid schedule at every (elements per thread, key-bit unroll), then
+    the persistent schedule at every (tile, CTAs per SM) with the best
+    unroll.  Outputs of the tensors are written (the protocol is
+    deterministic, so reruns give identical results)."""
     key = _mix_key(items)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
@@ -102,15 +113,25 @@ def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
             cache = {}
         if key in cache:
             return cache[key]
-    b = ReluBatch(ctx, items, 0, 0, schedule=1)
-    best = {"schedule": 1, "tile_elems": 256, "ctas_per_sm": 0,
-            "ms": time_ms(b.run, reps=reps, warmup=1)}
+    best = None
+
+    def consider(cfg):
+        nonlocal best
+        b = ReluBatch(ctx, items, cfg["tile_elems"], cfg["ctas_per_sm"], cfg["schedule"],
+                      cfg["elems_per_thread"], cfg["slot_unroll"])
+        ms = time_ms(b.run, reps=reps, warmup=1)
+        if best is None or ms < best["ms"]:
+            best = dict(cfg, ms=ms)
+
+    for ept in EPT_CANDIDATES:
+        for u in UNROLL_CANDIDATES:
+            consider({"schedule": 1, "tile_elems": 256 * ept, "ctas_per_sm": 0,
+                      "elems_per_thread": ept, "slot_unroll": u})
+    u = best["slot_unroll"]
     for tile in TILE_CANDIDATES:
         for cps in (0, 1, 2, 3):
-            b = ReluBatch(ctx, items, tile, cps, schedule=0)
-            ms = time_ms(b.run, reps=reps, warmup=1)
-            if ms < best["ms"]:
-                best = {"schedule": 0, "tile_elems": tile, "ctas_per_sm": cps, "ms": ms}
+            consider({"schedule": 0, "tile_elems": tile, "ctas_per_sm": cps,
+                      "elems_per_thread": 1, "slot_unroll": u})
     cache[key] = best
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

@@ -42,7 +42,7 @@ struct bc_ctx {
   unsigned int* d_counter = nullptr;     // one work counter per parameter group
   int* d_status = nullptr;
   uint32_t ntiles = 0;
-  int batch_ctas_per_sm = 0;
+  bc::BatchLaunch batch_launch{0, 1, 0};
   bc::BatchGroup groups[bc::kMaxBatchGroups];
   int ngroups = 0;
   bc_comm batch_comm{};                   // what one run of the plan adds
@@ -531,7 +531,12 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
   const bool grid_sched = cfg && cfg->schedule == BC_SCHED_GRID;
   if (cfg && cfg->schedule != BC_SCHED_GRID && cfg->schedule != BC_SCHED_PERSISTENT)
     return BC_EINVAL;
-  const int tile = grid_sched ? bc::kBlock : (cfg && cfg->tile_elems > 0) ? cfg->tile_elems : 512;
+  const int ept = cfg && cfg->elems_per_thread > 0 ? cfg->elems_per_thread : 1;
+  const int unroll = cfg ? cfg->slot_unroll : 0;
+  if ((grid_sched && ept != 1 && ept != 2 && ept != 4) || unroll < 0 || unroll > 3)
+    return BC_EINVAL;
+  const int tile = grid_sched ? bc::kBlock * ept
+                              : (cfg && cfg->tile_elems > 0) ? cfg->tile_elems : 512;
   if (tile > (1 << 30)) return BC_EINVAL;
   // persistent: CTAs per SM (0 = occupancy); grid schedule: -1
   const int per_sm = grid_sched ? -1 : (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : 0;
@@ -643,7 +648,7 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
   for (int g = 0; g < ngroups; ++g) ctx->groups[g] = groups[g];
   ctx->ngroups = ngroups;
   ctx->ntiles = (uint32_t)w;
-  ctx->batch_ctas_per_sm = per_sm;
+  ctx->batch_launch = bc::BatchLaunch{per_sm, grid_sched ? ept : 1, unroll};
   ctx->batch_comm = add;
   ctx->planned = true;
   return BC_OK;
@@ -654,7 +659,7 @@ int bc_relu_batch_run(bc_ctx* ctx) {
   BC_TRACE();
   CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int) * bc::kMaxBatchGroups, ctx->stream));
   CK(bc::launch_relu_batch(ctx->d_tensors, ctx->d_tiles, ctx->groups, ctx->ngroups,
-                           ctx->d_counter, ctx->d_status, ctx->num_sms, ctx->batch_ctas_per_sm,
+                           ctx->d_counter, ctx->d_status, ctx->num_sms, ctx->batch_launch,
                            ctx->stream));
   add_comm(&ctx->comm, ctx->batch_comm);
   return BC_OK;

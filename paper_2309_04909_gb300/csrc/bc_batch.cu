@@ -1,0 +1,207 @@
+// Batched DReLU/ReLU over many tensors (the batching of Alg. drelu / Alg.
+// relu across a network's layers and requests): one launch per parameter
+// group (l, lx, c, p) over that group's range of a tile table.
+//
+// Two schedules:
+//   grid        one CTA per tile of 256 x EPT elements, EPT elements per
+//               thread; the hardware CTA scheduler is the queue.
+//   persistent  one grid sized to residency whose warps take the next tile
+//               from the group's atomic counter (no block barrier, no waits),
+//               so uneven tensors balance down to one tile per warp.
+// Per-group kernels keep the register allocation of a single variant.  The
+// key-bit (message-slot) loop unroll UNROLL and EPT are template parameters
+// chosen per plan, so an autotuner can pick them; the key widths of the
+// benchmarked workloads (lx = 24 at l = 64, lx = 14 and 9 at l = 32) have
+// every variant, other widths take the generic kernel with the default
+// unroll.
+#include "bc_element.cuh"
+
+namespace bc {
+namespace {
+
+template <typename Lane, int LX, bool SHORT, bool RELU, int UNROLL>
+__device__ __forceinline__ void run_tile(const ReluConsts& k, const BatchTensor& bt,
+                                         uint64_t start, uint32_t count, uint32_t lane,
+                                         uint32_t* perm) {
+  const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
+  const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
+  Lane* o0 = static_cast<Lane*>(bt.o0);
+  Lane* o1 = static_cast<Lane*>(bt.o1);
+  const AuditPtrs none{};
+#pragma unroll 1
+  for (uint32_t j = lane; j < count; j += 32) {
+    const uint64_t i = start + j;
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+    o0[i] = r0;
+    o1[i] = r1;
+  }
+}
+
+template <typename Lane, int LX, bool SHORT, int UNROLL>
+__global__ void __launch_bounds__(kBlock)
+    relu_batch_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
+                      const BatchTile* __restrict__ tiles, uint32_t begin, uint32_t end,
+                      unsigned int* __restrict__ counter, int* __restrict__ status) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t tile = 0;
+    if (lane == 0) tile = begin + atomicAdd(counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= end) break;
+    const BatchTile tl = tiles[tile];
+    const BatchTensor bt = tensors[tl.tensor];
+    if (tl.start + tl.count > bt.n) {   // a malformed table: record, skip
+      if (lane == 0) atomicExch(status, BC_ECHECK);
+      continue;
+    }
+    if (bt.op == BC_OP_DRELU)
+      run_tile<Lane, LX, SHORT, false, UNROLL>(k, bt, tl.start, tl.count, lane, perm);
+    else
+      run_tile<Lane, LX, SHORT, true, UNROLL>(k, bt, tl.start, tl.count, lane, perm);
+  }
+}
+
+// Grid schedule: one CTA per tile of at most kBlock * EPT elements; thread t
+// takes elements t, t + kBlock, ... of the tile (coalesced at every step).
+// EPT = 1 has no loop, so nothing is kept live across elements.
+template <typename Lane, int LX, bool SHORT, bool RELU, int UNROLL, int EPT>
+__device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor& bt,
+                                          const BatchTile& tl, uint32_t* perm) {
+  const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
+  const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
+  Lane* o0 = static_cast<Lane*>(bt.o0);
+  Lane* o1 = static_cast<Lane*>(bt.o1);
+  const AuditPtrs none{};
+  if (EPT == 1) {
+    if (threadIdx.x >= tl.count) return;
+    const uint64_t i = tl.start + threadIdx.x;
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+    o0[i] = r0;
+    o1[i] = r1;
+    return;
+  }
+#pragma unroll 1
+  for (uint32_t j = threadIdx.x; j < tl.count; j += kBlock) {
+    const uint64_t i = tl.start + j;
+    Lane r0, r1;
+    bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+    o0[i] = r0;
+    o1[i] = r1;
+  }
+}
+
+template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>
+__global__ void __launch_bounds__(kBlock)
+    relu_batch_grid_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
+                           const BatchTile* __restrict__ tiles, uint32_t begin,
+                           int* __restrict__ status) {
+  __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  uint32_t* perm = perm_s + threadIdx.x;
+  const BatchTile tl = tiles[begin + blockIdx.x];
+  const BatchTensor bt = tensors[tl.tensor];
+  if (tl.count > (uint32_t)(kBlock * EPT) || tl.start + tl.count > bt.n) {   // malformed: skip
+    if (threadIdx.x == 0) atomicExch(status, BC_ECHECK);
+    return;
+  }
+  if (bt.op == BC_OP_DRELU)
+    grid_tile<Lane, LX, SHORT, false, UNROLL, EPT>(k, bt, tl, perm);
+  else
+    grid_tile<Lane, LX, SHORT, true, UNROLL, EPT>(k, bt, tl, perm);
+}
+
+template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>
+cudaError_t launch_grid(const BatchGroup& g, const BatchTensor* tensors, const BatchTile* tiles,
+                        int* status, cudaStream_t s) {
+  const uint32_t ntiles = g.end - g.begin;
+  if (ntiles == 0) return cudaSuccess;
+  relu_batch_grid_kernel<Lane, LX, SHORT, UNROLL, EPT>
+      <<<ntiles, kBlock, 0, s>>>(g.k, tensors, tiles, g.begin, status);
+  return cudaGetLastError();
+}
+
+template <typename Lane, int LX, bool SHORT, int UNROLL>
+cudaError_t launch_persistent(const BatchGroup& g, const BatchTensor* tensors,
+                              const BatchTile* tiles, unsigned int* counter, int* status,
+                              int num_sms, int ctas_per_sm, cudaStream_t s) {
+  auto kern = relu_batch_kernel<Lane, LX, SHORT, UNROLL>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  const uint64_t warps_needed = g.end - g.begin;             // at most one tile per warp
+  uint64_t grid = (uint64_t)num_sms * per_sm;
+  const uint64_t cap = (warps_needed * 32 + kBlock - 1) / kBlock;
+  if (cap < grid) grid = cap;
+  if (grid == 0) return cudaSuccess;
+  kern<<<(unsigned)grid, kBlock, 0, s>>>(g.k, tensors, tiles, g.begin, g.end, counter, status);
+  return cudaGetLastError();
+}
+
+template <typename Lane, int LX, bool SHORT, int UNROLL>
+cudaError_t launch_sched(const BatchGroup& g, const BatchTensor* tensors, const BatchTile* tiles,
+                         unsigned int* counter, int* status, int num_sms,
+                         const BatchLaunch& L, cudaStream_t s) {
+  if (L.ctas_per_sm >= 0)
+    return launch_persistent<Lane, LX, SHORT, UNROLL>(g, tensors, tiles, counter, status,
+                                                      num_sms, L.ctas_per_sm, s);
+  switch (L.elems_per_thread) {
+    case 2: return launch_grid<Lane, LX, SHORT, UNROLL, 2>(g, tensors, tiles, status, s);
+    case 4: return launch_grid<Lane, LX, SHORT, UNROLL, 4>(g, tensors, tiles, status, s);
+    default: return launch_grid<Lane, LX, SHORT, UNROLL, 1>(g, tensors, tiles, status, s);
+  }
+}
+
+// Key widths with every unroll variant.
+template <typename Lane, int LX, bool SHORT>
+cudaError_t launch_tuned(const BatchGroup& g, const BatchTensor* tensors, const BatchTile* tiles,
+                         unsigned int* counter, int* status, int num_sms, const BatchLaunch& L,
+                         cudaStream_t s) {
+  switch (L.slot_unroll) {
+    case 1:
+      return launch_sched<Lane, LX, SHORT, 1>(g, tensors, tiles, counter, status, num_sms, L, s);
+    case 3:
+      return launch_sched<Lane, LX, SHORT, 3>(g, tensors, tiles, counter, status, num_sms, L, s);
+    default:
+      return launch_sched<Lane, LX, SHORT, kSlotUnroll>(g, tensors, tiles, counter, status,
+                                                        num_sms, L, s);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
+                              const BatchGroup* groups, int ngroups, unsigned int* counters,
+                              int* status, int num_sms, const BatchLaunch& L, cudaStream_t s) {
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const BatchGroup& g = groups[gi];
+    if (g.end <= g.begin) continue;
+    unsigned int* ctr = counters + gi;
+    cudaError_t e;
+    if (g.k.ring_bits > 32) {
+      if (g.k.lx == 24 && g.k.c + g.k.lx < 32)
+        e = launch_tuned<uint64_t, 24, true>(g, tensors, tiles, ctr, status, num_sms, L, s);
+      else
+        e = launch_sched<uint64_t, 0, false, kSlotUnroll>(g, tensors, tiles, ctr, status, num_sms,
+                                                          L, s);
+    } else if (g.k.lx == 14) {
+      e = launch_tuned<uint32_t, 14, false>(g, tensors, tiles, ctr, status, num_sms, L, s);
+    } else if (g.k.lx == 9) {
+      e = launch_tuned<uint32_t, 9, false>(g, tensors, tiles, ctr, status, num_sms, L, s);
+    } else {
+      e = launch_sched<uint32_t, 0, false, kSlotUnroll>(g, tensors, tiles, ctr, status, num_sms,
+                                                        L, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace bc

@@ -1,0 +1,234 @@
+// The per-element body of Alg. drelu / Alg. relu, shared by the single-tensor,
+// fused-step and batched kernels.
+//
+// One thread owns one element at a time and runs, in registers, the local
+// work of all three parties:
+//   P0, P1  steps 1-2   flip both shares by (-1)^t, t from seed01
+//           step 3      windowed deterministic truncation (Alg. newtrc2) at
+//                       every key-bit position i = 0..lx
+//           step 4      pair sums v_i = u_i + u_(i+1) - 1
+//           step 5      Alg. modswitch into Z_p
+//           step 6      seed01 shuffle (Fisher-Yates, staged in shared memory)
+//           step 7-8    mask by r_k in Z_p^*, reshare by z_k
+//   P2      step 9      reconstruct each w_k and test it for zero
+//           step 10     reply: [DReLU']_1 to P1 (DReLU) or e = DReLU' - b (ReLU)
+//   P0, P1  step 11     unflip (DReLU) / Beaver finish (ReLU)
+// The lx+1 windows are never stored: message slot k recomputes the window of
+// the index i = perm[k] from the two shares, so the l-fold expansion of the
+// paper's step 3 costs two funnel shifts per slot and no memory traffic.
+// Draws shared by P0 and P1 (everything from seed01) are generated once per
+// element and used by both simulated parties.
+#pragma once
+#include "bc_internal.h"
+
+// Default unroll of the message-slot loop (compile-time).
+#ifndef BC_SLOT_UNROLL
+#define BC_SLOT_UNROLL 2
+#endif
+
+namespace bc {
+
+
+constexpr int kSlotUnroll = BC_SLOT_UNROLL;
+
+template <int LX, bool WIDE>
+struct SlotMath;
+
+// p fits in 31 bits (lx <= 30): sums of two residues stay below 2^32.
+template <int LX>
+struct SlotMath<LX, false> {
+  static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t s = a + b;
+    const uint32_t d = s - p;
+    return d < s ? d : s;   // s >= p  <=>  s - p does not wrap
+  }
+  static __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b, uint32_t p) {
+    const uint32_t d = a - b;
+    return a >= b ? d : d + p;
+  }
+};
+template <int LX>
+struct SlotMath<LX, true> {
+  static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b, uint32_t p) {
+    return add_mod(a, b, p);
+  }
+  static __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b, uint32_t p) {
+    return sub_mod(a, b, p);
+  }
+};
+
+template <typename Lane>
+__device__ __forceinline__ void store_lane(void* base, uint64_t i, Lane v) {
+  reinterpret_cast<Lane*>(base)[i] = v;
+}
+
+// The Beaver triple of the ReLU product for one element (Alg. relu
+// preprocessing): a0,b0,c0 from seed02, a1,b1 from seed12.
+template <typename Lane>
+struct Triple {
+  Lane a0, b0, c0, a1, b1;
+};
+
+template <typename Lane>
+__device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32_t purpose,
+                                                    Lane mask, const RoundKeys& rk) {
+  Triple<Lane> T;
+  const U32x4 q0 = ep.block_at(kPair02, purpose, 0, rk);
+  const U32x4 q1 = ep.block_at(kPair12, purpose, 0, rk);
+  if (sizeof(Lane) == 4) {
+    T.a0 = (Lane)q0.x;
+    T.b0 = (Lane)q0.y;
+    T.c0 = (Lane)q0.z;
+  } else {
+    const U32x4 q2 = ep.block_at(kPair02, purpose, 1, rk);
+    T.a0 = block_elem<Lane>(q0, 0);
+    T.b0 = block_elem<Lane>(q0, 1);
+    T.c0 = block_elem<Lane>(q2, 0);
+  }
+  T.a1 = block_elem<Lane>(q1, 0);
+  T.b1 = block_elem<Lane>(q1, 1);
+  T.a0 &= mask; T.b0 &= mask; T.c0 &= mask; T.a1 &= mask; T.b1 &= mask;
+  return T;
+}
+
+// The 32 window bits starting at bit sh of a lane.  SHORT: sh < 32 is known
+// (c + lx < 32), so a single funnel shift of the two halves suffices.
+template <bool SHORT>
+__device__ __forceinline__ uint32_t window32(uint64_t a, uint32_t sh) {
+  if (SHORT) return __funnelshift_r((uint32_t)a, (uint32_t)(a >> 32), sh);
+  return (uint32_t)(a >> sh);
+}
+template <bool SHORT>
+__device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
+  return a >> sh;
+}
+
+// Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
+// column of the shared-memory shuffle table (stride kBlock words).
+// DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
+// (the RSS protocol finishes differently).  UNROLL: unroll of the loop over
+// the lx + 1 message slots (the key-bit loop).
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false,
+          int UNROLL = kSlotUnroll>
+__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
+                                                 uint32_t tensor_id, Lane s0, Lane s1,
+                                                 uint64_t elem, uint32_t* perm, Lane& out0,
+                                                 Lane& out1, const AuditPtrs& aud,
+                                                 uint64_t out_idx) {
+  constexpr bool kWide = (LX == 0) || (LX > 30);
+  using M = SlotMath<LX, kWide>;
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  const uint32_t L = lx + 1;
+  const Lane mask = (Lane)k.ring_mask;
+  const uint32_t p = k.mp.p;
+  const ElemPhilox ep(elem, tensor_id);
+
+  // ---- seed01 stream: t (step 1) and the shuffle words (step 6) ----------
+#pragma unroll
+  for (uint32_t s = 0; s < (LX ? (uint32_t)(LX + 1) : (uint32_t)kMaxSlots); ++s) {
+    if (LX || s < L) perm[s * kBlock] = s;
+  }
+  uint32_t t = 0;
+  const uint32_t nblk = (L + 3) >> 2;
+  const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
+#pragma unroll
+  for (uint32_t b = 0; b < (LX ? (uint32_t)((LX + 4) >> 2) : 8u); ++b) {
+    if (!LX && b >= nblk) break;
+    const U32x4 wb = perm_stream.block((uint64_t)kPhiloxM1 * b, rk);
+    const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t widx = 4 * b + q;
+      if (widx == 0) {
+        t = ws[0] & 1u;
+      } else if (widx < L) {
+        // Fisher-Yates step j = lx + 1 - widx: partner = floor(W (j+1) / 2^32)
+        const uint32_t j = L - widx;
+        const uint32_t partner = __umulhi(ws[q], j + 1);
+        const uint32_t a = perm[j * kBlock];
+        const uint32_t c = perm[partner * kBlock];
+        perm[j * kBlock] = c;
+        perm[partner * kBlock] = a;
+      }
+    }
+  }
+
+  // ---- steps 1-2: flip by (-1)^t --------------------------------------------
+  const Lane f0 = t ? ring_neg(s0, mask) : s0;
+  const Lane nf1 = t ? s1 : ring_neg(s1, mask);   // 2^l - [x]_1 of the flipped share
+
+  // ---- steps 3-9 over message slots k ----------------------------------------
+  uint32_t any_zero = 0;
+  const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
+  uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
+#pragma unroll UNROLL
+  for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
+    const uint32_t i = perm[slot * kBlock];
+    const uint32_t sh = k.c + i;
+    const uint32_t y0 = window32<SHORT>(f0, sh);
+    const uint32_t y1 = window32<SHORT>(nf1, sh);
+    const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
+    // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
+    const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
+    const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
+    // step 5: Alg. modswitch
+    const uint32_t m0 = v0 ? v0 : k.two_lx;
+    const uint32_t m1 = v1 + k.p_minus_2lx;
+    // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
+    // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
+    const U32x4 rz = mask_stream.block(mb, rk);
+    const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+    const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
+    uint32_t w0 = mont_mul<kWide>(m0, rho, k.mp);
+    uint32_t w1 = mont_mul<kWide>(m1, rho, k.mp);
+    // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
+    w0 = M::add(w0, z, p);
+    w1 = M::sub(w1, z, p);
+    if (AUDIT) {
+      if (aud.w0) aud.w0[out_idx * L + slot] = w0;
+      if (aud.w1) aud.w1[out_idx * L + slot] = w1;
+    }
+    // step 9: P2 reconstructs w_k and tests it
+    any_zero |= (M::add(w0, w1, p) == 0u) ? 1u : 0u;
+  }
+  const uint32_t dprime = any_zero;
+  if (DPONLY) {
+    out0 = (Lane)dprime;
+    out1 = (Lane)t;
+    return;
+  }
+
+  if (!RELU) {
+    // step 10: [DReLU']_0 = d0 from seed02 (P0 derives it), [DReLU']_1 to P1
+    const U32x4 rb = ep.block_at(kPair02, kPurReply, 0, rk);
+    const Lane d0 = block_elem<Lane>(rb, 0) & mask;
+    const Lane d1 = ((Lane)dprime - d0) & mask;
+    // step 11: [DReLU] = [DReLU' xor t], the public t added by P0
+    out0 = t ? (Lane)((Lane)1 - d0) & mask : d0;
+    out1 = t ? ring_neg(d1, mask) : d1;
+    if (AUDIT && aud.reply) store_lane<Lane>(aud.reply, out_idx, d1);
+  } else {
+    const Triple<Lane> T = draw_triple<Lane>(ep, kPurReluTriple, mask, rk);
+    const Lane c1 = (Lane)((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0) & mask;   // P2 -> P1 (pre)
+    const Lane e = (Lane)((Lane)dprime - T.b0 - T.b1) & mask;             // P2 -> P0, P1
+    const Lane open0 = (Lane)(s0 - T.a0) & mask;                          // P0 -> P1
+    const Lane open1 = (Lane)(s1 - T.a1) & mask;                          // P1 -> P0
+    const Lane d = (Lane)(open0 + open1) & mask;
+    const Lane xd0 = (Lane)(d * (e + T.b0) + e * T.a0 + T.c0) & mask;
+    const Lane xd1 = (Lane)(d * T.b1 + e * T.a1 + c1) & mask;
+    out0 = t ? (Lane)(s0 - xd0) & mask : xd0;
+    out1 = t ? (Lane)(s1 - xd1) & mask : xd1;
+    if (AUDIT) {
+      if (aud.reply) store_lane<Lane>(aud.reply, out_idx, e);
+      if (aud.open0) store_lane<Lane>(aud.open0, out_idx, open0);
+      if (aud.open1) store_lane<Lane>(aud.open1, out_idx, open1);
+      if (aud.pre_c1) store_lane<Lane>(aud.pre_c1, out_idx, c1);
+    }
+  }
+  if (AUDIT) {
+    if (aud.t) aud.t[out_idx] = (uint8_t)t;
+    if (aud.dprime) aud.dprime[out_idx] = (uint8_t)dprime;
+  }
+}
+
+}  // namespace bc

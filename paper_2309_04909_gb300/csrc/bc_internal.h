@@ -70,13 +70,21 @@ struct BatchGroup {
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
                         cudaStream_t s);
-// Launches one kernel per non-empty group.  ctas_per_sm >= 0: persistent
-// schedule (0 = occupancy), `counters` holds one zeroed work counter per
-// group.  ctas_per_sm < 0: grid schedule, one CTA per tile of <= kBlock
-// elements (counters unused).
+// Launch shape of a batched run.  ctas_per_sm >= 0: persistent schedule
+// (0 = occupancy).  ctas_per_sm < 0: grid schedule, one CTA per tile of at
+// most kBlock * elems_per_thread elements (1, 2 or 4).  slot_unroll: unroll of
+// the key-bit loop (1, 2 or 3; 0 = default).
+struct BatchLaunch {
+  int ctas_per_sm;
+  int elems_per_thread;
+  int slot_unroll;
+};
+// Launches one kernel per non-empty group; for the persistent schedule
+// `counters` holds one zeroed work counter per group.
 cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
                               const BatchGroup* groups, int ngroups, unsigned int* counters,
-                              int* status, int num_sms, int ctas_per_sm, cudaStream_t s);
+                              int* status, int num_sms, const BatchLaunch& launch,
+                              cudaStream_t s);
 
 // The fused step of a linear layer followed by a ReLU: Beaver product of
 // [x][y], Alg. smltrc and Alg. newtrc2 of the product by `trunc` bits, and

@@ -181,8 +181,8 @@ extern "C" int bc_relu_batch_static(uint64_t seed, int device, void* cuda_stream
       rc = BC_ECUDA;
       break;
     }
-    if (bc::launch_relu_batch(d_tensors, d_tiles, groups, ngroups, counters, status, num_sms, 0,
-                              s) != cudaSuccess)
+    if (bc::launch_relu_batch(d_tensors, d_tiles, groups, ngroups, counters, status, num_sms,
+                              bc::BatchLaunch{0, 1, 0}, s) != cudaSuccess)
       rc = BC_ECUDA;
   } while (0);
   if (prev != device) cudaSetDevice(prev);

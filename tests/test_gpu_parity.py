@@ -308,15 +308,30 @@ def test_batch_matches_single_calls(ctx):
         items.append((prm, s0, s1, o0, o1, 900 + ti, 1 if op else 0))
         fn = ctx.drelu if op else ctx.relu
         singles.append(fn(prm, s0, s1, tensor_id=900 + ti))
-    for tile, sched, cps in ((0, 0, 0), (1000, 0, 2), (4096, 0, 1), (0, 1, 0)):
+    # (tile, schedule, CTAs per SM, elements per thread, key-bit unroll)
+    for tile, sched, cps, ept, unroll in ((0, 0, 0, 0, 0), (1000, 0, 2, 0, 3), (4096, 0, 1, 0, 1),
+                                          (0, 1, 0, 0, 0), (0, 1, 0, 2, 1), (0, 1, 0, 4, 3),
+                                          (0, 1, 0, 4, 2)):
         for it in items:
             it[3].fill_(0)
             it[4].fill_(0)
-        ctx.relu_batch_plan(items, tile_elems=tile, ctas_per_sm=cps, schedule=sched)
+        ctx.relu_batch_plan(items, tile_elems=tile, ctas_per_sm=cps, schedule=sched,
+                            elems_per_thread=ept, slot_unroll=unroll)
         ctx.relu_batch_run()
         assert ctx.batch_status() == 0
         for it, (r0, r1) in zip(items, singles):
             assert torch.equal(it[3], r0) and torch.equal(it[4], r1)
+
+
+def test_batch_config_out_of_range_rejected(ctx):
+    from paper_2309_04909_gb300 import BicoptorError
+    s = torch.zeros(1000, dtype=torch.int64, device="cuda")
+    o = torch.empty_like(s)
+    items = [(Params(64, 24, 0), s, s, o, o, 1)]
+    for kw in ({"schedule": 1, "elems_per_thread": 3}, {"schedule": 1, "elems_per_thread": 8},
+               {"slot_unroll": 4}, {"slot_unroll": -1}):
+        with pytest.raises(BicoptorError):
+            ctx.relu_batch_plan(items, **kw)
 
 
 def test_full_size_config2_sampled(ctx):
