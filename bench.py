@@ -533,6 +533,14 @@ def trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev):
     return out
 
 
+def batched_frac(parts, ms):
+    """Fraction of the integer-multiplier roofline reached by a batched ReLU
+    run: parts = (elements, l, lx) of each parameter class."""
+    from paper_2309_04909_gb300 import costmodel
+    ops = sum(n * costmodel.mul_ops_per_element(lx, ring, relu=True) for n, ring, lx in parts)
+    return ops / (ms / 1e3) / costmodel.int_mul_peak_ops()
+
+
 def b_persist_ms(ctx, items):
     """Best persistent-schedule time over the autotuner's tile candidates."""
     from paper_2309_04909_gb300.batch import TILE_CANDIDATES, ReluBatch, time_ms
@@ -589,6 +597,7 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "speedup_vs_plain_eager": plain_ms / batched_graph_ms,
             "speedup_vs_plain_graph": plain_graph_ms / batched_graph_ms,
             "batched_elems_per_s": total / (batched_graph_ms / 1e3),
+            "batched_roofline_frac": batched_frac([(total, 64, 24)], batched_graph_ms),
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
@@ -771,6 +780,8 @@ def resnet18_batched(ctx, dev, batch=32):
             "plain_graph_ms": plain_ms, "batched_graph_ms": batched_ms,
             "speedup_vs_plain_graph": plain_ms / batched_ms,
             "batched_elems_per_s": total / (batched_ms / 1e3),
+            "batched_roofline_frac": batched_frac([(total // 2, 64, 24), (total // 2, 32, 14)],
+                                                  batched_ms),
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
