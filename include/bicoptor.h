@@ -370,6 +370,25 @@ int bc_reserve(bc_ctx *ctx, size_t chunk);
 int bc_count_trunc_failures(bc_ctx *ctx, int out_bits, int k, const int64_t *x, const void *o0,
                             const void *o1, size_t n, unsigned long long *count);
 
+/* ---- integer-pipe microbenchmarks (measuring aid) ------------------------ */
+
+/* The paper has no counterpart: this measures, on `device`, the rates of the
+ * integer instructions the hot path is bound by, for its roofline.  Each
+ * kernel keeps 8 independent chains per thread over 8 CTAs of 256 threads per
+ * SM (the widening products run as Philox-4x32 rounds, the hot path's form);
+ * the best of three runs is reported, in warp-lane instructions per
+ * second, plus the SM clock one CTA saw (cycle counter against the global
+ * timer).  Allocates a few bytes and a stream, runs about 0.3 s, synchronises;
+ * BC_ECUDA on a CUDA failure. */
+typedef struct {
+  double imad_wide_per_s;   /* 32x32->64 products, in Philox rounds          */
+  double imad_per_s;        /* 32-bit multiply-adds                           */
+  double alu_per_s;         /* integer-ALU instructions (xor, add pairs)      */
+  double sm_mhz;            /* SM clock during the last run                   */
+  int sm_count;
+} bc_int_peaks;
+int bc_measure_int_peaks(int device, bc_int_peaks *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libbicoptor.so")
 SOURCES = ["bc_relu.cu", "bc_batch.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu",
-           "bc_parties.cu"]
+           "bc_parties.cu", "bc_peaks.cu"]
 HEADERS = ["bc_device.cuh", "bc_element.cuh", "bc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -115,6 +115,12 @@ class BatchConfig(ctypes.Structure):
                 ("elems_per_thread", c_int), ("slot_unroll", c_int)]
 
 
+class IntPeaks(ctypes.Structure):
+    _fields_ = [("imad_wide_per_s", ctypes.c_double), ("imad_per_s", ctypes.c_double),
+                ("alu_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("sm_count", c_int)]
+
+
 class LinearReluArgs(ctypes.Structure):
     _fields_ = [("ring_bits", c_int), ("trunc_bits", c_int), ("relu", DreluParams),
                 ("x0", c_void_p), ("x1", c_void_p), ("y0", c_void_p), ("y1", c_void_p),
@@ -158,6 +164,7 @@ SIGNATURES = {
     "bc_reserve": (c_int, [c_void_p, c_size]),
     "bc_set_host_path": (c_int, [c_void_p, c_int]),
     "bc_set_checked": (c_int, [c_void_p, c_int]),
+    "bc_measure_int_peaks": (c_int, [c_int, P(IntPeaks)]),
     "bc_count_trunc_failures": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                         c_size, c_void_p]),
     "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),

@@ -84,6 +84,29 @@ def linear_relu_int_ops_per_element(lx: int, ring_bits: int) -> int:
     return product_int_ops_per_element(ring_bits) + int_ops_per_element(lx, ring_bits, True)
 
 
+def mul_counts(lx: int, ring_bits: int, relu: bool = True, product: bool = False):
+    """(widening 32x32->64 products, single 32-bit products) per element, the
+    split of the multiplier lane-operations above (a widening product is 2 of
+    them): Philox 20 widening per block; per slot two 64x32 high products
+    (1 widening + 1 single each) and two Montgomery products (2 widening + 1
+    single each); lx single for the shuffle; a 64-bit ring product is 1
+    widening + 2 single (l > 32) or 1 single."""
+    L = lx + 1
+    wide = philox_blocks(lx, ring_bits, relu) * 20 + L * 6
+    single = L * 4 + lx
+    if relu:
+        if ring_bits > 32:
+            wide, single = wide + 5, single + 10
+        else:
+            single += 5
+    if product:
+        if ring_bits > 32:
+            wide, single = wide + 3 * 20 + 6, single + 12
+        else:
+            wide, single = wide + 2 * 20, single + 6
+    return wide, single
+
+
 def hbm_bytes_per_element_linear_relu(ring_bits: int, det_bits: int = 48) -> int:
     """Fused step: read x0, x1, y0, y1; write the ReLU and the deterministic
     truncation shares (det lanes 8 bytes when l - k > 32)."""
