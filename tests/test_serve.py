@@ -128,3 +128,28 @@ def test_engine_cancellation_and_deadlines():
             assert r.deadline_s is not None
     # no chunk of a dropped request was launched after it was dropped
     assert all(r.done <= r.elements for r in reqs)
+
+
+def test_engine_under_load_simulated():
+    """The serving trace on a simulated device of the measured batched
+    capacity: below capacity every request finishes within a few of its own
+    service times and throughput follows the offered load; above it the
+    device stays saturated and the queue grows."""
+    from paper_2309_04909_gb300 import workloads as W
+    per = {"vgg16": sum(W.VGG16_32_LAYERS), "lenet": sum(W.LENET_28_LAYERS)}
+    cap = 7.7e9
+    mean = 0.5 * 32.5 * (per["vgg16"] + per["lenet"])
+    out = {}
+    for frac in (0.5, 1.2):
+        trace = W.serving_trace(frac * cap / mean, 1.0, seed=4)
+        reqs = [ServeRequest(r.rid, r.arrival_s, r.images * per[r.net], r.net, r.images)
+                for r in trace]
+        st = Engine(FakeExecutor(cap), 40 << 30).run(reqs)
+        assert st.completed == len(reqs)
+        out[frac] = st.summary()
+    half, over = out[0.5], out[1.2]
+    largest = 64 * per["vgg16"] / cap * 1e3                 # ms of the largest request alone
+    assert half["p99_ms"] < 4 * largest and half["max_waiting"] < 20
+    assert abs(half["elems_per_s"] / (0.5 * cap) - 1) < 0.15
+    assert over["elems_per_s"] > 0.95 * cap                   # saturated
+    assert over["p50_ms"] > 20 * half["p50_ms"] and over["max_waiting"] > 100
