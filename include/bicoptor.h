@@ -106,7 +106,8 @@ int bc_synchronize(bc_ctx *ctx);
  * on the GPU the input lanes that are not canonical (a bit at or above l set;
  * l = 32 and l = 64 lanes always are), waits for the count, and returns
  * BC_EINVAL without launching the operation if any lane fails.  The wait
- * makes every checked call synchronous with the context stream. */
+ * makes every checked call synchronous with the context stream.
+ * bc_linear_relu_host scans its host inputs on the host instead. */
 int bc_set_checked(bc_ctx *ctx, int on);
 const char *bc_strerror(int code);
 /* Text of the last CUDA error seen by this context (empty if none). */

@@ -706,6 +706,22 @@ int linear_relu_device(bc_ctx* ctx, const bc_linear_relu_args* a, const bc::Line
   return BC_OK;
 }
 
+// Checked mode on host buffers: every lane of the n-lane array below 2^ring_bits
+// (scanned where the data lives, before anything is copied or launched).
+bool host_canonical(const void* a, size_t n, int ring_bits) {
+  if (ring_bits == 32 || ring_bits == 64) return true;
+  if (ring_bits < 32) {
+    const uint32_t* v = static_cast<const uint32_t*>(a);
+    for (size_t i = 0; i < n; ++i)
+      if (v[i] >> ring_bits) return false;
+  } else {
+    const uint64_t* v = static_cast<const uint64_t*>(a);
+    for (size_t i = 0; i < n; ++i)
+      if (v[i] >> ring_bits) return false;
+  }
+  return true;
+}
+
 // Device address of a host pointer that the GPU can load from and store to
 // (page-locked memory of the CUDA allocator or registered with it), else NULL.
 void* mapped_host(const void* p) {
@@ -781,6 +797,9 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   const bool det = a->det0 != nullptr;
   if (a->n == 0) return BC_OK;
   BC_TRACE();
+  if (ctx->checked)
+    for (const void* h : {a->x0, a->x1, a->y0, a->y1})
+      if (!host_canonical(h, a->n, a->ring_bits)) return BC_EINVAL;
   // direct path: every buffer is mapped page-locked memory, so the fused
   // kernel loads the inputs and stores the outputs across the host link
   const void* hp[8] = {a->x0, a->x1, a->y0, a->y1, a->relu0, a->relu1, a->det0, a->det1};

@@ -71,3 +71,25 @@ def test_audit_comparison_catches_one_corrupted_message(ctx):
     w0[1234, 7] ^= 1                                  # one bit of one message
     assert not np.array_equal(w0, eaud["w0"])
     assert np.argwhere(w0 != eaud["w0"]).tolist() == [[1234, 7]]
+
+
+def test_checked_host_buffers(ctx):
+    """The host-buffer step in checked mode refuses a non-canonical host lane
+    before anything runs; canonical inputs give the unchecked result."""
+    ring, k, n = 48, 8, 5001
+    prm = Params(ring, 11, 2)
+    x0, x1 = _shares(ctx, ring, n, 11, seed=1)
+    y0, y1 = _shares(ctx, ring, n, 12, seed=2)
+    hx = [t.cpu().pin_memory() for t in (x0, x1, y0, y1)]
+    want = {nm: torch.empty(n, dtype=torch.int64).pin_memory() for nm in ("relu0", "relu1")}
+    ctx.linear_relu_host(ring, k, prm, *hx, tensor_id=13, out=want)
+    ctx.set_checked(True)
+    got = {nm: torch.full((n,), 7, dtype=torch.int64).pin_memory() for nm in ("relu0", "relu1")}
+    ctx.linear_relu_host(ring, k, prm, *hx, tensor_id=13, out=got)
+    assert all(torch.equal(got[nm], want[nm]) for nm in got)
+    bad = [t.clone().pin_memory() for t in hx]
+    bad[2][77] |= 1 << ring
+    fresh = {nm: torch.full((n,), 7, dtype=torch.int64).pin_memory() for nm in ("relu0", "relu1")}
+    with pytest.raises(BicoptorError):
+        ctx.linear_relu_host(ring, k, prm, *bad, tensor_id=13, out=fresh)
+    assert all(bool((t == 7).all()) for t in fresh.values())
