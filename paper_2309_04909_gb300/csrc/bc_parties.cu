@@ -43,8 +43,9 @@ __device__ __forceinline__ uint32_t seed01_shuffle(const ElemPhilox& ep, uint32_
   for (uint32_t s = 0; s < L; ++s) perm[s * kPB] = s;
   uint32_t t = 0;
   const uint32_t nblk = (L + 3) >> 2;
+  const StreamPhilox stream(ep, kPair01, kPurPerm, rk);
   for (uint32_t b = 0; b < nblk; ++b) {
-    const U32x4 wb = ep.block_at(kPair01, kPurPerm, b, rk);
+    const U32x4 wb = stream.block((uint64_t)kPhiloxM1 * b, rk);
     const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kPB)
   // steps 1-2 and the P1 pre-negation: P0 keeps [x]_0 (flipped), P1 keeps
   // 2^l - [x]_1 of its flipped share
   const Lane f = party == 0 ? (t ? ring_neg(s, mask) : s) : (t ? s : ring_neg(s, mask));
+  const StreamPhilox mask_stream(ep, kPair01, kPurMask, k.rk);
   uint64_t mb = 0;
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     const uint32_t ii = perm[slot * kPB];
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kPB)
       const uint32_t v = (0u - (y & k.mx) - ((y >> 1) & next_mask)) & k.mx;
       m = v + k.p_minus_2lx;
     }
-    const U32x4 rz = ep.block(kPair01, kPurMask, mb, k.rk);                  // step 7
+    const U32x4 rz = mask_stream.block(mb, k.rk);                             // step 7
     const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
     uint32_t w = mont_mul(m, rho, k.mp);
@@ -171,6 +173,9 @@ __global__ void __launch_bounds__(kPB)
   const Lane mask = (Lane)k.ring_mask;
   const uint64_t g = i >> 5;
   uint32_t any_zero = 0;
+  // the slots are independent (only the OR accumulates), so unrolling lets
+  // the loads of several slots be in flight at once
+#pragma unroll 5
   for (uint32_t slot = 0; slot < L; ++slot) {                // step 9
     const uint64_t off = (slot * a.groups + g) * B;
     const uint32_t w0 = unpack(a.w[0] + off, B, lane);
