@@ -242,10 +242,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)          # before NCCL, so each rank binds its own GPU
+    dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
 
     n = args.n
     xi, yi = workload_inputs(n, seed=SEED + rank)   # each rank its own batch (replicas)
