@@ -122,3 +122,10 @@ def test_host_direct_rejects_pageable(ctx):
             ctx.linear_relu_host(64, 16, Params(64, 24, 0), *hx, tensor_id=1, out=out)
     finally:
         ctx.set_host_path(ctx.HOST_AUTO)
+
+
+def test_host_path_value_checked(ctx):
+    for bad in (-1, 3, 99):
+        with pytest.raises(BicoptorError):
+            ctx.set_host_path(bad)
+    ctx.set_host_path(ctx.HOST_AUTO)
