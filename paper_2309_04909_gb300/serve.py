@@ -155,12 +155,22 @@ class ServeStats:
                 return None
             return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
 
+        # latency histogram: counts per power-of-two bucket of milliseconds,
+        # keyed by the bucket's upper edge ("<=1", "<=2", ..., ">1024")
+        hist: Dict[str, int] = {}
+        for v in lat:
+            ms, edge = 1e3 * v, 1.0
+            while ms > edge and edge <= 1024.0:
+                edge *= 2.0
+            key = f"<={edge:g}" if edge <= 1024.0 else ">1024"
+            hist[key] = hist.get(key, 0) + 1
         return {"requests": self.requests, "completed": self.completed,
                 "elements": self.elements, "wall_s": self.wall_s,
                 "elems_per_s": self.elements / self.wall_s if self.wall_s > 0 else 0.0,
                 "p50_ms": None if not lat else 1e3 * pct(0.50),
                 "p99_ms": None if not lat else 1e3 * pct(0.99),
                 "max_ms": None if not lat else 1e3 * lat[-1],
+                "latency_histogram_ms": hist,
                 "iterations": self.iterations, "peak_bytes": self.peak_bytes,
                 "max_waiting": self.max_waiting, "rejected": self.rejected,
                 "expired": self.expired, "cancelled": self.cancelled}

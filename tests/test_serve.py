@@ -4,7 +4,7 @@ import random
 
 import pytest
 
-from paper_2309_04909_gb300.serve import Arena, Engine, FakeExecutor, ServeRequest
+from paper_2309_04909_gb300.serve import Arena, Engine, FakeExecutor, ServeRequest, ServeStats
 
 
 def test_arena_first_fit_and_coalescing():
@@ -153,3 +153,10 @@ def test_engine_under_load_simulated():
     assert abs(half["elems_per_s"] / (0.5 * cap) - 1) < 0.15
     assert over["elems_per_s"] > 0.95 * cap                   # saturated
     assert over["p50_ms"] > 20 * half["p50_ms"] and over["max_waiting"] > 100
+
+
+def test_latency_histogram():
+    st = ServeStats(5, 5, 10, 1.0, [0.0005, 0.0015, 0.003, 0.003, 2.0], 1, 0, 0)
+    h = st.summary()["latency_histogram_ms"]
+    assert h == {"<=1": 1, "<=2": 1, "<=4": 2, ">1024": 1}
+    assert sum(h.values()) == 5
