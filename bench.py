@@ -365,6 +365,7 @@ def main():
                                                 line["unfused_chain"]["relu_ms"])
         line["rss_relu"] = rss_bench(ctx, prm, buf, n)
         line["drelu_l32_uniform"] = uniform_l32_drelu_check(ctx, dev)
+        line["size_sweep_l64"] = size_sweep(ctx, dev)
         line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
         line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
         line["serving"] = serving_bench(ctx, dev, bvp["batched_elems_per_s"],
@@ -698,6 +699,35 @@ def parties_bench(ctx, prm, buf, n, fused_ms):
             "message_bytes_per_element": msg_bytes / n,
             "protocol_bits_per_element_p0_to_p2": (prm.lx + 1) ** 2,
             "identical_to_fused": same, "launches": 3}
+
+
+def size_sweep(ctx, dev):
+    """DReLU and ReLU throughput against batch size on device-resident
+    shares, l = 64: at the paper's key width lx = 7 (its unit-test setting)
+    and at lx = 24; one launch per call, CUDA events.  Small batches show
+    the fixed launch cost; large ones the kernel's rate."""
+    import torch
+    from paper_2309_04909_gb300 import Params
+    from paper_2309_04909_gb300.batch import time_ms
+    out = {}
+    nmax = 10 ** 8
+    g = torch.Generator(device=dev).manual_seed(5)
+    s0 = torch.randint(-2**62, 2**62, (nmax,), device=dev, generator=g)
+    s1 = torch.randint(-2**62, 2**62, (nmax,), device=dev, generator=g)
+    o0, o1 = torch.empty_like(s0), torch.empty_like(s1)
+    for lx in (7, 24):
+        prm = Params(64, lx, 0)
+        for op in ("drelu", "relu"):
+            fn = ctx.drelu if op == "drelu" else ctx.relu
+            row = {}
+            for e in range(3, 9):
+                n = 10 ** e
+                a, b, c, d = s0[:n], s1[:n], o0[:n], o1[:n]
+                ms = time_ms(lambda: fn(prm, a, b, 5, out=(c, d)), reps=10 if e < 8 else 3,
+                             warmup=2)
+                row[f"1e{e}"] = {"ms": ms, "elems_per_s": n / (ms / 1e3)}
+            out[f"{op}_lx{lx}"] = row
+    return out
 
 
 def uniform_l32_drelu_check(ctx, dev):
