@@ -702,10 +702,12 @@ def parties_bench(ctx, prm, buf, n, fused_ms):
 
 
 def size_sweep(ctx, dev):
-    """DReLU and ReLU throughput against batch size on device-resident
-    shares, l = 64: at the paper's key width lx = 7 (its unit-test setting)
-    and at lx = 24; one launch per call, CUDA events.  Small batches show
-    the fixed launch cost; large ones the kernel's rate."""
+    """DReLU and ReLU against batch size on device-resident shares, l = 64:
+    at the paper's key width lx = 7 (its unit-test setting) and at lx = 24.
+    Ten calls are replayed from a CUDA graph, so the time is the GPU's (a
+    launch of up to about 10^5 elements runs the four-lanes-per-element
+    kernel); `eager_us_per_call` is the same call made from Python, whose
+    host cost dominates at small batches."""
     import torch
     from paper_2309_04909_gb300 import Params
     from paper_2309_04909_gb300.batch import time_ms
@@ -715,6 +717,7 @@ def size_sweep(ctx, dev):
     s0 = torch.randint(-2**62, 2**62, (nmax,), device=dev, generator=g)
     s1 = torch.randint(-2**62, 2**62, (nmax,), device=dev, generator=g)
     o0, o1 = torch.empty_like(s0), torch.empty_like(s1)
+    side = torch.cuda.Stream()
     for lx in (7, 24):
         prm = Params(64, lx, 0)
         for op in ("drelu", "relu"):
@@ -723,9 +726,21 @@ def size_sweep(ctx, dev):
             for e in range(3, 9):
                 n = 10 ** e
                 a, b, c, d = s0[:n], s1[:n], o0[:n], o1[:n]
-                ms = time_ms(lambda: fn(prm, a, b, 5, out=(c, d)), reps=10 if e < 8 else 3,
-                             warmup=2)
+                call = lambda: fn(prm, a, b, 5, out=(c, d))
+                reps = 10 if e < 8 else 2
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(side):
+                    call()
+                torch.cuda.current_stream().wait_stream(side)
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(reps):
+                        call()
+                ms = time_ms(graph.replay, reps=3, warmup=1) / reps
                 row[f"1e{e}"] = {"ms": ms, "elems_per_s": n / (ms / 1e3)}
+                if e == 3:
+                    row["eager_us_per_call"] = 1e3 * time_ms(call, reps=20, warmup=3)
             out[f"{op}_lx{lx}"] = row
     return out
 

@@ -69,18 +69,17 @@ struct Triple {
   Lane a0, b0, c0, a1, b1;
 };
 
+// The triple from its Philox blocks: q0 = seed02 block 0, q1 = seed12 block
+// 0, q2 = seed02 block 1 (used for l > 32 only).
 template <typename Lane>
-__device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32_t purpose,
-                                                    Lane mask, const RoundKeys& rk) {
+__device__ __forceinline__ Triple<Lane> triple_from_blocks(const U32x4& q0, const U32x4& q1,
+                                                           const U32x4& q2, Lane mask) {
   Triple<Lane> T;
-  const U32x4 q0 = ep.block_at(kPair02, purpose, 0, rk);
-  const U32x4 q1 = ep.block_at(kPair12, purpose, 0, rk);
   if (sizeof(Lane) == 4) {
     T.a0 = (Lane)q0.x;
     T.b0 = (Lane)q0.y;
     T.c0 = (Lane)q0.z;
   } else {
-    const U32x4 q2 = ep.block_at(kPair02, purpose, 1, rk);
     T.a0 = block_elem<Lane>(q0, 0);
     T.b0 = block_elem<Lane>(q0, 1);
     T.c0 = block_elem<Lane>(q2, 0);
@@ -89,6 +88,15 @@ __device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32
   T.b1 = block_elem<Lane>(q1, 1);
   T.a0 &= mask; T.b0 &= mask; T.c0 &= mask; T.a1 &= mask; T.b1 &= mask;
   return T;
+}
+
+template <typename Lane>
+__device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32_t purpose,
+                                                    Lane mask, const RoundKeys& rk) {
+  const U32x4 q0 = ep.block_at(kPair02, purpose, 0, rk);
+  const U32x4 q1 = ep.block_at(kPair12, purpose, 0, rk);
+  const U32x4 q2 = sizeof(Lane) == 4 ? q0 : ep.block_at(kPair02, purpose, 1, rk);
+  return triple_from_blocks<Lane>(q0, q1, q2, mask);
 }
 
 // The 32 window bits starting at bit sh of a lane.  SHORT: sh < 32 is known
@@ -103,6 +111,43 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
   return a >> sh;
 }
 
+// Steps 3-9 of one message slot whose window index is i: P0's and P1's
+// windows (Alg. newtrc2), pair sums, Alg. modswitch, the mask r_k and the
+// reshare z_k from the slot's seed01 block (mb = M1 * slot), and P2's zero
+// test.  Returns 1 when w0 + w1 = 0 mod p; w0, w1 are the two messages.
+template <int LX, bool SHORT, typename Lane>
+__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, const RoundKeys& rk,
+                                                   Lane f0, Lane nf1, uint32_t i,
+                                                   const StreamPhilox& mask_stream, uint64_t mb,
+                                                   uint32_t& w0, uint32_t& w1) {
+  constexpr bool kWide = (LX == 0) || (LX > 30);
+  using M = SlotMath<LX, kWide>;
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  const uint32_t p = k.mp.p;
+  const uint32_t sh = k.c + i;
+  const uint32_t y0 = window32<SHORT>(f0, sh);
+  const uint32_t y1 = window32<SHORT>(nf1, sh);
+  const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
+  // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
+  const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
+  const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
+  // step 5: Alg. modswitch
+  const uint32_t m0 = v0 ? v0 : k.two_lx;
+  const uint32_t m1 = v1 + k.p_minus_2lx;
+  // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
+  // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
+  const U32x4 rz = mask_stream.block(mb, rk);
+  const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+  const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
+  w0 = mont_mul<kWide>(m0, rho, k.mp);
+  w1 = mont_mul<kWide>(m1, rho, k.mp);
+  // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
+  w0 = M::add(w0, z, p);
+  w1 = M::sub(w1, z, p);
+  // step 9: P2 reconstructs w_k and tests it
+  return (M::add(w0, w1, p) == 0u) ? 1u : 0u;
+}
+
 // Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
 // column of the shared-memory shuffle table (stride kBlock words).
 // DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
@@ -115,12 +160,9 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
                                                  uint64_t elem, uint32_t* perm, Lane& out0,
                                                  Lane& out1, const AuditPtrs& aud,
                                                  uint64_t out_idx) {
-  constexpr bool kWide = (LX == 0) || (LX > 30);
-  using M = SlotMath<LX, kWide>;
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
   const uint32_t L = lx + 1;
   const Lane mask = (Lane)k.ring_mask;
-  const uint32_t p = k.mp.p;
   const ElemPhilox ep(elem, tensor_id);
 
   // ---- seed01 stream: t (step 1) and the shuffle words (step 6) ----------
@@ -163,33 +205,13 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
   uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
 #pragma unroll UNROLL
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
-    const uint32_t i = perm[slot * kBlock];
-    const uint32_t sh = k.c + i;
-    const uint32_t y0 = window32<SHORT>(f0, sh);
-    const uint32_t y1 = window32<SHORT>(nf1, sh);
-    const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
-    // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
-    const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
-    const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
-    // step 5: Alg. modswitch
-    const uint32_t m0 = v0 ? v0 : k.two_lx;
-    const uint32_t m1 = v1 + k.p_minus_2lx;
-    // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
-    // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
-    const U32x4 rz = mask_stream.block(mb, rk);
-    const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
-    const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
-    uint32_t w0 = mont_mul<kWide>(m0, rho, k.mp);
-    uint32_t w1 = mont_mul<kWide>(m1, rho, k.mp);
-    // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
-    w0 = M::add(w0, z, p);
-    w1 = M::sub(w1, z, p);
+    uint32_t w0, w1;
+    any_zero |= slot_zero_test<LX, SHORT>(k, rk, f0, nf1, perm[slot * kBlock], mask_stream, mb,
+                                          w0, w1);
     if (AUDIT) {
       if (aud.w0) aud.w0[out_idx * L + slot] = w0;
       if (aud.w1) aud.w1[out_idx * L + slot] = w1;
     }
-    // step 9: P2 reconstructs w_k and tests it
-    any_zero |= (M::add(w0, w1, p) == 0u) ? 1u : 0u;
   }
   const uint32_t dprime = any_zero;
   if (DPONLY) {

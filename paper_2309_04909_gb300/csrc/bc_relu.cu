@@ -30,12 +30,143 @@ __global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
   o1[i] = r1;
 }
 
+// Small batches: four lanes per element.  A launch of fewer elements than one
+// wave of the one-element-per-thread kernel takes the time of one thread's
+// whole key-bit loop (about 27 us at lx = 24), so here the four lanes of an
+// element share its work: each expands part of the shuffle stream, lane 0
+// applies the shuffle, each lane takes every fourth message slot, the lanes
+// OR their zero tests, and the finish's Philox blocks are drawn by different
+// lanes.  Same arithmetic and draws as bicoptor_element, so the outputs are
+// bit-identical.
+constexpr int kSplit = 4;
+constexpr int kSplitElems = kBlock / kSplit;   // elements per CTA
+
+template <typename Lane, int LX, bool SHORT, bool RELU>
+__global__ void __launch_bounds__(kBlock)
+    relu_split_kernel(const ReluConsts k, const Lane* __restrict__ sh0,
+                      const Lane* __restrict__ sh1, uint64_t n, Lane* __restrict__ o0,
+                      Lane* __restrict__ o1) {
+  constexpr uint32_t kSlotsMax = LX ? LX + 1 : kMaxSlots;
+  constexpr uint32_t kWordsMax = (kSlotsMax + 3) / 4 * 4;
+  __shared__ uint32_t perm_s[kSlotsMax * kSplitElems];
+  __shared__ uint32_t words_s[kWordsMax * kSplitElems];
+  const uint32_t el = threadIdx.x / kSplit, part = threadIdx.x % kSplit;
+  const uint32_t base = (threadIdx.x & 31u) & ~(uint32_t)(kSplit - 1);   // lane of part 0
+  const uint64_t i0 = (uint64_t)blockIdx.x * kSplitElems + el;
+  const bool valid = i0 < n;
+  const uint64_t i = valid ? i0 : n - 1;   // lanes past the end shadow the last element
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  const uint32_t L = lx + 1;
+  const Lane mask = (Lane)k.ring_mask;
+  const RoundKeys& rk = k.rk;
+  const ElemPhilox ep(k.elem_base + i, k.tensor_id);
+  uint32_t* perm = perm_s + el;
+  uint32_t* words = words_s + el;
+
+  // seed01 shuffle stream (steps 1 and 6): block b drawn by lane b mod 4
+  const uint32_t nblk = (L + 3) >> 2;
+  const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
+  for (uint32_t b = part; b < nblk; b += kSplit) {
+    const U32x4 wb = perm_stream.block((uint64_t)kPhiloxM1 * b, rk);
+    words[(4 * b + 0) * kSplitElems] = wb.x;
+    words[(4 * b + 1) * kSplitElems] = wb.y;
+    words[(4 * b + 2) * kSplitElems] = wb.z;
+    words[(4 * b + 3) * kSplitElems] = wb.w;
+  }
+  __syncwarp();
+  uint32_t t = 0;
+  if (part == 0) {
+    for (uint32_t sl = 0; sl < L; ++sl) perm[sl * kSplitElems] = sl;
+    t = words[0] & 1u;
+    for (uint32_t widx = 1; widx < L; ++widx) {   // Fisher-Yates step j = lx + 1 - widx
+      const uint32_t j = L - widx;
+      const uint32_t partner = __umulhi(words[widx * kSplitElems], j + 1);
+      const uint32_t a = perm[j * kSplitElems];
+      const uint32_t c = perm[partner * kSplitElems];
+      perm[j * kSplitElems] = c;
+      perm[partner * kSplitElems] = a;
+    }
+  }
+  __syncwarp();
+  t = __shfl_sync(0xffffffffu, t, base);
+
+  // steps 1-2, then steps 3-9 over this lane's message slots
+  const Lane s0 = sh0[i], s1 = sh1[i];
+  const Lane f0 = t ? ring_neg(s0, mask) : s0;
+  const Lane nf1 = t ? s1 : ring_neg(s1, mask);
+  uint32_t any_zero = 0;
+  const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
+  for (uint32_t slot = part; slot < L; slot += kSplit) {
+    uint32_t w0, w1;
+    any_zero |= slot_zero_test<LX, SHORT>(k, rk, f0, nf1, perm[slot * kSplitElems], mask_stream,
+                                          (uint64_t)kPhiloxM1 * slot, w0, w1);
+  }
+  any_zero |= __shfl_xor_sync(0xffffffffu, any_zero, 1);
+  any_zero |= __shfl_xor_sync(0xffffffffu, any_zero, 2);
+  const uint32_t dprime = any_zero;
+
+  Lane out0, out1;
+  if (!RELU) {
+    // steps 10-11 (lane 0 finishes)
+    const U32x4 rb = ep.block_at(kPair02, kPurReply, 0, rk);
+    const Lane d0 = block_elem<Lane>(rb, 0) & mask;
+    const Lane d1 = ((Lane)dprime - d0) & mask;
+    out0 = t ? (Lane)((Lane)1 - d0) & mask : d0;
+    out1 = t ? ring_neg(d1, mask) : d1;
+  } else {
+    // Alg. relu: the triple's blocks are drawn by lanes 0, 1 (and 2 for l > 32)
+    const U32x4 mine = part == 0 ? ep.block_at(kPair02, kPurReluTriple, 0, rk)
+                       : part == 1 ? ep.block_at(kPair12, kPurReluTriple, 0, rk)
+                                   : ep.block_at(kPair02, kPurReluTriple, 1, rk);
+    U32x4 q1, q2;
+    q1.x = __shfl_sync(0xffffffffu, mine.x, base + 1);
+    q1.y = __shfl_sync(0xffffffffu, mine.y, base + 1);
+    q1.z = __shfl_sync(0xffffffffu, mine.z, base + 1);
+    q1.w = __shfl_sync(0xffffffffu, mine.w, base + 1);
+    q2.x = __shfl_sync(0xffffffffu, mine.x, base + 2);
+    q2.y = __shfl_sync(0xffffffffu, mine.y, base + 2);
+    q2.z = q2.w = 0u;
+    const Triple<Lane> T = triple_from_blocks<Lane>(mine, q1, q2, mask);
+    const Lane c1 = (Lane)((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0) & mask;
+    const Lane e = (Lane)((Lane)dprime - T.b0 - T.b1) & mask;
+    const Lane d = (Lane)((s0 - T.a0) + (s1 - T.a1)) & mask;
+    const Lane xd0 = (Lane)(d * (e + T.b0) + e * T.a0 + T.c0) & mask;
+    const Lane xd1 = (Lane)(d * T.b1 + e * T.a1 + c1) & mask;
+    out0 = t ? (Lane)(s0 - xd0) & mask : xd0;
+    out1 = t ? (Lane)(s1 - xd1) & mask : xd1;
+  }
+  if (part == 0 && valid) {
+    o0[i] = out0;
+    o1[i] = out1;
+  }
+}
+
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
 cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n, void* o0,
                      void* o1, const AuditPtrs& aud, cudaStream_t s) {
   const uint64_t grid = (n + kBlock - 1) / kBlock;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  if (!AUDIT) {
+    // up to about two waves of the split kernel beat one wave of the
+    // element-per-thread kernel, whose time is one element's whole loop
+    static int split_per_sm = 0, num_sms = 0;
+    if (split_per_sm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &split_per_sm, relu_split_kernel<Lane, LX, SHORT, RELU>, kBlock, 0);
+      if (split_per_sm < 1) split_per_sm = 1;
+    }
+    const uint64_t split_grid = (n + kSplitElems - 1) / kSplitElems;
+    if (split_grid <= 2ull * (uint64_t)num_sms * (uint64_t)split_per_sm) {
+      relu_split_kernel<Lane, LX, SHORT, RELU><<<(unsigned)split_grid, kBlock, 0, s>>>(
+          k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1), n,
+          static_cast<Lane*>(o0), static_cast<Lane*>(o1));
+      return cudaGetLastError();
+    }
+  }
   relu_kernel<Lane, LX, SHORT, RELU, AUDIT><<<(unsigned)grid, kBlock, 0, s>>>(
       k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1), n, static_cast<Lane*>(o0),
       static_cast<Lane*>(o1), aud);

@@ -201,6 +201,25 @@ def test_largest_prime_rss(ctx):
         assert np.array_equal(to_np(g).astype(np.uint64), w)
 
 
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+@pytest.mark.parametrize("ring,lx,c,mag,n", [(64, 24, 0, 23, 1), (64, 24, 0, 23, 63),
+                                            (64, 24, 0, 23, 1000), (64, 7, 0, 6, 5001),
+                                            (32, 14, 4, 17, 777), (16, 5, 2, 6, 300),
+                                            (64, 20, 3, 22, 4097), (32, 9, 14, 22, 70_001)])
+def test_small_batch_parity(ctx, op, ring, lx, c, mag, n):
+    """Small launches (the four-lanes-per-element kernel, partial warps and
+    CTAs included) are bit-identical to the oracle."""
+    x = W.magnitude_bounded_ints(n, mag, seed=n + lx)
+    s0, s1 = _shares(ctx, ring, x, 40)
+    fn = ctx.drelu if op == "drelu" else ctx.relu
+    o0, o1 = fn(Params(ring, lx, c), s0, s1, tensor_id=41)
+    es0, es1 = O.share(ring, masked(x, ring), SEED, 40)
+    ofn = O.drelu if op == "drelu" else O.relu
+    e0, e1 = ofn(O.params(ring, lx, c), es0, es1, SEED, 41, threads=8)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
 def test_protocol_empty_and_single(ctx):
     prm = Params(64, 24, 0)
     z = torch.empty(0, dtype=torch.int64, device="cuda")
