@@ -148,8 +148,11 @@ cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
   if (!AUDIT) {
-    // up to about two waves of the split kernel beat one wave of the
-    // element-per-thread kernel, whose time is one element's whole loop
+    // the split kernel's time grows with n from a few microseconds; the
+    // element-per-thread kernel's is one element's latency up to a full
+    // wave: about 7.5 us below one CTA per SM at lx = 24, rising to 12 and
+    // 17.5 us as CTAs share the SMs.  On GB300 they cross near 0.3 waves of
+    // the split kernel (about 1.2e4 elements at lx = 24).
     static int split_per_sm = 0, num_sms = 0;
     if (split_per_sm == 0) {
       int dev = 0;
@@ -160,7 +163,7 @@ cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint
       if (split_per_sm < 1) split_per_sm = 1;
     }
     const uint64_t split_grid = (n + kSplitElems - 1) / kSplitElems;
-    if (split_grid <= 2ull * (uint64_t)num_sms * (uint64_t)split_per_sm) {
+    if (10 * split_grid <= 3ull * (uint64_t)num_sms * (uint64_t)split_per_sm) {   // 0.3 waves
       relu_split_kernel<Lane, LX, SHORT, RELU><<<(unsigned)split_grid, kBlock, 0, s>>>(
           k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1), n,
           static_cast<Lane*>(o0), static_cast<Lane*>(o1));
