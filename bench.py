@@ -32,8 +32,8 @@ N_DEFAULT = 1 << 22
 RING, FRAC, K_TRUNC, LX, KEY_OFF = 64, 16, 16, 24, 0
 SEED = 1
 # DRAM bytes per element of the fused step kernel: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2^21-element launch (91.12 MB) / its elements
-TRAFFIC_PER_ELEM = 43.45
+# dram__bytes_write.sum of one 2^21-element launch (90.20 MB) / its elements
+TRAFFIC_PER_ELEM = 43.01
 
 
 def parse():
@@ -47,7 +47,8 @@ def parse():
                     help="fused: one kernel per step (default); chain: the same step as four "
                          "launches (product, two truncations, ReLU) through HBM, each timed")
     ap.add_argument("--no-extras", action="store_true",
-                    help="time the step alone: skip e2e and the batched/serving/cpu extras")
+                    help="time the step alone (for profiling): skip e2e, the multiplier "
+                         "microbenchmark and the batched/serving/cpu extras")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window of each serving run (60 s in the full trace)")
@@ -321,7 +322,7 @@ def main():
         "gpu_launches": args.steps,
         "clocks": ck,
     }
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         # the multiplier's rates measured by our own microbenchmark (after the
         # timed region): the time the step's algorithmic products need at
         # those rates, against the kernel's time
