@@ -43,6 +43,14 @@ MUTANTS = {
                                 "X[j] = rmod(S[j] + T[j], ell);"),
     "rss_zero_sharing_sign": ("out[i] = rmod(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] - g[j], ell);",
                               "out[i] = rmod(a[i] * b[i] + a[i] * b[j] + a[j] * b[i] + g[i] + g[j], ell);"),
+    "mask_skipped_for_p1": ("sh1[k] = (uint32_t)(((uint64_t)sh1[k] * r[k]) % p);",
+                            "sh1[k] = sh1[k];"),
+    "mask_rho_can_be_zero": ("uint32_t rho = 1u + (uint32_t)(((u128)wr * (u128)(P->p - 1u)) >> 64);",
+                             "uint32_t rho = (uint32_t)(((u128)wr * (u128)(P->p - 1u)) >> 64);"),
+    "shuffle_p0_only": ("sh0[k] = m0[perm[k]]; sh1[k] = m1[perm[k]];",
+                        "sh0[k] = m0[perm[k]]; sh1[k] = m1[k];"),
+    "trunc_then_mul_y_by_kx": ("uint64_t ty0 = smltrc_p0(y0[i], ell, ky), ty1 = smltrc_p1(y1[i], ell, ky);",
+                               "uint64_t ty0 = smltrc_p0(y0[i], ell, kx), ty1 = smltrc_p1(y1[i], ell, kx);"),
     "aby3_signed_division": ("if (ell < 128 && (v >> (ell - 1)) & 1) v -= ((__int128)1 << ell);",
                              "if (0) v -= ((__int128)1 << ell);"),
 }

@@ -513,13 +513,14 @@ def test_aby3_fixed_r_hides_e1_and_random_r_does_not():
             assert fails > 1000
 
 
-def test_truncate_then_multiply_exact_composition():
+@pytest.mark.parametrize("f", [26, 25])
+def test_truncate_then_multiply_exact_composition(f):
     """Alg. linear: shares reconstruct to trc(x, kx) * trc(y, ky) where each
     truncation is Alg. smltrc's (the Beaver product is exact), and the result
     stays within (|x| + |y|) / 2^(f/2) + 1 of x y / 2^f for in-range inputs,
-    where multiply-then-truncate at l = 64 with f = 26 fails often."""
+    where multiply-then-truncate at l = 64 with f = 26 fails often.  An odd f
+    splits the truncation unevenly (Sec. 4.2), so kx and ky differ."""
     from paper_2309_04909_gb300 import workloads as W
-    f = 26
     X = W.gaussian_reals(20000, 4.0, seed=5, stream=0)
     Y = W.gaussian_reals(20000, 4.0, seed=5, stream=1)
     xi = np.rint(np.ldexp(X, f)).astype(np.int64)
