@@ -50,15 +50,23 @@ class Params:
     p: int = 0
 
     def c_struct(self) -> DreluParams:
-        return DreluParams(self.ring_bits, self.lx, self.key_off, self.p)
+        # one ctypes struct per distinct parameter set (the library only reads it)
+        c = _PRM_STRUCTS.get(self)
+        if c is None:
+            c = _PRM_STRUCTS[self] = DreluParams(self.ring_bits, self.lx, self.key_off, self.p)
+        return c
 
     @property
     def slots(self) -> int:
         return self.lx + 1
 
 
+_PRM_STRUCTS: Dict["Params", DreluParams] = {}
+
+
 def _ptr(t: Optional[torch.Tensor]):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    # a plain int: ctypes converts it for c_void_p arguments and fields
+    return None if t is None else t.data_ptr()
 
 
 class Context:
@@ -69,6 +77,7 @@ class Context:
         self._lib = _native.lib()
         self.device = torch.device("cuda", device)
         self._stream = stream
+        self._last_stream = None
         h = ctypes.c_void_p()
         self._check(self._lib.bc_create(ctypes.byref(h), seed, device, self._stream_handle()))
         self._h = h
@@ -80,8 +89,13 @@ class Context:
         return ctypes.c_void_p(s.cuda_stream)
 
     def _sync_stream(self):
-        # calls follow torch's current stream unless a stream was pinned
-        self._lib.bc_set_stream(self._h, self._stream_handle())
+        # calls follow torch's current stream unless a stream was pinned; the
+        # library is told only when the stream changes
+        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        h = s.cuda_stream
+        if h != self._last_stream:
+            self._lib.bc_set_stream(self._h, h)
+            self._last_stream = h
 
     def _check(self, rc: int):
         if rc != 0:
@@ -107,7 +121,8 @@ class Context:
 
     @staticmethod
     def _need(t: torch.Tensor, bits: int, name: str):
-        if t.dtype != lane_dtype(bits) or not t.is_cuda or not t.is_contiguous():
+        if (t.dtype is not (torch.int64 if bits > 32 else torch.int32) or not t.is_cuda
+                or not t.is_contiguous()):
             raise BicoptorError(f"{name}: expected a contiguous CUDA {lane_dtype(bits)} tensor")
 
     # -- sharing ----------------------------------------------------------------

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <initializer_list>
@@ -242,8 +243,15 @@ const char* bc_last_cuda_error(bc_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
 uint32_t bc_prime_above(int lx) {
   if (lx < 1 || lx > 31) return 0;
+  // trial division takes microseconds at lx = 24 and every call with p = 0
+  // asks, so each lx is searched once (a racing second search stores the
+  // same value)
+  static std::atomic<uint32_t> found[32];
+  const uint32_t known = found[lx].load(std::memory_order_relaxed);
+  if (known) return known;
   uint64_t q = ((uint64_t)1 << lx) + 1;
   while (!is_prime32(q)) ++q;
+  found[lx].store((uint32_t)q, std::memory_order_relaxed);
   return (uint32_t)q;
 }
 
