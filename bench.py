@@ -347,35 +347,58 @@ def main():
     # the long extras run in the single-GPU run only (N > 1 runs measure the
     # scaled step; every rank's GPU would otherwise be held for minutes)
     if rank == 0 and world == 1 and not args.no_extras:
-        # every intermediate of the step, for the extras that read them
-        ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
-        line["unfused_chain"] = chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms)
-        line["e2e"]["paths"] = e2e_paths(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf)
-        line["trunc_failures"] = trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev)
-        line["linear_layer_truncation"] = linear_trunc_table(ctx, dev)
-        rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
-        rate1, m1, dt1 = cpu_rate(max(2.0, args.cpu_seconds / 5), xi, yi, 1)
-        line["cpu_baseline"] = {"value": rate, "unit": "elems/s", "cores": _threads(),
-                                "kind": "oracle",
-                                "sample": f"first {m2} elements of the workload, full step "
-                                          f"(share, product, both truncations, ReLU), {dt:.1f} s",
-                                "single_thread": {"value": rate1, "sample_elems": m1,
-                                                  "seconds": dt1}}
-        line["cpu_baseline_batched_configs"] = cpu_configs(_threads())
-        line["party_separated"] = parties_bench(ctx, prm, buf, n,
-                                                line["unfused_chain"]["relu_ms"])
-        line["rss_relu"] = rss_bench(ctx, prm, buf, n)
-        line["drelu_l32_uniform"] = uniform_l32_drelu_check(ctx, dev)
-        line["size_sweep_l64"] = size_sweep(ctx, dev)
-        line["batched_vs_plain"] = bvp = vgg16_batched_vs_plain(ctx, dev)
-        line["resnet18_mixed_batched"] = resnet18_batched(ctx, dev)
-        line["serving"] = serving_bench(ctx, dev, bvp["batched_elems_per_s"],
-                                        args.serve_seconds, bvp)
+        run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, dev):
+    """The single-GPU extras, each recorded under its key.  An extra that
+    fails records its error instead, so the headline line is always printed."""
+    import torch
+
+    def extra(key, fn, into=None):
+        try:
+            (into if into is not None else line)[key] = fn()
+        except Exception as exc:   # noqa: BLE001 - recorded, the headline stands
+            (into if into is not None else line)[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            try:
+                torch.cuda.synchronize()
+            except Exception:      # noqa: BLE001 - a sticky CUDA error is already recorded
+                pass
+
+    def cpu_baseline():
+        rate, m2, dt = cpu_rate(args.cpu_seconds, xi, yi, _threads())
+        rate1, m1, dt1 = cpu_rate(max(2.0, args.cpu_seconds / 5), xi, yi, 1)
+        return {"value": rate, "unit": "elems/s", "cores": _threads(), "kind": "oracle",
+                "sample": f"first {m2} elements of the workload, full step "
+                          f"(share, product, both truncations, ReLU), {dt:.1f} s",
+                "single_thread": {"value": rate1, "sample_elems": m1, "seconds": dt1}}
+
+    # every intermediate of the step, for the extras that read them
+    ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
+    extra("unfused_chain", lambda: chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms))
+    if "e2e" in line:
+        extra("paths", lambda: e2e_paths(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf),
+              into=line["e2e"])
+    extra("trunc_failures", lambda: trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev))
+    extra("linear_layer_truncation", lambda: linear_trunc_table(ctx, dev))
+    extra("cpu_baseline", cpu_baseline)
+    extra("cpu_baseline_batched_configs", lambda: cpu_configs(_threads()))
+    relu_ms = line["unfused_chain"].get("relu_ms", kern_ms)
+    extra("party_separated", lambda: parties_bench(ctx, prm, buf, n, relu_ms))
+    extra("rss_relu", lambda: rss_bench(ctx, prm, buf, n))
+    extra("drelu_l32_uniform", lambda: uniform_l32_drelu_check(ctx, dev))
+    extra("size_sweep_l64", lambda: size_sweep(ctx, dev))
+    extra("batched_vs_plain", lambda: vgg16_batched_vs_plain(ctx, dev))
+    extra("resnet18_mixed_batched", lambda: resnet18_batched(ctx, dev))
+    bvp = line["batched_vs_plain"]
+    if "batched_elems_per_s" in bvp:
+        extra("serving", lambda: serving_bench(ctx, dev, bvp["batched_elems_per_s"],
+                                               args.serve_seconds, bvp))
 
 
 def _threads():
