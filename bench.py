@@ -43,9 +43,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--step", default="fused", choices=["fused", "chain"],
+    ap.add_argument("--step", default="fused", choices=["fused", "chain", "parties", "rss"],
                     help="fused: one kernel per step (default); chain: the same step as four "
-                         "launches (product, two truncations, ReLU) through HBM, each timed")
+                         "launches (product, two truncations, ReLU) through HBM, each timed; "
+                         "parties / rss: the ReLU of the step's truncated product by the "
+                         "party-separated launches / the RSS protocol (for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the step alone (for profiling): skip e2e, the multiplier "
                          "microbenchmark and the batched/serving/cpu extras")
@@ -267,6 +269,10 @@ def main():
         chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev)
         ctx.close()
         return
+    if args.step in ("parties", "rss"):
+        variant_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev)
+        ctx.close()
+        return
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -468,6 +474,44 @@ def chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev):
                          "traffic": None, "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",
                          "mul_ops_per_element": muls, "kernel_ms": r["relu_ms"]},
             "gpu_launches": 4 * args.steps, "chain": r}
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
+
+
+def variant_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev):
+    """`--step parties` / `--step rss`: the ReLU of the step's truncated
+    product by the party-separated launches (messages in device buffers) or
+    by the RSS protocol, timed as the step (for profiling those paths)."""
+    import torch
+    from paper_2309_04909_gb300.replicas import max_over_ranks
+    ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
+    if args.step == "parties":
+        msgs = ctx.party_buffers(prm, n)
+        out = (torch.empty_like(buf["relu0"]), torch.empty_like(buf["relu1"]))
+        run = lambda: ctx.relu_parties(prm, buf["trc0"], buf["trc1"], 4, out=out, msgs=msgs)
+        launches = 3
+    else:
+        z = torch.zeros_like(buf["trc0"])
+        ys = tuple(torch.empty_like(buf["trc0"]) for _ in range(3))
+        run = lambda: ctx.rss_relu(prm, buf["trc0"], z, buf["trc1"], 4, out=ys)
+        launches = 1
+    for _ in range(max(3, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+    line = {"metric": METRIC, "value": n * world / (ms / 1e3), "unit": "elems/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"ReLU of the step's truncated product, {args.step} path",
+                       "n": n},
+            "gpu_launches": launches * args.steps}
     if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(line), flush=True)
 
