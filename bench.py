@@ -387,6 +387,7 @@ def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, de
     # every intermediate of the step, for the extras that read them
     ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
     extra("unfused_chain", lambda: chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms))
+    extra("hbm_kernels_isolated", lambda: hbm_isolated(ctx, dev))
     if "e2e" in line:
         extra("paths", lambda: e2e_paths(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf),
               into=line["e2e"])
@@ -450,6 +451,54 @@ def chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, fused_ms, steps=20, warmup=3):
             "relu_ms": ms[3], "equal_to_fused": same if fused_ms else None,
             "hbm_kernels": {"mul_beaver": hbm(ms[0], 48), "trunc_prob": hbm(ms[1], 32),
                             "trunc_det": hbm(ms[2], 32)}}
+
+
+def hbm_isolated(ctx, dev, log2n=25, iters=20, warmup=3):
+    """Each HBM-bound kernel of the C-ABI alone, at 2^25 elements: every l = 64
+    array is 256 MiB, twice the 129 MB L2, so every launch reads its inputs
+    from HBM.  Each kernel is timed with CUDA events around `iters`
+    back-to-back launches on the context's stream."""
+    import torch
+    from paper_2309_04909_gb300 import prime_above
+    hbm_peak = 6793.4   # GB/s, measured STREAM-style copy on this pool's GB300s
+    n = 1 << log2n
+    g = torch.Generator(device=dev).manual_seed(0x4B4D)
+    lo, hi = -(1 << 63), (1 << 63) - 1
+
+    def u64():
+        return torch.randint(lo, hi, (n,), dtype=torch.int64, device=dev, generator=g)
+
+    x0, x1, y0, y1 = u64(), u64(), u64(), u64()
+    xf = torch.randint(-(1 << 40), 1 << 40, (n,), dtype=torch.int64, device=dev, generator=g)
+    m0 = torch.randint(0, 1 << 24, (n,), dtype=torch.int32, device=dev, generator=g)
+    m1 = torch.randint(0, 1 << 24, (n,), dtype=torch.int32, device=dev, generator=g)
+    o0, o1 = torch.empty_like(x0), torch.empty_like(x0)
+    p24 = prime_above(24)
+    kernels = {
+        # name: (call, algorithmic bytes per element)
+        "share": (lambda: ctx.share(RING, xf, 7), 24),
+        "reconstruct": (lambda: ctx.reconstruct(RING, x0, x1), 24),
+        "trunc_prob": (lambda: ctx.trunc_prob(RING, K_TRUNC, x0, x1, out=(o0, o1)), 32),
+        "trunc_det": (lambda: ctx.trunc_det(RING, K_TRUNC, 0, x0, x1, out=(o0, o1)), 32),
+        "mod_switch_lx24": (lambda: ctx.mod_switch(24, p24, m0, m1), 16),
+        "mul_beaver": (lambda: ctx.mul_beaver(RING, x0, x1, y0, y1, 8, out=(o0, o1)), 48),
+    }
+    out = {"n": n, "iters": iters, "hbm_peak_GB/s": hbm_peak, "l2": "inputs > L2 (no flush)"}
+    for name, (call, bpe) in kernels.items():
+        for _ in range(warmup):
+            call()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(iters):
+            call()
+        e.record()
+        torch.cuda.synchronize()
+        us = s.elapsed_time(e) * 1e3 / iters
+        gbs = bpe * n / (us / 1e6) / 1e9
+        out[name] = {"us": us, "bytes_per_element": bpe, "GB/s": gbs,
+                     "frac_of_measured_hbm": gbs / hbm_peak}
+    return out
 
 
 def chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev):

@@ -43,7 +43,7 @@ extern "C" {
 #define BC_EINVAL (-1)   /* bad argument: sizes, parameters, NULL pointers      */
 #define BC_ENOMEM (-2)   /* device workspace could not be reserved               */
 #define BC_ECUDA (-3)    /* a CUDA call failed (see bc_last_cuda_error)          */
-#define BC_ETIMEOUT (-4) /* a bounded device wait gave up (persistent batch)     */
+#define BC_ETIMEOUT (-4) /* a bounded device wait gave up (bc_parties_status)   */
 #define BC_ECHECK (-5)   /* a device-side consistency check failed               */
 #define BC_ELIMIT (-6)   /* request exceeds a fixed capacity (bc_relu_batch_static) */
 
@@ -201,10 +201,11 @@ int bc_rss_relu(bc_ctx *ctx, const bc_drelu_params *prm, const void *x0, const v
  * the caller).  Every message of Alg. drelu / Alg. relu lives here between
  * the sender's kernel and the receiver's:
  *   w0, w1      P0 -> P2 and P1 -> P2 (step 8), bc_party_msg_words(lx, n)
- *               uint32 words each: the lx+1 values of lx+1 bits per element,
- *               packed (groups of 32 elements; slot k of group g occupies the
- *               lx+1 words at (k * ceil(n/32) + g) * (lx+1), element 32g+l at
- *               bits [l (lx+1), (l+1)(lx+1)))
+ *               uint32 words each, 16-byte aligned: the lx+1 values of lx+1
+ *               bits per element, packed (groups of 32 elements; slot k of
+ *               group g occupies the lx+1 words at (g * (lx+1) + k) * (lx+1),
+ *               element 32g+l at bits [l (lx+1), (l+1)(lx+1)); the group
+ *               count is ceil(n/32) rounded up to a multiple of 8)
  *   reply       lanes [n]: [DReLU']_1 to P1 (DReLU) / e = DReLU' - b (ReLU)
  *   open0/1     lanes [n]: P0 -> P1 and P1 -> P0 shares of d = x - a (ReLU)
  *   pre_c1      lanes [n]: P2 -> P1 preprocessing [c]_1 (ReLU)              */
@@ -213,7 +214,8 @@ typedef struct {
   void *reply, *open0, *open1, *pre_c1;
 } bc_party_msgs;
 
-/* uint32 words of one packed w buffer for n elements (ceil(n/32)*32*(lx+1)^2 bits). */
+/* uint32 words of one packed w buffer for n elements: (lx+1)^2 bits per
+ * element, n rounded up to a multiple of 256. */
 size_t bc_party_msg_words(int lx, size_t n);
 
 /* Alg. drelu / Alg. relu with each party's local work in its own kernel and
@@ -225,6 +227,15 @@ int bc_drelu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, c
                      size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
 int bc_relu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
                     size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
+/* P2's kernel waits (at most 50 ms) for the bulk copies of its messages.
+ * BC_OK, or BC_ETIMEOUT if that wait gave up in a party-separated call since
+ * the last read (that call's outputs are then undefined).  Synchronises the
+ * context's stream and clears the status. */
+int bc_parties_status(bc_ctx *ctx);
+/* Test hook for that bounded wait: while on (nonzero), P2's kernel issues no
+ * copies, so its wait runs out after 1 ms and bc_parties_status reports
+ * BC_ETIMEOUT.  Off by default; for tests only. */
+int bc_test_drop_p2_copies(bc_ctx *ctx, int on);
 
 int bc_get_comm(bc_ctx *ctx, bc_comm *out);
 int bc_reset_comm(bc_ctx *ctx);
@@ -284,7 +295,7 @@ int bc_relu_batch_run(bc_ctx *ctx);
 /* plan + run. */
 int bc_relu_batch(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
                   const bc_batch_config *cfg);
-/* Status word of the last batched launch (BC_OK or BC_ETIMEOUT/BC_ECHECK);
+/* Status word of the last batched launch (BC_OK or BC_ECHECK);
  * synchronises the context's stream. */
 int bc_batch_status(bc_ctx *ctx);
 

@@ -301,6 +301,15 @@ class Context:
     def relu_parties(self, prm: Params, s0, s1, tensor_id: int, out=None, msgs=None):
         return self._parties(self._lib.bc_relu_parties, prm, s0, s1, tensor_id, out, msgs)
 
+    def parties_status(self) -> int:
+        """0, or BC_ETIMEOUT (-4) if P2's bounded wait for its messages gave up
+        in a party-separated call since the last read; synchronises, clears."""
+        return int(self._lib.bc_parties_status(self._h))
+
+    def test_drop_p2_copies(self, on: bool = True):
+        """Test hook: P2's kernel issues no message copies, so its wait runs out."""
+        self._check(self._lib.bc_test_drop_p2_copies(self._h, 1 if on else 0))
+
     # -- batched ------------------------------------------------------------------
     def relu_batch_plan(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0,
                         schedule: int = 0, elems_per_thread: int = 0, slot_unroll: int = 0):

@@ -169,6 +169,8 @@ SIGNATURES = {
                                         c_size, c_void_p]),
     "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),
     "bc_party_msg_words": (c_size, [c_int, c_size]),
+    "bc_parties_status": (c_int, [c_void_p]),
+    "bc_test_drop_p2_copies": (c_int, [c_void_p, c_int]),
     "bc_rss_drelu": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_void_p, c_size, c_u32,
                              c_void_p, c_void_p, c_void_p]),
     "bc_rss_relu": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_void_p, c_size, c_u32,

@@ -57,6 +57,9 @@ struct bc_ctx {
   // checked mode: canonical-form check of every input before a call
   bool checked = false;
   unsigned long long* d_check = nullptr;
+  // party-separated calls: P2's wait status (sticky until read); test hook
+  int* d_party_status = nullptr;
+  bool drop_p2_copies = false;
 };
 
 namespace {
@@ -271,6 +274,8 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_check, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_party_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_party_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&ctx->plan_ev[i], cudaEventDisableTiming);
@@ -303,6 +308,7 @@ int bc_destroy(bc_ctx* ctx) {
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_check);
+  cudaFree(ctx->d_party_status);
   for (int i = 0; i < 4; ++i) cudaFree(ctx->stage[i]);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   delete ctx;
@@ -497,6 +503,8 @@ static int run_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0,
   if (!ctx || !m) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !o0 || !o1 || !m->w0 || !m->w1 || !m->reply)) return BC_EINVAL;
   if (n && relu && (!m->open0 || !m->open1 || !m->pre_c1)) return BC_EINVAL;
+  // P2 fetches the packed messages with bulk copies: 16-byte aligned buffers
+  if (n && ((((uintptr_t)m->w0) | ((uintptr_t)m->w1)) & 15u)) return BC_EINVAL;
   bc::ReluConsts k;
   int rc = make_consts(ctx, prm, tensor_id, &k);
   if (rc) return rc;
@@ -504,7 +512,8 @@ static int run_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0,
   if ((rc = check_canonical(ctx, prm->ring_bits, {sh0, sh1}, n))) return rc;
   if (n)
     CK(bc::launch_parties(k, relu, sh0, sh1, n, o0, o1, m->w0, m->w1, m->open0, m->open1,
-                          m->reply, m->pre_c1, ctx->stream));
+                          m->reply, m->pre_c1, ctx->d_party_status, ctx->drop_p2_copies,
+                          ctx->stream));
   add_comm(&ctx->comm, relu_comm(prm->ring_bits, prm->lx, n, relu));
   return BC_OK;
 }
@@ -517,6 +526,21 @@ int bc_drelu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, c
 int bc_relu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
                     size_t n, uint32_t tensor_id, void* o0, void* o1, const bc_party_msgs* m) {
   return run_parties(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, m, true);
+}
+
+int bc_parties_status(bc_ctx* ctx) {
+  if (!ctx) return BC_EINVAL;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->d_party_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_party_status, 0, sizeof(int), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return st;
+}
+
+int bc_test_drop_p2_copies(bc_ctx* ctx, int on) {
+  if (!ctx) return BC_EINVAL;
+  ctx->drop_p2_copies = on != 0;
+  return BC_OK;
 }
 
 int bc_get_comm(bc_ctx* ctx, bc_comm* out) {

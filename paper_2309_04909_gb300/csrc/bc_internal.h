@@ -113,9 +113,12 @@ cudaError_t launch_rss(const ReluConsts& k, bool relu, const void* const* x, uin
 
 // Party-separated DReLU/ReLU (three launches, messages in device buffers).
 uint64_t party_msg_words(uint32_t lx, uint64_t n);
+// `status` is set to BC_ETIMEOUT if P2's kernel gives up waiting for its
+// messages; drop_copies (testing only) makes it issue no copies so that it does.
 cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                            uint64_t n, void* o0, void* o1, uint32_t* w0, uint32_t* w1,
-                           void* open0, void* open1, void* reply, void* pre_c1, cudaStream_t s);
+                           void* open0, void* open1, void* reply, void* pre_c1, int* status,
+                           bool drop_copies, cudaStream_t s);
 
 cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
                          uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,

@@ -14,18 +14,78 @@
 // Unlike the fused kernel, P0 and P1 each expand seed01 (t, the shuffle, the
 // masks) themselves, as separate servers would.
 //
-// Packed w layout: elements in groups of 32; for slot k and group g the lx+1
-// words at (k * G + g) * (lx+1) (G = ceil(n / 32)) hold the 32 values of the
-// group, element 32 g + l at bits [l (lx+1), (l+1)(lx+1)).  The buffer is
-// exactly L * G * 32 * (lx+1) bits: the protocol's (lx+1)^2 bits per element
-// and sender, padded only in the last group.
+// Packed w layout: elements in groups of 32; for group g and slot k the lx+1
+// words at (g * L + k) * (lx+1) (L = lx+1 slots) hold the 32 values of the
+// group, element 32 g + l at bits [l (lx+1), (l+1)(lx+1)).  A group's whole
+// message is thus contiguous, and so are the 8 groups of one 256-thread CTA.
+// The group count is padded to a multiple of 8, so the buffer holds the
+// protocol's (lx+1)^2 bits per element and sender, padded to a multiple of
+// 256 elements.  P2's kernel fetches its CTA's two messages with bulk
+// asynchronous copies (cp.async.bulk) into shared memory.
+#include <mutex>
+
 #include "bc_internal.h"
 
 namespace bc {
 namespace {
 
 constexpr int kPB = kBlock;             // threads per CTA
-constexpr int kWarps = kPB / 32;
+constexpr int kWarps = kPB / 32;        // groups of 32 elements per CTA
+constexpr uint32_t kBulkChunk = 16384;  // bytes per bulk copy instruction
+constexpr uint64_t kWaitNs = 50000000;  // P2's wait for its messages: 50 ms
+constexpr uint64_t kTestWaitNs = 1000000;
+
+// ---- bulk asynchronous copies and their mbarrier ----------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// make the initialised barrier visible to the async proxy that completes it
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) that completes its bytes on the mbarrier at `bar`
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier for at most limit_ns nanoseconds
+// (and at most 2^22 polls); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
 
 template <typename Lane>
 __device__ __forceinline__ Lane lane_at(const void* p, uint64_t i) {
@@ -103,7 +163,9 @@ struct PartyArgs {
   void* reply;              // P2 -> P1 / P2 -> P0, P1
   void* pre_c1;             // P2 -> P1 preprocessing (ReLU)
   uint64_t n;
-  uint64_t groups;          // ceil(n / 32)
+  int* status;              // set to BC_ETIMEOUT if P2 gives up waiting
+  uint32_t drop_copies;     // test hook: P2 issues no copies, so its wait runs out
+  uint64_t wait_ns;         // P2's wait limit
 };
 
 // ---- launch 1: P0 and P1, steps 1-8 (+ opening of x - a) --------------------
@@ -151,7 +213,7 @@ __global__ void __launch_bounds__(kPB)
     const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
     uint32_t w = mont_mul(m, rho, k.mp);
     w = party == 0 ? add_mod(w, z, k.mp.p) : sub_mod(w, z, k.mp.p);          // step 8
-    warp_pack(w, valid, B, lane, stage_s[warp], a.w[party] + (slot * a.groups + g) * B);
+    warp_pack(w, valid, B, lane, stage_s[warp], a.w[party] + (g * L + slot) * B);
   }
   if (RELU && valid) {
     // opening of d = x - a: P0 draws a0 from seed02, P1 draws a1 from seed12
@@ -162,44 +224,85 @@ __global__ void __launch_bounds__(kPB)
 }
 
 // ---- launch 2: P2 ---------------------------------------------------------------
+// One thread issues bulk copies of the CTA's two messages (8 groups x L slots x
+// B words from each of P0 and P1, contiguous in the group-major layout) into
+// shared memory; every thread draws its element's triple from seed02 / seed12
+// while they arrive, then waits on the mbarrier (bounded) and unpacks its lx+1
+// value pairs from shared memory.
 template <typename Lane, bool RELU>
 __global__ void __launch_bounds__(kPB)
     helper_kernel(const PartyArgs a) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
-  if (i >= a.n) return;
+  extern __shared__ __align__(128) uint32_t msg_s[];   // [2][kWarps * L * B]
+  __shared__ __align__(8) uint64_t bar_s;
   const ReluConsts& k = a.k;
   const uint32_t L = k.lx + 1, B = k.lx + 1;
+  const uint32_t group_words = L * B;
+  const uint32_t cta_words = kWarps * group_words;
+  const uint32_t bar = smem_addr(&bar_s);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = cta_words * 4u;            // 32 L B: a multiple of 16
+    mbar_arrive_expect_tx(bar, 2u * bytes);
+    if (!a.drop_copies) {
+      for (uint32_t party = 0; party < 2; ++party) {
+        const char* src = reinterpret_cast<const char*>(a.w[party] +
+                                                        (uint64_t)blockIdx.x * cta_words);
+        const uint32_t dst = smem_addr(msg_s + party * cta_words);
+        for (uint32_t off = 0; off < bytes; off += kBulkChunk)
+          bulk_copy_g2s(dst + off, src + off, min(kBulkChunk, bytes - off), bar);
+      }
+    }
+  }
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
+  const bool valid = i < a.n;
   const Lane mask = (Lane)k.ring_mask;
-  const uint64_t g = i >> 5;
+  const ElemPhilox ep(k.elem_base + (valid ? i : 0), k.tensor_id);
+  Lane d0 = 0, a0 = 0, b0 = 0, c0 = 0, a1 = 0, b1 = 0;
+  if (valid) {
+    if (!RELU) {
+      d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
+    } else {
+      // P2 knows seed02 and seed12: the whole triple
+      const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
+      const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
+      if (sizeof(Lane) == 4) {
+        a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
+      } else {
+        const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
+        a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1);
+        c0 = block_elem<Lane>(q2, 0);
+      }
+      a0 &= mask; b0 &= mask; c0 &= mask;
+      a1 = block_elem<Lane>(q1, 0) & mask;
+      b1 = block_elem<Lane>(q1, 1) & mask;
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0, a.wait_ns)) {
+    // give up: report, let any copy still in flight land before the CTA's
+    // shared memory is released (bounded too), and write nothing
+    atomicExch(a.status, BC_ETIMEOUT);
+    mbar_wait_bounded(bar, 0, a.wait_ns);
+    return;
+  }
+  if (!valid) return;
+  const uint32_t* m0 = msg_s + warp * group_words;
+  const uint32_t* m1 = msg_s + cta_words + warp * group_words;
   uint32_t any_zero = 0;
-  // the slots are independent (only the OR accumulates), so unrolling lets
-  // the loads of several slots be in flight at once
 #pragma unroll 5
   for (uint32_t slot = 0; slot < L; ++slot) {                // step 9
-    const uint64_t off = (slot * a.groups + g) * B;
-    const uint32_t w0 = unpack(a.w[0] + off, B, lane);
-    const uint32_t w1 = unpack(a.w[1] + off, B, lane);
+    const uint32_t w0 = unpack(m0 + slot * B, B, lane);
+    const uint32_t w1 = unpack(m1 + slot * B, B, lane);
     any_zero |= (add_mod(w0, w1, k.mp.p) == 0u) ? 1u : 0u;
   }
-  const ElemPhilox ep(k.elem_base + i, k.tensor_id);
   if (!RELU) {
-    const Lane d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
     lane_put<Lane>(a.reply, i, (Lane)((Lane)any_zero - d0) & mask);        // step 10 -> P1
     return;
   }
-  // P2 knows seed02 and seed12: the whole triple
-  const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
-  const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
-  Lane a0, b0, c0;
-  if (sizeof(Lane) == 4) {
-    a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
-  } else {
-    const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
-    a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
-  }
-  a0 &= mask; b0 &= mask; c0 &= mask;
-  const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
   lane_put<Lane>(a.pre_c1, i, (Lane)((a0 + a1) * (b0 + b1) - c0) & mask);  // [c]_1 -> P1
   lane_put<Lane>(a.reply, i, (Lane)((Lane)any_zero - b0 - b1) & mask);     // e -> P0, P1
 }
@@ -249,15 +352,28 @@ __global__ void __launch_bounds__(kPB)
   lane_put<Lane>(a.out[party], i, t ? (Lane)(s - xd) & mask : xd);
 }
 
+// dynamic shared memory of the P2 kernel: two messages of kWarps groups
+inline size_t helper_smem_bytes(uint32_t lx) {
+  return 2ull * kWarps * (lx + 1) * (lx + 1) * sizeof(uint32_t);
+}
+
 template <typename Lane, bool RELU>
 cudaError_t launch_parties_t(const PartyArgs& a, cudaStream_t s) {
   const uint64_t blocks = (a.n + kPB - 1) / kPB;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(helper_kernel<Lane, RELU>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)helper_smem_bytes(kMaxSlots - 1));
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   parties_local_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, 0, s>>>(a);
+  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, helper_smem_bytes(a.k.lx), s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   parties_finish_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
@@ -267,13 +383,14 @@ cudaError_t launch_parties_t(const PartyArgs& a, cudaStream_t s) {
 }  // namespace
 
 uint64_t party_msg_words(uint32_t lx, uint64_t n) {
-  const uint64_t groups = (n + 31) / 32;
+  const uint64_t groups = (n + kPB - 1) / kPB * kWarps;   // padded to whole CTAs
   return (uint64_t)(lx + 1) * groups * (lx + 1);
 }
 
 cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                            uint64_t n, void* o0, void* o1, uint32_t* w0, uint32_t* w1,
-                           void* open0, void* open1, void* reply, void* pre_c1, cudaStream_t s) {
+                           void* open0, void* open1, void* reply, void* pre_c1, int* status,
+                           bool drop_copies, cudaStream_t s) {
   PartyArgs a;
   a.k = k;
   a.sh[0] = sh0;
@@ -287,7 +404,9 @@ cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, cons
   a.reply = reply;
   a.pre_c1 = pre_c1;
   a.n = n;
-  a.groups = (n + 31) / 32;
+  a.status = status;
+  a.drop_copies = drop_copies ? 1u : 0u;
+  a.wait_ns = drop_copies ? kTestWaitNs : kWaitNs;
   if (k.ring_bits > 32)
     return relu ? launch_parties_t<uint64_t, true>(a, s) : launch_parties_t<uint64_t, false>(a, s);
   return relu ? launch_parties_t<uint32_t, true>(a, s) : launch_parties_t<uint32_t, false>(a, s);

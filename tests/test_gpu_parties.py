@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle as O
-from paper_2309_04909_gb300 import Context, Params, workloads as W
+from paper_2309_04909_gb300 import BicoptorError, Context, Params, workloads as W
 from tests._util import masked, to_np
 
 pytestmark = [pytest.mark.gpu,
@@ -15,10 +15,16 @@ pytestmark = [pytest.mark.gpu,
 SEED = 0x9A27_1E5
 
 
+def padded_groups(n: int) -> int:
+    """Groups of 32 elements in a packed buffer: whole CTAs of 8 groups."""
+    return -(-n // 256) * 8
+
+
 def unpack_w(words: np.ndarray, lx: int, n: int) -> np.ndarray:
-    """Inverse of the packed message layout: (n, lx+1) values."""
-    B, L, G = lx + 1, lx + 1, (n + 31) // 32
-    w = words.view(np.uint32).astype(np.uint64).reshape(L, G, B)
+    """Inverse of the packed message layout (group-major: group g, slot k at
+    words (g L + k) B): (n, lx+1) values."""
+    B, L, G = lx + 1, lx + 1, padded_groups(n)
+    w = words.view(np.uint32).astype(np.uint64).reshape(G, L, B).transpose(1, 0, 2)
     bits = np.zeros((L, G, 32 * B), dtype=np.uint8)
     for b in range(32):
         bits[:, :, b::32] = ((w >> np.uint64(b)) & np.uint64(1)).astype(np.uint8)
@@ -44,7 +50,8 @@ def test_parties_match_fused_and_oracle(op, ring, lx, c, mag, n):
     f0, f1 = fused(prm, s0, s1, tensor_id=6)
     p0, p1, msgs = parties(prm, s0, s1, tensor_id=6)
     assert torch.equal(f0, p0) and torch.equal(f1, p1)
-    assert msgs["w0"].numel() == (lx + 1) * ((n + 31) // 32) * (lx + 1)
+    assert msgs["w0"].numel() == (lx + 1) * padded_groups(n) * (lx + 1)
+    assert ctx.parties_status() == 0
     es0, es1 = O.share(ring, masked(x, ring), SEED, 5)
     ofn = O.drelu if op == "drelu" else O.relu
     e0, e1, aud = ofn(O.params(ring, lx, c), es0, es1, SEED, 6, audit=True, threads=8)
@@ -56,4 +63,43 @@ def test_parties_match_fused_and_oracle(op, ring, lx, c, mag, n):
     if op == "relu":
         for k in ("open0", "open1", "pre_c1"):
             assert np.array_equal(to_np(msgs[k]).astype(np.uint64), aud[k])
+    ctx.close()
+
+
+def test_p2_wait_runs_out_and_reports():
+    """P2's bounded wait for its bulk copies: with the test hook on, no copy
+    is issued, the wait gives up after its limit, the call reports
+    BC_ETIMEOUT through the status word, and the context stays usable."""
+    ctx = Context(SEED)
+    n = 700                      # three CTAs, the last one partial
+    x = W.magnitude_bounded_ints(n, 20, seed=3)
+    s0, s1 = ctx.share(64, torch.from_numpy(x).cuda(), 5)
+    prm = Params(64, 24, 0)
+    assert ctx.parties_status() == 0
+    ctx.test_drop_p2_copies(True)
+    ctx.relu_parties(prm, s0, s1, tensor_id=6)
+    assert ctx.parties_status() == -4          # BC_ETIMEOUT
+    assert ctx.parties_status() == 0           # reading clears it
+    ctx.test_drop_p2_copies(False)
+    p0, p1, _ = ctx.relu_parties(prm, s0, s1, tensor_id=6)
+    f0, f1 = ctx.relu(prm, s0, s1, tensor_id=6)
+    assert torch.equal(p0, f0) and torch.equal(p1, f1)
+    assert ctx.parties_status() == 0
+    ctx.close()
+
+
+def test_unaligned_message_buffer_rejected():
+    """The packed buffers are read by bulk copies: a buffer that is not
+    16-byte aligned is rejected before anything is launched."""
+    ctx = Context(SEED)
+    n = 300
+    x = W.magnitude_bounded_ints(n, 20, seed=4)
+    s0, s1 = ctx.share(64, torch.from_numpy(x).cuda(), 5)
+    prm = Params(64, 24, 0)
+    msgs = ctx.party_buffers(prm, n)
+    words = msgs["w0"].numel()
+    base = torch.empty(words + 4, dtype=torch.int32, device=s0.device)
+    msgs["w0"] = base[1:words + 1]             # 4 bytes past a 16-byte boundary
+    with pytest.raises(BicoptorError):
+        ctx.relu_parties(prm, s0, s1, tensor_id=6, msgs=msgs)
     ctx.close()
