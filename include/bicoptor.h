@@ -254,7 +254,9 @@ typedef struct {
   bc_drelu_params params;
   uint64_t elem_offset;    /* element index of sh0[0] within the tensor
                               `tensor_id` (a slice of a larger tensor gets
-                              the randomness of those elements); usually 0 */
+                              the randomness of those elements); usually 0.
+                              elem_offset + n <= 2^48 (the Philox counter
+                              holds 48 index bits), else BC_EINVAL */
 } bc_tensor_desc;
 
 /* Schedule of the batched launch (0 fields = library default).

@@ -582,6 +582,7 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
     const bc_tensor_desc& d = descs[t];
     if (d.op != BC_OP_RELU && d.op != BC_OP_DRELU) return BC_EINVAL;
     if (d.n && (!d.sh0 || !d.sh1 || !d.o0 || !d.o1)) return BC_EINVAL;
+    if (!bc::elem_range_ok(d.elem_offset, d.n)) return BC_EINVAL;
     bc::ReluConsts k;
     int rc = make_consts(ctx, &d.params, 0, &k);
     if (rc) return rc;

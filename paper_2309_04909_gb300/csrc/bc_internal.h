@@ -11,6 +11,13 @@ namespace bc {
 constexpr int kBlock = 256;     // threads per CTA of every kernel
 constexpr int kMaxSlots = 32;   // lx + 1 <= 32
 
+// The Philox counter carries 48 bits of the element index (word 0 and the low
+// 16 bits of word 3), so the elements of one tensor id are numbered below 2^48.
+constexpr uint64_t kMaxElemIndex = 1ull << 48;
+inline bool elem_range_ok(uint64_t first, uint64_t n) {
+  return first <= kMaxElemIndex && n <= kMaxElemIndex - first;
+}
+
 // Per-call constants of Alg. drelu / Alg. relu, passed by value.
 struct ReluConsts {
   RoundKeys rk;

@@ -85,6 +85,7 @@ extern "C" int bc_relu_batch_static(uint64_t seed, int device, void* cuda_stream
     const bc_tensor_desc& d = descs[t];
     if (d.op != BC_OP_RELU && d.op != BC_OP_DRELU) return BC_EINVAL;
     if (d.n && (!d.sh0 || !d.sh1 || !d.o0 || !d.o1)) return BC_EINVAL;
+    if (!bc::elem_range_ok(d.elem_offset, d.n)) return BC_EINVAL;
     ntiles += (d.n + tile - 1) / tile;
   }
   if (ntiles > BC_STATIC_MAX_TILES) return BC_ELIMIT;

@@ -146,14 +146,6 @@ __device__ __forceinline__ void warp_pack(uint32_t v, bool valid, uint32_t B, ui
   __syncwarp();
 }
 
-__device__ __forceinline__ uint32_t unpack(const uint32_t* src, uint32_t B, uint32_t lane) {
-  const uint32_t bit = lane * B;
-  const uint32_t w = bit >> 5, s = bit & 31u;
-  const uint64_t two = (uint64_t)src[w] | ((s + B > 32u) ? ((uint64_t)src[w + 1] << 32) : 0ull);
-  const uint32_t mask = B >= 32u ? 0xffffffffu : ((1u << B) - 1u);
-  return (uint32_t)(two >> s) & mask;
-}
-
 struct PartyArgs {
   ReluConsts k;
   const void* sh[2];        // [x]_0 (P0's input), [x]_1 (P1's input)
@@ -290,14 +282,22 @@ __global__ void __launch_bounds__(kPB)
     return;
   }
   if (!valid) return;
+  // this lane's B-bit field in each slot's B words: bits [sh, sh + B) of the
+  // word pair (wl, wh); wh is clamped into the slot, where it is not needed
+  const uint32_t bit = lane * B, wl = bit >> 5, sh = bit & 31u;
+  const uint32_t wh = min(wl + 1u, B - 1u);
+  const uint32_t vmask = B >= 32u ? 0xffffffffu : ((1u << B) - 1u);
+  const uint32_t p = k.mp.p;
   const uint32_t* m0 = msg_s + warp * group_words;
-  const uint32_t* m1 = msg_s + cta_words + warp * group_words;
+  const uint32_t* m1 = m0 + cta_words;
   uint32_t any_zero = 0;
 #pragma unroll 5
-  for (uint32_t slot = 0; slot < L; ++slot) {                // step 9
-    const uint32_t w0 = unpack(m0 + slot * B, B, lane);
-    const uint32_t w1 = unpack(m1 + slot * B, B, lane);
-    any_zero |= (add_mod(w0, w1, k.mp.p) == 0u) ? 1u : 0u;
+  for (uint32_t slot = 0; slot < L; ++slot, m0 += B, m1 += B) {   // step 9
+    const uint32_t w0 = __funnelshift_r(m0[wl], m0[wh], sh) & vmask;
+    const uint32_t w1 = __funnelshift_r(m1[wl], m1[wh], sh) & vmask;
+    // w0, w1 < p, so w0 + w1 = 0 mod p iff the sum is 0 or p; as p < 2^32 a
+    // 32-bit sum equals p only when the sum is p
+    any_zero |= ((w0 + w1 == p) | ((w0 | w1) == 0u)) ? 1u : 0u;
   }
   if (!RELU) {
     lane_put<Lane>(a.reply, i, (Lane)((Lane)any_zero - d0) & mask);        // step 10 -> P1

@@ -342,6 +342,40 @@ def test_batch_matches_single_calls(ctx):
             assert torch.equal(it[3], r0) and torch.equal(it[4], r1)
 
 
+@pytest.mark.parametrize("op", ["relu", "drelu"])
+@pytest.mark.parametrize("start", [2**32 - 300, 2**40 + 12_345, 2**48 - 1000])
+def test_element_index_above_32_bits(ctx, op, start):
+    """A slice of a tensor at a large element offset: the element index needs
+    more than 32 bits (the counter's fourth word carries bits 32..47), up to
+    the last index the counter holds, 2^48 - 1.  The outputs match the oracle
+    run at the same element indices."""
+    ring, lx, c, n = 64, 24, 0, 1000
+    x = W.magnitude_bounded_ints(n, 23, seed=91)
+    s0, s1 = _shares(ctx, ring, x, 71)
+    o0, o1 = ctx._empty(n, ring), ctx._empty(n, ring)
+    items = [(Params(ring, lx, c), s0, s1, o0, o1, 72, 0 if op == "relu" else 1, start)]
+    ctx.relu_batch_plan(items)
+    ctx.relu_batch_run()
+    assert ctx.batch_status() == 0
+    es0, es1 = O.share(ring, masked(x, ring), SEED, 71)
+    ofn = O.relu if op == "relu" else O.drelu
+    idx = np.arange(start, start + n, dtype=np.uint64)
+    e0, e1 = ofn(O.params(ring, lx, c), es0, es1, SEED, 72, idx=idx, threads=8)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+
+
+def test_element_index_past_48_bits_rejected(ctx):
+    from paper_2309_04909_gb300 import BicoptorError
+    s = torch.zeros(1000, dtype=torch.int64, device="cuda")
+    o = torch.empty_like(s)
+    ok = [(Params(64, 24, 0), s, s, o, o, 1, 0, 2**48 - 1000)]
+    ctx.relu_batch_plan(ok)                    # ends exactly at 2^48
+    for off in (2**48 - 999, 2**48, 2**64 - 1):
+        with pytest.raises(BicoptorError):
+            ctx.relu_batch_plan([(Params(64, 24, 0), s, s, o, o, 1, 0, off)])
+
+
 def test_batch_config_out_of_range_rejected(ctx):
     from paper_2309_04909_gb300 import BicoptorError
     s = torch.zeros(1000, dtype=torch.int64, device="cuda")
