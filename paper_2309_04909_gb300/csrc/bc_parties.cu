@@ -129,21 +129,41 @@ __device__ __forceinline__ uint32_t seed01_t(const ElemPhilox& ep, const RoundKe
   return ep.block_at(kPair01, kPurPerm, 0, rk).x & 1u;
 }
 
-// Pack one (lx+1)-bit value per lane of the warp into the group's B words at
-// `dst` (B = lx+1 <= 32).  `stage` is this warp's 32-word shared scratch.
-__device__ __forceinline__ void warp_pack(uint32_t v, bool valid, uint32_t B, uint32_t lane,
-                                          uint32_t* stage, uint32_t* dst) {
-  stage[lane] = 0u;
-  __syncwarp();
-  if (valid) {
-    const uint32_t bit = lane * B;
-    const uint32_t w = bit >> 5, s = bit & 31u;
-    atomicOr(&stage[w], v << s);
-    if (s + B > 32u) atomicOr(&stage[w + 1], v >> (32u - s));
+// Pack the group's L slots after the slot loop.  `vals` holds the warp's
+// values, value of lane l for slot k at vals[k * kPB + l] (each thread's
+// column of the shuffle table, overwritten slot by slot).  Lane j < B writes
+// word j of every slot: bits [32 j, 32 j + 32) of the 32 B-bit values laid end
+// to end.  Value l0 = floor(32 j / B) enters shifted right by r0 = 32 j - l0 B,
+// the next ones shifted left by B - r0, 2B - r0, ...  For B >= 16 a word takes
+// at most three values, and the shifts are fixed before the slot loop.
+__device__ __forceinline__ void pack_group(const uint32_t* vals, uint32_t L, uint32_t B,
+                                           uint32_t lane, uint32_t* dst) {
+  if (lane >= B) return;
+  const uint32_t lo_bit = lane * 32u;
+  const uint32_t l0 = lo_bit / B;
+  const uint32_t r0 = lo_bit - l0 * B;
+  if (B >= 16u) {
+    const uint32_t s1 = B - r0, s2 = s1 + B;                  // 0 < s1 <= B
+    const bool has1 = l0 + 1u <= 31u && s1 < 32u;
+    const bool has2 = l0 + 2u <= 31u && s2 < 32u;
+    const uint32_t* v0 = vals + l0;
+    const uint32_t* v1 = vals + (has1 ? l0 + 1u : l0);
+    const uint32_t* v2 = vals + (has2 ? l0 + 2u : l0);
+    const uint32_t m1 = has1 ? 0xffffffffu : 0u, m2 = has2 ? 0xffffffffu : 0u;
+    const uint32_t t1 = has1 ? s1 : 0u, t2 = has2 ? s2 : 0u;
+    for (uint32_t slot = 0; slot < L; ++slot) {
+      const uint32_t o = slot * kPB;
+      dst[slot * B] = (v0[o] >> r0) | ((v1[o] << t1) & m1) | ((v2[o] << t2) & m2);
+    }
+    return;
   }
-  __syncwarp();
-  if (lane < B) dst[lane] = stage[lane];
-  __syncwarp();
+  const uint32_t l1 = min(31u, (lo_bit + 31u) / B);
+  for (uint32_t slot = 0; slot < L; ++slot) {
+    uint32_t word = vals[slot * kPB + l0] >> r0;
+    for (uint32_t l = l0 + 1u, sh = B - r0; l <= l1; ++l, sh += B)   // sh < 32
+      word |= vals[slot * kPB + l] << sh;
+    dst[slot * B] = word;
+  }
 }
 
 struct PartyArgs {
@@ -165,7 +185,6 @@ template <typename Lane, bool RELU>
 __global__ void __launch_bounds__(kPB)
     parties_local_kernel(const PartyArgs a) {
   __shared__ uint32_t perm_s[kMaxSlots * kPB];
-  __shared__ uint32_t stage_s[kWarps][32];
   const uint32_t party = blockIdx.y;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
@@ -205,8 +224,10 @@ __global__ void __launch_bounds__(kPB)
     const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
     uint32_t w = mont_mul(m, rho, k.mp);
     w = party == 0 ? add_mod(w, z, k.mp.p) : sub_mod(w, z, k.mp.p);          // step 8
-    warp_pack(w, valid, B, lane, stage_s[warp], a.w[party] + (g * L + slot) * B);
+    perm[slot * kPB] = valid ? w : 0u;   // the table entry read above is not needed again
   }
+  __syncwarp();
+  pack_group(perm_s + warp * 32u, L, B, lane, a.w[party] + g * L * B + lane);
   if (RELU && valid) {
     // opening of d = x - a: P0 draws a0 from seed02, P1 draws a1 from seed12
     const U32x4 q = ep.block_at(party == 0 ? kPair02 : kPair12, kPurReluTriple, 0, k.rk);
