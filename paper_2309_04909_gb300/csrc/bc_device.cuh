@@ -210,10 +210,6 @@ __device__ __forceinline__ void beaver_mul(const ElemPhilox& ep, const RoundKeys
   o1 = (Lane)(d * b1 + e * a1 + c1) & mask;
 }
 
-// low 32 bits of (a >> sh) for 0 <= sh < 64
-__device__ __forceinline__ uint32_t lo32_shr(uint64_t a, uint32_t sh) { return (uint32_t)(a >> sh); }
-__device__ __forceinline__ uint32_t lo32_shr(uint32_t a, uint32_t sh) { return a >> sh; }
-
 // ---------------------------------------------------------------------------
 // Z_p, odd p < 2^32 with p in (2^lx, 2^(lx+1)).
 // ---------------------------------------------------------------------------
