@@ -35,7 +35,10 @@ def unpack_w(words: np.ndarray, lx: int, n: int) -> np.ndarray:
 
 
 CASES = [(64, 24, 0, 23, 10_007), (32, 9, 14, 22, 4_099), (32, 14, 4, 17, 3_000),
-         (64, 7, 0, 6, 64), (64, 31, 2, 32, 1_001), (16, 5, 2, 6, 33)]
+         (64, 7, 0, 6, 64), (64, 31, 2, 32, 1_001), (16, 5, 2, 6, 33),
+         # one element; one full group; a CTA one short of / exactly / one past 256
+         (64, 24, 0, 23, 1), (64, 24, 0, 23, 32), (64, 24, 0, 23, 255), (64, 24, 0, 23, 256),
+         (32, 14, 4, 17, 257)]
 
 
 @pytest.mark.parametrize("op", ["drelu", "relu"])
@@ -102,4 +105,15 @@ def test_unaligned_message_buffer_rejected():
     msgs["w0"] = base[1:words + 1]             # 4 bytes past a 16-byte boundary
     with pytest.raises(BicoptorError):
         ctx.relu_parties(prm, s0, s1, tensor_id=6, msgs=msgs)
+    ctx.close()
+
+
+def test_parties_empty_input():
+    ctx = Context(SEED)
+    prm = Params(64, 24, 0)
+    e = torch.empty(0, dtype=torch.int64, device="cuda")
+    assert ctx._lib.bc_party_msg_words(24, 0) == 0
+    p0, p1, _ = ctx.relu_parties(prm, e, e, tensor_id=1)
+    assert p0.numel() == 0 and p1.numel() == 0
+    assert ctx.parties_status() == 0
     ctx.close()
