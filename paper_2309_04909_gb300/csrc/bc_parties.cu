@@ -22,8 +22,6 @@
 // protocol's (lx+1)^2 bits per element and sender, padded to a multiple of
 // 256 elements.  P2's kernel fetches its CTA's two messages with bulk
 // asynchronous copies (cp.async.bulk) into shared memory.
-#include <mutex>
-
 #include "bc_internal.h"
 
 namespace bc {
@@ -383,18 +381,18 @@ cudaError_t launch_parties_t(const PartyArgs& a, cudaStream_t s) {
   const uint64_t blocks = (a.n + kPB - 1) / kPB;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(helper_kernel<Lane, RELU>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)helper_smem_bytes(kMaxSlots - 1));
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+  // above 48 KB (lx >= 27) the kernel needs the opt-in, which is per device:
+  // set it on the current device at each such launch
+  const size_t smem = helper_smem_bytes(a.k.lx);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        helper_kernel<Lane, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   parties_local_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, helper_smem_bytes(a.k.lx), s>>>(a);
+  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, smem, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   parties_finish_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);

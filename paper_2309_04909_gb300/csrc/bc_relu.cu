@@ -153,15 +153,15 @@ cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint
     // wave: about 7.5 us below one CTA per SM at lx = 24, rising to 12 and
     // 17.5 us as CTAs share the SMs.  On GB300 they cross near 0.3 waves of
     // the split kernel (about 1.2e4 elements at lx = 24).
-    static int split_per_sm = 0, num_sms = 0;
-    if (split_per_sm == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &split_per_sm, relu_split_kernel<Lane, LX, SHORT, RELU>, kBlock, 0);
-      if (split_per_sm < 1) split_per_sm = 1;
-    }
+    static const int split_per_sm = [] {   // a property of the kernel on this architecture
+      int v = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, relu_split_kernel<Lane, LX, SHORT, RELU>,
+                                                    kBlock, 0);
+      return v < 1 ? 1 : v;
+    }();
+    int dev = 0, num_sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t split_grid = (n + kSplitElems - 1) / kSplitElems;
     if (10 * split_grid <= 3ull * (uint64_t)num_sms * (uint64_t)split_per_sm) {   // 0.3 waves
       relu_split_kernel<Lane, LX, SHORT, RELU><<<(unsigned)split_grid, kBlock, 0, s>>>(
