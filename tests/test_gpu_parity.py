@@ -454,7 +454,8 @@ def test_trunc_then_mul(ctx, bits, kx, ky):
 
 @pytest.mark.parametrize("op", ["drelu", "relu"])
 @pytest.mark.parametrize("ring,lx,c,mag,n", [(64, 24, 0, 23, 20_011), (32, 14, 4, 17, 9_999),
-                                            (32, 9, 14, 22, 4_096), (16, 5, 2, 6, 777)])
+                                            (32, 9, 14, 22, 4_096), (16, 5, 2, 6, 777),
+                                            (64, 7, 0, 6, 1), (64, 31, 0, 32, 300)])
 def test_rss_parity(ctx, op, ring, lx, c, mag, n):
     x = W.magnitude_bounded_ints(n, mag, seed=n)
     rng = np.random.default_rng(n)
@@ -467,3 +468,9 @@ def test_rss_parity(ctx, op, ring, lx, c, mag, n):
     e = O.rss_drelu(O.params(ring, lx, c), x0, x1, x2, SEED, 9, relu=(op == "relu"), threads=8)
     for g, w in zip(ys, e[:3]):
         assert np.array_equal(to_np(g).astype(np.uint64), w)
+
+
+def test_rss_empty_input(ctx):
+    e = torch.empty(0, dtype=torch.int64, device="cuda")
+    ys = ctx.rss_relu(Params(64, 24, 0), e, e, e, tensor_id=9)
+    assert all(y.numel() == 0 for y in ys)
