@@ -4,8 +4,6 @@ import ctypes
 import os
 import re
 
-import pytest
-
 from paper_2309_04909_gb300 import _native
 
 HEADER = os.path.join(_native.INCLUDE, "bicoptor.h")

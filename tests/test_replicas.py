@@ -5,7 +5,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 import torch.multiprocessing as mp
 
 from paper_2309_04909_gb300.replicas import max_over_ranks, rank_seed, shard_by_size

@@ -2,8 +2,6 @@
 continuous-batching scheduler on a simulated device."""
 import random
 
-import pytest
-
 from paper_2309_04909_gb300.serve import Arena, Engine, FakeExecutor, ServeRequest, ServeStats
 
 
