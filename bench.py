@@ -681,6 +681,24 @@ def b_persist_ms(ctx, items):
                for t in TILE_CANDIDATES for c in (0, 2))
 
 
+def median_ms(fn, reps=20, warmup=3):
+    """Median over `reps` runs of fn, each bracketed by its own CUDA events on
+    the current stream.  The batched sets are larger than L2, so runs need no
+    flush between them."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for st, en in evs:
+        st.record()
+        fn()
+        en.record()
+    torch.cuda.synchronize()
+    return statistics.median(st.elapsed_time(en) for st, en in evs)
+
+
 def vgg16_batched_vs_plain(ctx, dev, batch=128):
     """The 13 ReLU tensors of a VGG-16 on 32x32 inputs for
     `batch` images (1,664 tensors, 35,389,440 elements at batch 128), l = 64,
@@ -689,7 +707,7 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
     over the tile queue (autotuned tile / CTAs per SM), eager and graph."""
     import torch
     from paper_2309_04909_gb300 import Params, workloads as W
-    from paper_2309_04909_gb300.batch import ReluBatch, autotune, time_ms
+    from paper_2309_04909_gb300.batch import ReluBatch, autotune
     ts = W.vgg16_batch(batch, seed=2)
     allx = np.concatenate([np.rint(np.ldexp(r, 16)).astype(np.int64) for r in ts.reals])
     total = allx.size
@@ -710,18 +728,18 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
         for it in plain_items:
             ctx.relu(it[0], it[1], it[2], it[5], out=(it[3], it[4]))
 
-    plain_ms = time_ms(plain, reps=3, warmup=1)
+    plain_ms = median_ms(plain)
     g = torch.cuda.CUDAGraph()
     torch.cuda.synchronize()
     with torch.cuda.graph(g):
         plain()
-    plain_graph_ms = time_ms(g.replay, reps=5, warmup=1)
+    plain_graph_ms = median_ms(g.replay)
     best = autotune(ctx, items, reps=2, use_cache=False)
     b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"],
                   best["elems_per_thread"], best["slot_unroll"])
-    batched_ms = time_ms(b.run, reps=5, warmup=1)
+    batched_ms = median_ms(b.run)
     b.capture()
-    batched_graph_ms = time_ms(b.run, reps=5, warmup=1)
+    batched_graph_ms = median_ms(b.run)
     identical = bool(torch.equal(o0, q0) and torch.equal(o1, q1))
     return {"workload": f"VGG-16 32x32 ReLU set, batch {batch}: {len(ts.sizes)} tensors, "
                         f"{total} elements, l=64 f=16 lx=24",
@@ -735,6 +753,7 @@ def vgg16_batched_vs_plain(ctx, dev, batch=128):
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
             "persistent_best_ms": b_persist_ms(ctx, items),
+            "timing": "median of 20 runs, CUDA events per run, after 3 warm-up runs",
             "status": b.status(), "identical_to_plain": identical}
 
 
@@ -913,7 +932,7 @@ def resnet18_batched(ctx, dev, batch=32):
     launch per tensor (graph-replayed)."""
     import torch
     from paper_2309_04909_gb300 import Params, workloads as W
-    from paper_2309_04909_gb300.batch import ReluBatch, autotune, time_ms
+    from paper_2309_04909_gb300.batch import ReluBatch, autotune
     ts = W.resnet18_mixed_batch(batch, seed=3)
     items, plain, keep = [], [], []
     for ring, frac, prm in ((64, 16, Params(64, 24, 0)), (32, 12, Params(32, 14, 4))):
@@ -944,12 +963,12 @@ def resnet18_batched(ctx, dev, batch=32):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         run_plain()
-    plain_ms = time_ms(g.replay, reps=3, warmup=1)
+    plain_ms = median_ms(g.replay)
     best = autotune(ctx, items, reps=1, use_cache=False)
     b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"],
                   best["elems_per_thread"], best["slot_unroll"])
     b.capture()
-    batched_ms = time_ms(b.run, reps=3, warmup=1)
+    batched_ms = median_ms(b.run)
     identical = all(torch.equal(a[3], p[3]) and torch.equal(a[4], p[4])
                     for a, p in zip(items, plain))
     return {"workload": f"ResNet-18 224x224 ReLU set x{batch} at l=64 and l=32: "
@@ -962,6 +981,7 @@ def resnet18_batched(ctx, dev, batch=32):
             "schedule": "grid" if best["schedule"] == 1 else "persistent",
             "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
             "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
+            "timing": "median of 20 runs, CUDA events per run, after 3 warm-up runs",
             "status": b.status(), "identical_to_plain": bool(identical)}
 
 
