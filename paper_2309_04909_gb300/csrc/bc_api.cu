@@ -267,7 +267,8 @@ int bc_create(bc_ctx** out, uint64_t seed, int device, void* cuda_stream) {
   ctx->rk = make_round_keys(seed);
   ctx->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaSetDevice(device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned int) * bc::kMaxBatchGroups);
@@ -838,7 +839,8 @@ int bc_linear_relu_host(bc_ctx* ctx, const bc_linear_relu_args* a) {
   const void* hp[8] = {a->x0, a->x1, a->y0, a->y1, a->relu0, a->relu1, a->det0, a->det1};
   void* dp[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool direct = ctx->host_path != BC_HOST_STAGED;
-  for (int q = 0; q < (det ? 8 : 6) && direct; ++q) direct = (dp[q] = mapped_host(hp[q])) != nullptr;
+  for (int q = 0; q < (det ? 8 : 6) && direct; ++q)
+    direct = (dp[q] = mapped_host(hp[q])) != nullptr;
   if (direct) {
     const bc::LinearIo io{dp[0], dp[1], dp[2], dp[3], nullptr, nullptr, nullptr,
                           nullptr, dp[6], dp[7], dp[4], dp[5]};

@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kBlock)
   }
   uint64_t acc = 0;
 #pragma unroll
-  for (int j = 0; j < kChains; ++j) acc ^= ((uint64_t)b[j] << 32) ^ a[j] ^ ((uint64_t)c[j] << 17) ^ d[j];
+  for (int j = 0; j < kChains; ++j)
+    acc ^= ((uint64_t)b[j] << 32) ^ a[j] ^ ((uint64_t)c[j] << 17) ^ d[j];
   if (acc == 0x0123456789ABCDEFull) sink[0] = acc;   // keeps every chain live
 }
 

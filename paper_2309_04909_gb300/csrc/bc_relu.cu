@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kBlock)
 
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
 cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n, void* o0,
-                     void* o1, const AuditPtrs& aud, cudaStream_t s) {
+                     void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
   const uint64_t grid = (n + kBlock - 1) / kBlock;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
@@ -159,9 +159,6 @@ cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint
                                                     kBlock, 0);
       return v < 1 ? 1 : v;
     }();
-    int dev = 0, num_sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t split_grid = (n + kSplitElems - 1) / kSplitElems;
     if (10 * split_grid <= 3ull * (uint64_t)num_sms * (uint64_t)split_per_sm) {   // 0.3 waves
       relu_split_kernel<Lane, LX, SHORT, RELU><<<(unsigned)split_grid, kBlock, 0, s>>>(
@@ -178,18 +175,18 @@ cudaError_t launch_t(const ReluConsts& k, const void* sh0, const void* sh1, uint
 
 template <typename Lane, bool RELU, bool AUDIT>
 cudaError_t launch_lx(const ReluConsts& k, const void* sh0, const void* sh1, uint64_t n,
-                      void* o0, void* o1, const AuditPtrs& aud, cudaStream_t s) {
+                      void* o0, void* o1, const AuditPtrs& aud, int num_sms, cudaStream_t s) {
   const bool shrt = sizeof(Lane) == 8 && k.c + k.lx < 32;
   switch (k.lx) {
     case 24:
-      return shrt ? launch_t<Lane, 24, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s)
-                  : launch_t<Lane, 24, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
-    case 14: return launch_t<Lane, 14, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
-    case 9: return launch_t<Lane, 9, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+      return shrt ? launch_t<Lane, 24, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                  : launch_t<Lane, 24, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 14: return launch_t<Lane, 14, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    case 9: return launch_t<Lane, 9, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
     case 7:
-      return shrt ? launch_t<Lane, 7, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s)
-                  : launch_t<Lane, 7, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
-    default: return launch_t<Lane, 0, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, s);
+      return shrt ? launch_t<Lane, 7, true, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                  : launch_t<Lane, 7, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
+    default: return launch_t<Lane, 0, false, RELU, AUDIT>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
   }
 }
 
@@ -375,23 +372,22 @@ cudaError_t launch_rss(const ReluConsts& k, bool relu, const void* const* x, uin
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
                         cudaStream_t s) {
-  (void)num_sms;
   const bool lane64 = k.ring_bits > 32;
   const bool audit = aud.any();
   if (lane64) {
     if (relu) {
-      return audit ? launch_lx<uint64_t, true, true>(k, sh0, sh1, n, o0, o1, aud, s)
-                   : launch_lx<uint64_t, true, false>(k, sh0, sh1, n, o0, o1, aud, s);
+      return audit ? launch_lx<uint64_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                   : launch_lx<uint64_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
     }
-    return audit ? launch_lx<uint64_t, false, true>(k, sh0, sh1, n, o0, o1, aud, s)
-                 : launch_lx<uint64_t, false, false>(k, sh0, sh1, n, o0, o1, aud, s);
+    return audit ? launch_lx<uint64_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                 : launch_lx<uint64_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
   }
   if (relu) {
-    return audit ? launch_lx<uint32_t, true, true>(k, sh0, sh1, n, o0, o1, aud, s)
-                 : launch_lx<uint32_t, true, false>(k, sh0, sh1, n, o0, o1, aud, s);
+    return audit ? launch_lx<uint32_t, true, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+                 : launch_lx<uint32_t, true, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
   }
-  return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, s)
-               : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, s);
+  return audit ? launch_lx<uint32_t, false, true>(k, sh0, sh1, n, o0, o1, aud, num_sms, s)
+               : launch_lx<uint32_t, false, false>(k, sh0, sh1, n, o0, o1, aud, num_sms, s);
 }
 
 cudaError_t launch_linear_relu(const LinearConsts& c, const LinearIo& io, uint64_t n,
