@@ -62,6 +62,8 @@ class Params:
 
 
 _PRM_STRUCTS: Dict["Params", DreluParams] = {}
+# the current stream's raw cudaStream_t of a device, as an int (torch's own accessor)
+_RAW_STREAM = getattr(torch._C, "_cuda_getCurrentRawStream", None)
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -76,6 +78,7 @@ class Context:
     def __init__(self, seed: int, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
         self._lib = _native.lib()
         self.device = torch.device("cuda", device)
+        self._dev_index = device
         self._stream = stream
         self._last_stream = None
         h = ctypes.c_void_p()
@@ -90,9 +93,14 @@ class Context:
 
     def _sync_stream(self):
         # calls follow torch's current stream unless a stream was pinned; the
-        # library is told only when the stream changes
-        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
-        h = s.cuda_stream
+        # library is told only when the stream changes.  The raw handle is read
+        # without building a Stream object where torch offers that.
+        if self._stream is not None:
+            h = self._stream.cuda_stream
+        elif _RAW_STREAM is not None:
+            h = _RAW_STREAM(self._dev_index)
+        else:
+            h = torch.cuda.current_stream(self.device).cuda_stream
         if h != self._last_stream:
             self._lib.bc_set_stream(self._h, h)
             self._last_stream = h

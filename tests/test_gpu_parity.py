@@ -474,3 +474,30 @@ def test_rss_empty_input(ctx):
     e = torch.empty(0, dtype=torch.int64, device="cuda")
     ys = ctx.rss_relu(Params(64, 24, 0), e, e, e, tensor_id=9)
     assert all(y.numel() == 0 for y in ys)
+
+
+def test_calls_follow_torch_current_stream(ctx):
+    """Calls launch on torch's current stream: a call inside torch's CUDA-graph
+    capture is captured (a launch on any other stream would break the
+    capture), and a call under a side-stream context matches the default one."""
+    n = 5_000
+    x = W.magnitude_bounded_ints(n, 23, seed=93)
+    s0, s1 = _shares(ctx, 64, x, 94)
+    prm = Params(64, 24, 0)
+    want0, want1 = ctx.relu(prm, s0, s1, tensor_id=95)
+    o0, o1 = torch.empty_like(s0), torch.empty_like(s1)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.relu(prm, s0, s1, tensor_id=95, out=(o0, o1))
+    side.synchronize()
+    assert torch.equal(o0, want0) and torch.equal(o1, want1)
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        ctx.relu(prm, s0, s1, tensor_id=95, out=(o0, o1))
+    o0.zero_()
+    o1.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(o0, want0) and torch.equal(o1, want1)
