@@ -392,7 +392,7 @@ int bc_count_trunc_failures(bc_ctx *ctx, int out_bits, int k, const int64_t *x, 
  * SM (the widening products run as Philox-4x32 rounds, the hot path's form);
  * the best of three runs is reported, in warp-lane instructions per
  * second, plus the SM clock one CTA saw (cycle counter against the global
- * timer).  Allocates a few bytes and a stream, runs about 0.3 s, synchronises;
+ * timer).  Allocates a few bytes and a stream, runs about 0.4 s, synchronises;
  * BC_ECUDA on a CUDA failure. */
 typedef struct {
   double imad_wide_per_s;   /* 32x32->64 products, in Philox rounds          */
@@ -400,6 +400,7 @@ typedef struct {
   double alu_per_s;         /* integer-ALU instructions (xor, add pairs)      */
   double sm_mhz;            /* SM clock during the last run                   */
   int sm_count;
+  double imad_hi_per_s;     /* high halves of 32x32 products (hi32(x*k))      */
 } bc_int_peaks;
 int bc_measure_int_peaks(int device, bc_int_peaks *out);
 

@@ -432,15 +432,17 @@ class Context:
 
 def measure_int_peaks(device: int = 0) -> Dict[str, float]:
     """Measured rates of the integer instructions that bound the hot path
-    (bc_measure_int_peaks): widening and 32-bit multiply-adds and integer-ALU
-    instructions per second, with the SM clock seen during the runs."""
+    (bc_measure_int_peaks): widening products, 32-bit multiply-adds, high
+    halves of products and integer-ALU instructions per second, with the SM
+    clock seen during the runs."""
     lib = _native.lib()
     p = _native.IntPeaks()
     rc = lib.bc_measure_int_peaks(device, ctypes.byref(p))
     if rc != 0:
         raise BicoptorError(f"bc_measure_int_peaks failed: {lib.bc_strerror(rc).decode()}")
     return {"imad_wide_per_s": p.imad_wide_per_s, "imad_per_s": p.imad_per_s,
-            "alu_per_s": p.alu_per_s, "sm_mhz": p.sm_mhz, "sm_count": p.sm_count}
+            "imad_hi_per_s": p.imad_hi_per_s, "alu_per_s": p.alu_per_s, "sm_mhz": p.sm_mhz,
+            "sm_count": p.sm_count}
 
 
 def relu_batch_static(seed: int, items: Sequence[Tuple], tile_elems: int = 0,

@@ -118,7 +118,7 @@ class BatchConfig(ctypes.Structure):
 class IntPeaks(ctypes.Structure):
     _fields_ = [("imad_wide_per_s", ctypes.c_double), ("imad_per_s", ctypes.c_double),
                 ("alu_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double),
-                ("sm_count", c_int)]
+                ("sm_count", c_int), ("imad_hi_per_s", ctypes.c_double)]
 
 
 class LinearReluArgs(ctypes.Structure):

@@ -17,11 +17,11 @@ that shows up as a higher fraction of the roofline, not as less work):
       window (Alg. newtrc2)     2 parties x 2 windows x (shift + mask)              8 ops
       pair sum (step 4)         2 parties x (add + mask)                            4
       modulo switch (step 5)    P0 test + select, P1 add                            3
-      rho_k, z_k from 128 bits  2 x (high product of the low word + widening)       5 ops, 2x3 mul
+      rho_k, z_k from 128 bits  2 x (high product of the low word + widening)       5 ops, 2x4 mul
       masking (step 7)          2 Montgomery products (wide, low, wide, cmp, sel)  10 ops, 2x5 mul
       reshare (step 8)          2 x (add, compare, select)                          6
       P2 (step 9)               add mod p (3) + zero test and OR (2)                5
-  shuffle (step 6)    lx swaps x (index high-multiply + 2 loads + 2 stores)         5 lx, lx mul
+  shuffle (step 6)    lx swaps x (index high-multiply + 2 loads + 2 stores)         5 lx, 2 lx mul
   flip (steps 1-2)    2 negations                                                   6
   ReLU finish         triple completion, openings, 5 ring products, select          40 ops (l>32) / 20
   DReLU finish        reply and unflip                                              8 ops
@@ -29,14 +29,17 @@ Philox blocks per element: ceil((lx+1)/4) (t and the shuffle) + (lx+1) (masks) +
 3 (ReLU triple, l > 32; 2 at l <= 32) or 1 (DReLU reply).
 
 "mul" counts multiplier lane-operations: a widening 32x32->64 product is 2, a
-low or high 32-bit product 1, a 64-bit low product 4.
+high 32-bit product (hi32(a b)) also 2, a low 32-bit product 1, a 64-bit low
+product 4.  The high product's weight is measured: chains of it issue at
+7.9 lanes per clock per sub-partition on GB300, the rate of widening products
+(7.2 in Philox rounds), against 16.0 for low products.
 """
 from __future__ import annotations
 
 PHILOX_BLOCK_OPS = 40
 PHILOX_BLOCK_MUL = 40             # 20 widening products
 SLOT_OPS = 8 + 4 + 3 + 5 + 10 + 6 + 5     # = 41
-SLOT_MUL = 6 + 10                          # draws + 2 Montgomery products
+SLOT_MUL = 8 + 10                          # draws + 2 Montgomery products
 
 
 def philox_blocks(lx: int, ring_bits: int, relu: bool) -> int:
@@ -56,7 +59,8 @@ def mul_ops_per_element(lx: int, ring_bits: int, relu: bool = True) -> int:
     """Multiplier lane-operations per element (see module doc)."""
     L = lx + 1
     finish = (20 if ring_bits > 32 else 5) if relu else 0
-    return philox_blocks(lx, ring_bits, relu) * PHILOX_BLOCK_MUL + L * SLOT_MUL + lx + finish
+    return (philox_blocks(lx, ring_bits, relu) * PHILOX_BLOCK_MUL + L * SLOT_MUL + 2 * lx
+            + finish)
 
 
 # The fused step of a linear layer followed by a ReLU adds, per element:
@@ -82,6 +86,16 @@ def linear_relu_mul_ops_per_element(lx: int, ring_bits: int) -> int:
 
 def linear_relu_int_ops_per_element(lx: int, ring_bits: int) -> int:
     return product_int_ops_per_element(ring_bits) + int_ops_per_element(lx, ring_bits, True)
+
+
+def mul_counts_split(lx: int, ring_bits: int, relu: bool = True, product: bool = False):
+    """(widening, low, high) products per element: mul_counts with its single
+    products split into low halves (Montgomery's q, ring cross terms) and high
+    halves (the 64x32 draws' hi32(lo q), one per draw, and the shuffle's lx
+    indices), which the multiplier may issue at different rates."""
+    wide, single = mul_counts(lx, ring_bits, relu, product)
+    high = 2 * (lx + 1) + lx
+    return wide, single - high, high
 
 
 def mul_counts(lx: int, ring_bits: int, relu: bool = True, product: bool = False):

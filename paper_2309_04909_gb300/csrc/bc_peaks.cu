@@ -10,6 +10,9 @@
 //   low multiply-add       x = x * x + c (32-bit; the square keeps a compiler
 //                          from folding unrolled steps into one)
 //   logic + add            x = (x ^ c) + K (two integer-ALU instructions)
+//   high product           x = hi32(x * K) ^ c (the form of the hot path's
+//                          64 x 32 draws and shuffle indices; the XOR goes to
+//                          the ALU pipe)
 // One CTA also reads its SM's cycle counter against the global nanosecond
 // timer, so the rates can be expressed per SM clock.
 #include "bc_internal.h"
@@ -62,8 +65,10 @@ __global__ void __launch_bounds__(kBlock)
           c[j] = n2;
         } else if (KIND == 1) {   // 32-bit multiply-add
           a[j] = a[j] * a[j] + b[j];
-        } else {                  // logic + add
+        } else if (KIND == 2) {   // logic + add
           a[j] = (a[j] ^ b[j]) + 0x9E3779B9u;
+        } else {                  // high product
+          a[j] = __umulhi(a[j], kPeakKeys[u]) ^ b[j];
         }
       }
     }
@@ -106,17 +111,19 @@ extern "C" int bc_measure_int_peaks(int device, bc_int_peaks* out) {
     }
     const unsigned grid = (unsigned)num_sms * bc::kPeakCtasPerSm;
     const int iters = 16384;
-    double* rates[3] = {&out->imad_wide_per_s, &out->imad_per_s, &out->alu_per_s};
+    double* rates[4] = {&out->imad_wide_per_s, &out->imad_per_s, &out->alu_per_s,
+                        &out->imad_hi_per_s};
     // instructions of the measured kind per thread: iters x 4 x chains, x2 for the two
     // products of a Philox round and for logic + add
-    const double per_thread[3] = {iters * 8.0 * bc::kChains, iters * 4.0 * bc::kChains,
-                                  iters * 8.0 * bc::kChains};
-    for (int kind = 0; kind < 3 && rc == BC_OK; ++kind) {
+    const double per_thread[4] = {iters * 8.0 * bc::kChains, iters * 4.0 * bc::kChains,
+                                  iters * 8.0 * bc::kChains, iters * 4.0 * bc::kChains};
+    for (int kind = 0; kind < 4 && rc == BC_OK; ++kind) {
       for (int rep = 0; rep < 3 && rc == BC_OK; ++rep) {   // first run warms the clocks
         cudaEventRecord(e0, s);
         if (kind == 0) bc::int_peak_kernel<0><<<grid, bc::kBlock, 0, s>>>(rep, iters, sink, probe);
         if (kind == 1) bc::int_peak_kernel<1><<<grid, bc::kBlock, 0, s>>>(rep, iters, sink, probe);
         if (kind == 2) bc::int_peak_kernel<2><<<grid, bc::kBlock, 0, s>>>(rep, iters, sink, probe);
+        if (kind == 3) bc::int_peak_kernel<3><<<grid, bc::kBlock, 0, s>>>(rep, iters, sink, probe);
         cudaEventRecord(e1, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
           rc = BC_ECUDA;

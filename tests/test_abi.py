@@ -49,4 +49,9 @@ def test_costmodel_counts():
     assert C.philox_blocks(24, 64, True) == 7 + 25 + 3
     assert C.philox_blocks(9, 32, False) == 3 + 10 + 1
     assert C.int_ops_per_element(24, 64) > C.int_ops_per_element(9, 32)
-    assert C.mul_ops_per_element(24, 64) == 35 * 40 + 25 * 16 + 24 + 20
+    # per slot: two 64x32 draws (widening + high product, 4 each) and two
+    # Montgomery products (5 each); the shuffle's lx high products (2 each)
+    assert C.mul_ops_per_element(24, 64) == 35 * 40 + 25 * 18 + 2 * 24 + 20
+    w, lo, hi = C.mul_counts_split(24, 64, relu=True, product=True)
+    assert (w, lo, hi) == (921, 72, 74)
+    assert 2 * w + lo + 2 * hi == C.linear_relu_mul_ops_per_element(24, 64)

@@ -17,4 +17,5 @@ def test_int_peaks_plausible():
     per_clock = lambda r: r / (p["sm_count"] * 4 * p["sm_mhz"] * 1e6)
     assert 8.0 < per_clock(p["imad_per_s"]) < 33.0
     assert 0.0 < p["imad_wide_per_s"] < p["imad_per_s"]
+    assert 0.0 < p["imad_hi_per_s"] <= 1.05 * p["imad_per_s"]
     assert p["alu_per_s"] > 0.0
