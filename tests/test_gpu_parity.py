@@ -387,7 +387,7 @@ def test_batch_config_out_of_range_rejected(ctx):
             ctx.relu_batch_plan(items, **kw)
 
 
-def test_full_size_config2_sampled(ctx):
+def test_full_size_step_l64_2p22_sampled(ctx):
     """N = 2^22 at l = 64, the benchmark's launch configuration; 4,096 sampled
     elements recomputed by the oracle."""
     n = 1 << 22
