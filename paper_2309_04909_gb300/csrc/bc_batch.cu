@@ -22,7 +22,7 @@ namespace {
 template <typename Lane, int LX, bool SHORT, bool RELU, int UNROLL>
 __device__ __forceinline__ void run_tile(const ReluConsts& k, const BatchTensor& bt,
                                          uint64_t start, uint32_t count, uint32_t lane,
-                                         uint32_t* perm) {
+                                         uint32_t* perm, const uint64_t* r2) {
   const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
   const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
   Lane* o0 = static_cast<Lane*>(bt.o0);
@@ -33,7 +33,7 @@ __device__ __forceinline__ void run_tile(const ReluConsts& k, const BatchTensor&
     const uint64_t i = start + j;
     Lane r0, r1;
     bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
-        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i, r2);
     o0[i] = r0;
     o1[i] = r1;
   }
@@ -45,12 +45,14 @@ __global__ void __launch_bounds__(kBlock)
                       const BatchTile* __restrict__ tiles, uint32_t begin, uint32_t end,
                       unsigned int* __restrict__ counter, int* __restrict__ status) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  __shared__ uint64_t r2_s[kBlock / 32][kMaxSlots];   // per warp: its tile's tensor
   uint32_t* perm = perm_s + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31u;
+  uint64_t* r2 = r2_s[threadIdx.x >> 5];
   for (;;) {
     uint32_t tile = 0;
     if (lane == 0) tile = begin + atomicAdd(counter, 1u);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
+    tile = __shfl_sync(0xffffffffu, tile, 0);   // also: every lane is done with the last tile
     if (tile >= end) break;
     const BatchTile tl = tiles[tile];
     const BatchTensor bt = tensors[tl.tensor];
@@ -58,10 +60,12 @@ __global__ void __launch_bounds__(kBlock)
       if (lane == 0) atomicExch(status, BC_ECHECK);
       continue;
     }
+    r2[lane] = round2_product(bt.tensor_id, lane, k.rk);   // kMaxSlots == 32 lanes
+    __syncwarp();
     if (bt.op == BC_OP_DRELU)
-      run_tile<Lane, LX, SHORT, false, UNROLL>(k, bt, tl.start, tl.count, lane, perm);
+      run_tile<Lane, LX, SHORT, false, UNROLL>(k, bt, tl.start, tl.count, lane, perm, r2);
     else
-      run_tile<Lane, LX, SHORT, true, UNROLL>(k, bt, tl.start, tl.count, lane, perm);
+      run_tile<Lane, LX, SHORT, true, UNROLL>(k, bt, tl.start, tl.count, lane, perm, r2);
   }
 }
 
@@ -70,7 +74,8 @@ __global__ void __launch_bounds__(kBlock)
 // EPT = 1 has no loop, so nothing is kept live across elements.
 template <typename Lane, int LX, bool SHORT, bool RELU, int UNROLL, int EPT>
 __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor& bt,
-                                          const BatchTile& tl, uint32_t* perm) {
+                                          const BatchTile& tl, uint32_t* perm,
+                                          const uint64_t* r2) {
   const Lane* sh0 = static_cast<const Lane*>(bt.sh0);
   const Lane* sh1 = static_cast<const Lane*>(bt.sh1);
   Lane* o0 = static_cast<Lane*>(bt.o0);
@@ -81,7 +86,7 @@ __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor
     const uint64_t i = tl.start + threadIdx.x;
     Lane r0, r1;
     bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
-        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i, r2);
     o0[i] = r0;
     o1[i] = r1;
     return;
@@ -91,7 +96,7 @@ __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor
     const uint64_t i = tl.start + j;
     Lane r0, r1;
     bicoptor_element<Lane, LX, SHORT, RELU, false, false, UNROLL>(
-        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i);
+        k, k.rk, bt.tensor_id, sh0[i], sh1[i], bt.elem_offset + i, perm, r0, r1, none, i, r2);
     o0[i] = r0;
     o1[i] = r1;
   }
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kBlock)
                            const BatchTile* __restrict__ tiles, uint32_t begin,
                            int* __restrict__ status) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  __shared__ uint64_t r2_s[kMaxSlots];   // the tile's tensor: round2_product(tensor_id, b)
   uint32_t* perm = perm_s + threadIdx.x;
   const BatchTile tl = tiles[begin + blockIdx.x];
   const BatchTensor bt = tensors[tl.tensor];
@@ -110,10 +116,12 @@ __global__ void __launch_bounds__(kBlock)
     if (threadIdx.x == 0) atomicExch(status, BC_ECHECK);
     return;
   }
+  if (threadIdx.x < kMaxSlots) r2_s[threadIdx.x] = round2_product(bt.tensor_id, threadIdx.x, k.rk);
+  __syncthreads();
   if (bt.op == BC_OP_DRELU)
-    grid_tile<Lane, LX, SHORT, false, UNROLL, EPT>(k, bt, tl, perm);
+    grid_tile<Lane, LX, SHORT, false, UNROLL, EPT>(k, bt, tl, perm, r2_s);
   else
-    grid_tile<Lane, LX, SHORT, true, UNROLL, EPT>(k, bt, tl, perm);
+    grid_tile<Lane, LX, SHORT, true, UNROLL, EPT>(k, bt, tl, perm, r2_s);
 }
 
 template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>

@@ -110,6 +110,16 @@ __device__ __forceinline__ U32x4 draw_block(uint32_t pair, uint32_t purpose, uin
   return philox((uint32_t)elem, tensor_id, block, stream_tag(pair, purpose, elem), rk);
 }
 
+// Round 2's first product of block b of any stream: M0 * (hi32(M1 b) ^
+// tensor_id ^ k0[0]).  Its operand is round 1's output word 0, which depends
+// on the block index and the tensor id only -- not on the element or the
+// stream -- so a CTA working on one tensor can share a table of it.
+__host__ __device__ __forceinline__ uint64_t round2_product(uint32_t tensor_id, uint32_t b,
+                                                            const RoundKeys& rk) {
+  const uint32_t a0 = (uint32_t)(((uint64_t)kPhiloxM1 * b) >> 32) ^ tensor_id ^ rk.k0[0];
+  return (uint64_t)kPhiloxM0 * a0;
+}
+
 // Philox blocks of one element with round 1 factored: every block of the
 // element shares c0 = lo32(elem), so M0 * c0 is computed once per element;
 // M1 * c2 (c2 = block index) is a constant or a running sum in the caller.
@@ -135,6 +145,21 @@ struct ElemPhilox {
                                             const RoundKeys& rk) const {
     return block(pair, purpose, (uint64_t)kPhiloxM1 * b, rk);
   }
+  // block b with round 2's first product p0 = round2_product(tensor_id, b)
+  // supplied by the caller
+  __device__ __forceinline__ U32x4 block_p0(uint32_t pair, uint32_t purpose, uint32_t b,
+                                            uint64_t p0, const RoundKeys& rk) const {
+    const uint32_t tag = (pair << 24) | (purpose << 16) | elem_hi16;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * (e_hi ^ tag ^ rk.k1[0]);
+    const uint32_t x1 = (uint32_t)((uint64_t)kPhiloxM1 * b);   // round 1's word 1
+    return philox_rounds_3_10((uint32_t)(p1 >> 32) ^ x1 ^ rk.k0[1], (uint32_t)p1,
+                              (uint32_t)(p0 >> 32) ^ e_lo ^ rk.k1[1], (uint32_t)p0, rk);
+  }
+  // block_at, or block_p0 from the table r2 (r2[b] = round2_product(tensor_id, b))
+  __device__ __forceinline__ U32x4 block_tab(uint32_t pair, uint32_t purpose, uint32_t b,
+                                             const uint64_t* r2, const RoundKeys& rk) const {
+    return r2 ? block_p0(pair, purpose, b, r2[b], rk) : block_at(pair, purpose, b, rk);
+  }
 };
 
 // The blocks of one (element, pair, purpose) stream, e.g. the lx + 1 mask
@@ -157,7 +182,10 @@ struct StreamPhilox {
   // block with M1 * block = mb (64-bit); equal to ElemPhilox::block
   __device__ __forceinline__ U32x4 block(uint64_t mb, const RoundKeys& rk) const {
     const uint32_t a0 = (uint32_t)(mb >> 32) ^ tensor_id ^ rk.k0[0];
-    const uint64_t p0 = (uint64_t)kPhiloxM0 * a0;
+    return block_p0(mb, (uint64_t)kPhiloxM0 * a0, rk);
+  }
+  // the same with round 2's first product p0 = round2_product(tensor_id, block)
+  __device__ __forceinline__ U32x4 block_p0(uint64_t mb, uint64_t p0, const RoundKeys& rk) const {
     return philox_rounds_3_10(q_hi ^ (uint32_t)mb ^ rk.k0[1], q_lo,
                               (uint32_t)(p0 >> 32) ^ e_lo ^ rk.k1[1], (uint32_t)p0, rk);
   }
@@ -188,17 +216,18 @@ __device__ __forceinline__ uint64_t block_elem<uint64_t>(const U32x4& b, int j) 
 // layers): the triple a0, b0, c0 comes from seed02 and a1, b1 from seed12
 // (purpose kPurMulTriple), P2 completes it with c1 = (a0 + a1)(b0 + b1) - c0;
 // P0 and P1 open d = x - a and e = y - b, and P0 adds the public d e.
+// r2 (optional): round2_product(tensor_id, b) for b = 0, 1.
 template <typename Lane>
 __device__ __forceinline__ void beaver_mul(const ElemPhilox& ep, const RoundKeys& rk, Lane mask,
                                            Lane x0, Lane x1, Lane y0, Lane y1, Lane& o0,
-                                           Lane& o1) {
-  const U32x4 q0 = ep.block_at(kPair02, kPurMulTriple, 0, rk);
-  const U32x4 q1 = ep.block_at(kPair12, kPurMulTriple, 0, rk);
+                                           Lane& o1, const uint64_t* r2 = nullptr) {
+  const U32x4 q0 = ep.block_tab(kPair02, kPurMulTriple, 0, r2, rk);
+  const U32x4 q1 = ep.block_tab(kPair12, kPurMulTriple, 0, r2, rk);
   Lane a0, b0, c0;
   if (sizeof(Lane) == 4) {
     a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
   } else {
-    const U32x4 q2 = ep.block_at(kPair02, kPurMulTriple, 1, rk);
+    const U32x4 q2 = ep.block_tab(kPair02, kPurMulTriple, 1, r2, rk);
     a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
   }
   const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;

@@ -92,10 +92,11 @@ __device__ __forceinline__ Triple<Lane> triple_from_blocks(const U32x4& q0, cons
 
 template <typename Lane>
 __device__ __forceinline__ Triple<Lane> draw_triple(const ElemPhilox& ep, uint32_t purpose,
-                                                    Lane mask, const RoundKeys& rk) {
-  const U32x4 q0 = ep.block_at(kPair02, purpose, 0, rk);
-  const U32x4 q1 = ep.block_at(kPair12, purpose, 0, rk);
-  const U32x4 q2 = sizeof(Lane) == 4 ? q0 : ep.block_at(kPair02, purpose, 1, rk);
+                                                    Lane mask, const RoundKeys& rk,
+                                                    const uint64_t* r2 = nullptr) {
+  const U32x4 q0 = ep.block_tab(kPair02, purpose, 0, r2, rk);
+  const U32x4 q1 = ep.block_tab(kPair12, purpose, 0, r2, rk);
+  const U32x4 q2 = sizeof(Lane) == 4 ? q0 : ep.block_tab(kPair02, purpose, 1, r2, rk);
   return triple_from_blocks<Lane>(q0, q1, q2, mask);
 }
 
@@ -113,13 +114,12 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
 
 // Steps 3-9 of one message slot whose window index is i: P0's and P1's
 // windows (Alg. newtrc2), pair sums, Alg. modswitch, the mask r_k and the
-// reshare z_k from the slot's seed01 block (mb = M1 * slot), and P2's zero
-// test.  Returns 1 when w0 + w1 = 0 mod p; w0, w1 are the two messages.
+// reshare z_k from the slot's seed01 block rz, and P2's zero test.  Returns 1
+// when w0 + w1 = 0 mod p; w0, w1 are the two messages.
 template <int LX, bool SHORT, typename Lane>
-__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, const RoundKeys& rk,
-                                                   Lane f0, Lane nf1, uint32_t i,
-                                                   const StreamPhilox& mask_stream, uint64_t mb,
-                                                   uint32_t& w0, uint32_t& w1) {
+__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0, Lane nf1,
+                                                   uint32_t i, const U32x4& rz, uint32_t& w0,
+                                                   uint32_t& w1) {
   constexpr bool kWide = (LX == 0) || (LX > 30);
   using M = SlotMath<LX, kWide>;
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
@@ -134,9 +134,8 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, const Ro
   // step 5: Alg. modswitch
   const uint32_t m0 = v0 ? v0 : k.two_lx;
   const uint32_t m1 = v1 + k.p_minus_2lx;
-  // step 7: rho_k, z_k from the slot's seed01 block; the mask r_k =
+  // step 7: rho_k, z_k from the slot's seed01 block rz; the mask r_k =
   // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
-  const U32x4 rz = mask_stream.block(mb, rk);
   const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
   const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
   w0 = mont_mul<kWide>(m0, rho, k.mp);
@@ -152,14 +151,16 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, const Ro
 // column of the shared-memory shuffle table (stride kBlock words).
 // DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
 // (the RSS protocol finishes differently).  UNROLL: unroll of the loop over
-// the lx + 1 message slots (the key-bit loop).
+// the lx + 1 message slots (the key-bit loop).  r2tab (optional): the CTA's
+// table of round2_product(tensor_id, b) for b = 0 .. lx, shared by its threads.
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false,
           int UNROLL = kSlotUnroll>
 __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
                                                  uint32_t tensor_id, Lane s0, Lane s1,
                                                  uint64_t elem, uint32_t* perm, Lane& out0,
                                                  Lane& out1, const AuditPtrs& aud,
-                                                 uint64_t out_idx) {
+                                                 uint64_t out_idx,
+                                                 const uint64_t* r2tab = nullptr) {
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
   const uint32_t L = lx + 1;
   const Lane mask = (Lane)k.ring_mask;
@@ -176,7 +177,8 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
 #pragma unroll
   for (uint32_t b = 0; b < (LX ? (uint32_t)((LX + 4) >> 2) : 8u); ++b) {
     if (!LX && b >= nblk) break;
-    const U32x4 wb = perm_stream.block((uint64_t)kPhiloxM1 * b, rk);
+    const uint64_t mbp = (uint64_t)kPhiloxM1 * b;
+    const U32x4 wb = r2tab ? perm_stream.block_p0(mbp, r2tab[b], rk) : perm_stream.block(mbp, rk);
     const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -206,8 +208,9 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
 #pragma unroll UNROLL
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     uint32_t w0, w1;
-    any_zero |= slot_zero_test<LX, SHORT>(k, rk, f0, nf1, perm[slot * kBlock], mask_stream, mb,
-                                          w0, w1);
+    const U32x4 rz =
+        r2tab ? mask_stream.block_p0(mb, r2tab[slot], rk) : mask_stream.block(mb, rk);
+    any_zero |= slot_zero_test<LX, SHORT>(k, f0, nf1, perm[slot * kBlock], rz, w0, w1);
     if (AUDIT) {
       if (aud.w0) aud.w0[out_idx * L + slot] = w0;
       if (aud.w1) aud.w1[out_idx * L + slot] = w1;
@@ -222,7 +225,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
 
   if (!RELU) {
     // step 10: [DReLU']_0 = d0 from seed02 (P0 derives it), [DReLU']_1 to P1
-    const U32x4 rb = ep.block_at(kPair02, kPurReply, 0, rk);
+    const U32x4 rb = ep.block_tab(kPair02, kPurReply, 0, r2tab, rk);
     const Lane d0 = block_elem<Lane>(rb, 0) & mask;
     const Lane d1 = ((Lane)dprime - d0) & mask;
     // step 11: [DReLU] = [DReLU' xor t], the public t added by P0
@@ -230,7 +233,7 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
     out1 = t ? ring_neg(d1, mask) : d1;
     if (AUDIT && aud.reply) store_lane<Lane>(aud.reply, out_idx, d1);
   } else {
-    const Triple<Lane> T = draw_triple<Lane>(ep, kPurReluTriple, mask, rk);
+    const Triple<Lane> T = draw_triple<Lane>(ep, kPurReluTriple, mask, rk, r2tab);
     const Lane c1 = (Lane)((T.a0 + T.a1) * (T.b0 + T.b1) - T.c0) & mask;   // P2 -> P1 (pre)
     const Lane e = (Lane)((Lane)dprime - T.b0 - T.b1) & mask;             // P2 -> P0, P1
     const Lane open0 = (Lane)(s0 - T.a0) & mask;                          // P0 -> P1

@@ -20,12 +20,15 @@ __global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
     relu_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
                 uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, const AuditPtrs aud) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  __shared__ uint64_t r2_s[kMaxSlots];
   uint32_t* perm = perm_s + threadIdx.x;
+  if (threadIdx.x < kMaxSlots) r2_s[threadIdx.x] = round2_product(k.tensor_id, threadIdx.x, k.rk);
+  __syncthreads();
   const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   Lane r0, r1;
   bicoptor_element<Lane, LX, SHORT, RELU, AUDIT>(k, k.rk, k.tensor_id, sh0[i], sh1[i],
-                                                 k.elem_base + i, perm, r0, r1, aud, i);
+                                                 k.elem_base + i, perm, r0, r1, aud, i, r2_s);
   o0[i] = r0;
   o1[i] = r1;
 }
@@ -98,8 +101,8 @@ __global__ void __launch_bounds__(kBlock)
   const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
   for (uint32_t slot = part; slot < L; slot += kSplit) {
     uint32_t w0, w1;
-    any_zero |= slot_zero_test<LX, SHORT>(k, rk, f0, nf1, perm[slot * kSplitElems], mask_stream,
-                                          (uint64_t)kPhiloxM1 * slot, w0, w1);
+    const U32x4 rz = mask_stream.block((uint64_t)kPhiloxM1 * slot, rk);
+    any_zero |= slot_zero_test<LX, SHORT>(k, f0, nf1, perm[slot * kSplitElems], rz, w0, w1);
   }
   any_zero |= __shfl_xor_sync(0xffffffffu, any_zero, 1);
   any_zero |= __shfl_xor_sync(0xffffffffu, any_zero, 2);
@@ -203,7 +206,13 @@ template <typename Lane, int LX, bool SHORT>
 __global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
     linear_relu_kernel(const LinearConsts c, const LinearIo io, uint64_t n) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  __shared__ uint64_t r2_s[kMaxSlots + 2];   // the ReLU's table, then the product's (b = 0, 1)
   uint32_t* perm = perm_s + threadIdx.x;
+  if (threadIdx.x < kMaxSlots)
+    r2_s[threadIdx.x] = round2_product(c.k.tensor_id, threadIdx.x, c.k.rk);
+  else if (threadIdx.x < kMaxSlots + 2)
+    r2_s[threadIdx.x] = round2_product(c.mul_tid, threadIdx.x - kMaxSlots, c.k.rk);
+  __syncthreads();
   const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const uint64_t elem = c.k.elem_base + i;
@@ -211,7 +220,8 @@ __global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
   Lane p0, p1;
   beaver_mul<Lane>(ElemPhilox(elem, c.mul_tid), c.k.rk, mask,
                    static_cast<const Lane*>(io.x0)[i], static_cast<const Lane*>(io.x1)[i],
-                   static_cast<const Lane*>(io.y0)[i], static_cast<const Lane*>(io.y1)[i], p0, p1);
+                   static_cast<const Lane*>(io.y0)[i], static_cast<const Lane*>(io.y1)[i], p0, p1,
+                   r2_s + kMaxSlots);
   // Alg. smltrc: P0 cut([z]_0, k); P1 2^l - cut(2^l - [z]_1, k)
   const Lane hi0 = p0 >> c.trunc;
   const Lane hi1 = ring_neg<Lane>(p1, mask) >> c.trunc;
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
   }
   Lane r0, r1;
   bicoptor_element<Lane, LX, SHORT, true, false>(c.k, c.k.rk, c.k.tensor_id, t0, t1, elem, perm,
-                                                 r0, r1, AuditPtrs{}, i);
+                                                 r0, r1, AuditPtrs{}, i, r2_s);
   static_cast<Lane*>(io.relu0)[i] = r0;
   static_cast<Lane*>(io.relu1)[i] = r1;
 }
