@@ -148,10 +148,14 @@ __global__ void __launch_bounds__(kBlock)
                       const Lane* __restrict__ x1, const Lane* __restrict__ y0,
                       const Lane* __restrict__ y1, uint64_t n, Lane* __restrict__ o0,
                       Lane* __restrict__ o1) {
+  __shared__ uint64_t r2_s[2];   // round2_product(tid, b) for the triple's blocks b = 0, 1
+  if (threadIdx.x < 2) r2_s[threadIdx.x] = round2_product(tid, threadIdx.x, rk);
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) {
     Lane p0, p1;
-    beaver_mul<Lane>(ElemPhilox(base + i, tid), rk, mask, x0[i], x1[i], y0[i], y1[i], p0, p1);
+    beaver_mul<Lane>(ElemPhilox(base + i, tid), rk, mask, x0[i], x1[i], y0[i], y1[i], p0, p1,
+                     r2_s);
     o0[i] = p0;
     o1[i] = p1;
   }

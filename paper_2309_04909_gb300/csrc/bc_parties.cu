@@ -97,13 +97,14 @@ __device__ __forceinline__ void lane_put(void* p, uint64_t i, Lane v) {
 // seed01: t and the Fisher-Yates shuffle (steps 1 and 6), into `perm`
 // (this thread's column of the shared table, stride kPB).
 __device__ __forceinline__ uint32_t seed01_shuffle(const ElemPhilox& ep, uint32_t L,
-                                                   uint32_t* perm, const RoundKeys& rk) {
+                                                   uint32_t* perm, const RoundKeys& rk,
+                                                   const uint64_t* r2) {
   for (uint32_t s = 0; s < L; ++s) perm[s * kPB] = s;
   uint32_t t = 0;
   const uint32_t nblk = (L + 3) >> 2;
   const StreamPhilox stream(ep, kPair01, kPurPerm, rk);
   for (uint32_t b = 0; b < nblk; ++b) {
-    const U32x4 wb = stream.block((uint64_t)kPhiloxM1 * b, rk);
+    const U32x4 wb = stream.block_p0((uint64_t)kPhiloxM1 * b, r2[b], rk);
     const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -123,8 +124,18 @@ __device__ __forceinline__ uint32_t seed01_shuffle(const ElemPhilox& ep, uint32_
   return t;
 }
 
-__device__ __forceinline__ uint32_t seed01_t(const ElemPhilox& ep, const RoundKeys& rk) {
-  return ep.block_at(kPair01, kPurPerm, 0, rk).x & 1u;
+__device__ __forceinline__ uint32_t seed01_t(const ElemPhilox& ep, const RoundKeys& rk,
+                                             const uint64_t* r2) {
+  return ep.block_tab(kPair01, kPurPerm, 0, r2, rk).x & 1u;
+}
+
+// The CTA's table of round2_product(tensor_id, b), b < kMaxSlots (one
+// widening product less per Philox block of every element); call from all
+// threads before any returns.
+__device__ __forceinline__ void fill_round2(uint64_t* r2, uint32_t tensor_id,
+                                            const RoundKeys& rk) {
+  if (threadIdx.x < kMaxSlots) r2[threadIdx.x] = round2_product(tensor_id, threadIdx.x, rk);
+  __syncthreads();
 }
 
 // Pack the group's L slots after the slot loop.  `vals` holds the warp's
@@ -183,6 +194,8 @@ template <typename Lane, bool RELU>
 __global__ void __launch_bounds__(kPB)
     parties_local_kernel(const PartyArgs a) {
   __shared__ uint32_t perm_s[kMaxSlots * kPB];
+  __shared__ uint64_t r2_s[kMaxSlots];
+  fill_round2(r2_s, a.k.tensor_id, a.k.rk);
   const uint32_t party = blockIdx.y;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(kPB)
   const uint64_t elem = k.elem_base + (valid ? i : 0);
   const ElemPhilox ep(elem, k.tensor_id);
   uint32_t* perm = perm_s + threadIdx.x;
-  const uint32_t t = seed01_shuffle(ep, L, perm, k.rk);
+  const uint32_t t = seed01_shuffle(ep, L, perm, k.rk, r2_s);
   const Lane s = valid ? lane_at<Lane>(a.sh[party], i) : (Lane)0;
   // steps 1-2 and the P1 pre-negation: P0 keeps [x]_0 (flipped), P1 keeps
   // 2^l - [x]_1 of its flipped share
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(kPB)
       const uint32_t v = (0u - (y & k.mx) - ((y >> 1) & next_mask)) & k.mx;
       m = v + k.p_minus_2lx;
     }
-    const U32x4 rz = mask_stream.block(mb, k.rk);                             // step 7
+    const U32x4 rz = mask_stream.block_p0(mb, r2_s[slot], k.rk);              // step 7
     const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
     uint32_t w = mont_mul(m, rho, k.mp);
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(kPB)
   pack_group(perm_s + warp * 32u, L, B, lane, a.w[party] + g * L * B + lane);
   if (RELU && valid) {
     // opening of d = x - a: P0 draws a0 from seed02, P1 draws a1 from seed12
-    const U32x4 q = ep.block_at(party == 0 ? kPair02 : kPair12, kPurReluTriple, 0, k.rk);
+    const U32x4 q = ep.block_tab(party == 0 ? kPair02 : kPair12, kPurReluTriple, 0, r2_s, k.rk);
     const Lane ai = block_elem<Lane>(q, 0) & mask;
     lane_put<Lane>(a.open[party], i, (Lane)(s - ai) & mask);
   }
@@ -245,6 +258,7 @@ __global__ void __launch_bounds__(kPB)
     helper_kernel(const PartyArgs a) {
   extern __shared__ __align__(128) uint32_t msg_s[];   // [2][kWarps * L * B]
   __shared__ __align__(8) uint64_t bar_s;
+  __shared__ uint64_t r2_s[2];
   const ReluConsts& k = a.k;
   const uint32_t L = k.lx + 1, B = k.lx + 1;
   const uint32_t group_words = L * B;
@@ -254,6 +268,7 @@ __global__ void __launch_bounds__(kPB)
     mbar_init(bar, 1);
     mbar_fence_init();
   }
+  if (threadIdx.x < 2) r2_s[threadIdx.x] = round2_product(k.tensor_id, threadIdx.x, k.rk);
   __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t bytes = cta_words * 4u;            // 32 L B: a multiple of 16
@@ -276,15 +291,15 @@ __global__ void __launch_bounds__(kPB)
   Lane d0 = 0, a0 = 0, b0 = 0, c0 = 0, a1 = 0, b1 = 0;
   if (valid) {
     if (!RELU) {
-      d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
+      d0 = block_elem<Lane>(ep.block_tab(kPair02, kPurReply, 0, r2_s, k.rk), 0) & mask;
     } else {
       // P2 knows seed02 and seed12: the whole triple
-      const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
-      const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
+      const U32x4 q0 = ep.block_tab(kPair02, kPurReluTriple, 0, r2_s, k.rk);
+      const U32x4 q1 = ep.block_tab(kPair12, kPurReluTriple, 0, r2_s, k.rk);
       if (sizeof(Lane) == 4) {
         a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
       } else {
-        const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
+        const U32x4 q2 = ep.block_tab(kPair02, kPurReluTriple, 1, r2_s, k.rk);
         a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1);
         c0 = block_elem<Lane>(q2, 0);
       }
@@ -330,17 +345,20 @@ __global__ void __launch_bounds__(kPB)
 template <typename Lane, bool RELU>
 __global__ void __launch_bounds__(kPB)
     parties_finish_kernel(const PartyArgs a) {
+  __shared__ uint64_t r2_s[2];
+  if (threadIdx.x < 2) r2_s[threadIdx.x] = round2_product(a.k.tensor_id, threadIdx.x, a.k.rk);
+  __syncthreads();
   const uint32_t party = blockIdx.y;
   const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
   if (i >= a.n) return;
   const ReluConsts& k = a.k;
   const Lane mask = (Lane)k.ring_mask;
   const ElemPhilox ep(k.elem_base + i, k.tensor_id);
-  const Lane t = (Lane)seed01_t(ep, k.rk);
+  const Lane t = (Lane)seed01_t(ep, k.rk, r2_s);
   if (!RELU) {
     // step 11: P0 has d0 from seed02, P1 the reply [DReLU']_1
     if (party == 0) {
-      const Lane d0 = block_elem<Lane>(ep.block_at(kPair02, kPurReply, 0, k.rk), 0) & mask;
+      const Lane d0 = block_elem<Lane>(ep.block_tab(kPair02, kPurReply, 0, r2_s, k.rk), 0) & mask;
       lane_put<Lane>(a.out[0], i, t ? (Lane)((Lane)1 - d0) & mask : d0);
     } else {
       const Lane d1 = lane_at<Lane>(a.reply, i);
@@ -353,18 +371,18 @@ __global__ void __launch_bounds__(kPB)
   const Lane s = lane_at<Lane>(a.sh[party], i);
   Lane xd;
   if (party == 0) {
-    const U32x4 q0 = ep.block_at(kPair02, kPurReluTriple, 0, k.rk);
+    const U32x4 q0 = ep.block_tab(kPair02, kPurReluTriple, 0, r2_s, k.rk);
     Lane a0, b0, c0;
     if (sizeof(Lane) == 4) {
       a0 = (Lane)q0.x; b0 = (Lane)q0.y; c0 = (Lane)q0.z;
     } else {
-      const U32x4 q2 = ep.block_at(kPair02, kPurReluTriple, 1, k.rk);
+      const U32x4 q2 = ep.block_tab(kPair02, kPurReluTriple, 1, r2_s, k.rk);
       a0 = block_elem<Lane>(q0, 0); b0 = block_elem<Lane>(q0, 1); c0 = block_elem<Lane>(q2, 0);
     }
     a0 &= mask; b0 &= mask; c0 &= mask;
     xd = (Lane)(d * (e + b0) + e * a0 + c0) & mask;
   } else {
-    const U32x4 q1 = ep.block_at(kPair12, kPurReluTriple, 0, k.rk);
+    const U32x4 q1 = ep.block_tab(kPair12, kPurReluTriple, 0, r2_s, k.rk);
     const Lane a1 = block_elem<Lane>(q1, 0) & mask, b1 = block_elem<Lane>(q1, 1) & mask;
     xd = (Lane)(d * b1 + e * a1 + lane_at<Lane>(a.pre_c1, i)) & mask;
   }

@@ -275,14 +275,15 @@ cudaError_t launch_linear_t(const LinearConsts& c, const LinearIo& io, uint64_t 
 
 template <typename Lane>
 __device__ __forceinline__ void draw3(const ElemPhilox& ep, uint32_t pair, uint32_t purpose,
-                                      Lane mask, const RoundKeys& rk, Lane out[3]) {
-  const U32x4 q0 = ep.block_at(pair, purpose, 0, rk);
+                                      Lane mask, const RoundKeys& rk, const uint64_t* r2,
+                                      Lane out[3]) {
+  const U32x4 q0 = ep.block_tab(pair, purpose, 0, r2, rk);
   if (sizeof(Lane) == 4) {
     out[0] = (Lane)q0.x & mask;
     out[1] = (Lane)q0.y & mask;
     out[2] = (Lane)q0.z & mask;
   } else {
-    const U32x4 q1 = ep.block_at(pair, purpose, 1, rk);
+    const U32x4 q1 = ep.block_tab(pair, purpose, 1, r2, rk);
     out[0] = block_elem<Lane>(q0, 0) & mask;
     out[1] = block_elem<Lane>(q0, 1) & mask;
     out[2] = block_elem<Lane>(q1, 0) & mask;
@@ -305,7 +306,10 @@ __global__ void __launch_bounds__(kBlock)
                const Lane* __restrict__ x2, uint64_t n, Lane* __restrict__ y0,
                Lane* __restrict__ y1, Lane* __restrict__ y2) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
+  __shared__ uint64_t r2_s[kMaxSlots];
   uint32_t* perm = perm_s + threadIdx.x;
+  if (threadIdx.x < kMaxSlots) r2_s[threadIdx.x] = round2_product(k.tensor_id, threadIdx.x, k.rk);
+  __syncthreads();
   const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const Lane mask = (Lane)k.ring_mask;
@@ -315,18 +319,18 @@ __global__ void __launch_bounds__(kBlock)
   const AuditPtrs none{};
   bicoptor_element<Lane, LX, SHORT, false, false, true>(k, k.rk, k.tensor_id,
                                                         (Lane)(X[0] + X[1]) & mask, X[2], elem,
-                                                        perm, dp, t, none, i);
+                                                        perm, dp, t, none, i, r2_s);
   const ElemPhilox ep(elem, k.tensor_id);
   Lane al[3], S[3], T[3], g[3], ST[3], Xs[3], Y[3];
-  draw3<Lane>(ep, kPair012, kPurRssT, mask, k.rk, al);
+  draw3<Lane>(ep, kPair012, kPurRssT, mask, k.rk, r2_s, al);
   T[0] = (Lane)(al[0] - al[2]) & mask;
   T[1] = (Lane)(al[1] - al[0] + t) & mask;
   T[2] = (Lane)(al[2] - al[1]) & mask;
-  const Lane sbit = (Lane)(ep.block_at(kPair2, kPurRssS, 0, k.rk).x & 1u);
-  S[1] = block_elem<Lane>(ep.block_at(kPair012, kPurRssS, 0, k.rk), 0) & mask;
-  S[2] = block_elem<Lane>(ep.block_at(kPair12, kPurRssS, 0, k.rk), 0) & mask;
+  const Lane sbit = (Lane)(ep.block_tab(kPair2, kPurRssS, 0, r2_s, k.rk).x & 1u);
+  S[1] = block_elem<Lane>(ep.block_tab(kPair012, kPurRssS, 0, r2_s, k.rk), 0) & mask;
+  S[2] = block_elem<Lane>(ep.block_tab(kPair12, kPurRssS, 0, r2_s, k.rk), 0) & mask;
   S[0] = (Lane)(sbit - S[1] - S[2]) & mask;                          // P2 -> P0
-  draw3<Lane>(ep, kPair012, kPurRssZ, mask, k.rk, g);
+  draw3<Lane>(ep, kPair012, kPurRssZ, mask, k.rk, r2_s, g);
   rss_mul3<Lane>(S, T, g, mask, ST);
 #pragma unroll
   for (int j = 0; j < 3; ++j) Xs[j] = (Lane)(S[j] + T[j] - 2 * ST[j]) & mask;   // [s xor t]
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kBlock)
   for (int j = 0; j < 3; ++j) Y[j] = (Lane)(Xs[j] - 2 * dd * Xs[j] + (j == 0 ? dd : 0)) & mask;
   if (RELU) {
     Lane gr[3], Z[3];
-    draw3<Lane>(ep, kPair012, kPurRssZr, mask, k.rk, gr);
+    draw3<Lane>(ep, kPair012, kPurRssZr, mask, k.rk, r2_s, gr);
     rss_mul3<Lane>(X, Y, gr, mask, Z);
     y0[i] = Z[0];
     y1[i] = Z[1];
