@@ -60,6 +60,24 @@ class Params:
     def slots(self) -> int:
         return self.lx + 1
 
+    @classmethod
+    def from_key_bits(cls, ring_bits: int, int_bits: int, frac_bits: int, kept_frac_bits: int,
+                      p: int = 0) -> "Params":
+        """The key bits of Sec. 6.1: the DReLU of a fixed-point value with
+        int_bits integer and frac_bits fractional bits looks only at the integer
+        bits and the top kept_frac_bits fractional bits.  So lx = int_bits +
+        kept_frac_bits, and the lowest key bit is c = frac_bits - kept_frac_bits
+        (l = 64 with 5 + 26 bits and 2 fractional bits kept gives lx = 7, c = 24:
+        the last 24 bits ignored).  The windows of step 3 then need c + 2 lx <= l."""
+        if not (0 <= kept_frac_bits <= frac_bits and int_bits >= 0):
+            raise ValueError("need 0 <= kept_frac_bits <= frac_bits and int_bits >= 0")
+        lx, c = int_bits + kept_frac_bits, frac_bits - kept_frac_bits
+        if not 1 <= lx <= 31:
+            raise ValueError(f"key bits lx = {lx} outside 1..31")
+        if c + 2 * lx > ring_bits:
+            raise ValueError(f"c + 2 lx = {c + 2 * lx} exceeds the ring's {ring_bits} bits")
+        return cls(ring_bits, lx, c, p)
+
 
 _PRM_STRUCTS: Dict["Params", DreluParams] = {}
 # the current stream's raw cudaStream_t of a device, as an int (torch's own accessor)

@@ -55,3 +55,19 @@ def test_costmodel_counts():
     w, lo, hi = C.mul_counts_split(24, 64, relu=True, product=True)
     assert (w, lo, hi) == (921, 72, 74)
     assert 2 * w + lo + 2 * hi == C.linear_relu_mul_ops_per_element(24, 64)
+
+
+def test_key_bit_params():
+    """Sec. 6.1's key bits: 5 + 26 bits with 2 fractional bits kept is lx = 7
+    with the last 24 bits ignored (the paper's example); 7 + 0 keeps no
+    fractional bit; windows that do not fit the ring are refused."""
+    import pytest
+    from paper_2309_04909_gb300 import Params
+    p = Params.from_key_bits(64, 5, 26, 2)
+    assert (p.ring_bits, p.lx, p.key_off) == (64, 7, 24)
+    p = Params.from_key_bits(64, 7, 26, 0)
+    assert (p.lx, p.key_off) == (7, 26)
+    assert Params.from_key_bits(32, 9, 14, 0) == Params(32, 9, 14)
+    for bad in ((64, 5, 26, 27), (64, 20, 26, 12), (32, 9, 14, 1), (64, 0, 0, 0)):
+        with pytest.raises(ValueError):
+            Params.from_key_bits(*bad)
