@@ -227,6 +227,13 @@ def max_threads() -> int:
     return int(lib().orc_max_threads())
 
 
+def set_threads(n: int) -> None:
+    """Threads of the elementwise loops (sharing, truncations, modulo switch,
+    products, reconstruct); 0 = all cores (OpenMP's default), 1 = one core.
+    drelu, relu and rss_drelu take their own `threads` argument."""
+    lib().orc_set_threads(int(n))
+
+
 def drelu_core_many(P: _Params, s0, s1, t, fy, r, z):
     """Vectorised drelu_core: fy, r, z are (n, lx+1) uint32 arrays (fy[:, 0]
     unused).  Returns DReLU' per row."""

@@ -37,6 +37,23 @@
 
 typedef unsigned __int128 u128;
 
+/* Element-parallel loops.  Every elementwise loop of this file runs its
+ * iterations independently (each element reads only its own inputs and its
+ * own Philox counters), so OpenMP splits them over the host cores without
+ * changing any value.  orc_set_threads(0) = OpenMP's default (all cores);
+ * orc_set_threads(1) runs everything on one core.  Small loops stay serial.
+ * orc_drelu, orc_relu and orc_rss_drelu take their thread count as an
+ * argument instead. */
+static int g_threads = 0;
+void orc_set_threads(int t) { g_threads = t > 0 ? t : 0; }
+#ifdef _OPENMP
+static int orc_threads(void) { return g_threads > 0 ? g_threads : omp_get_max_threads(); }
+#define ORC_PARALLEL_FOR \
+    _Pragma("omp parallel for schedule(static) num_threads(orc_threads()) if(n >= 4096)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
 /* ------------------------------------------------------------------------- */
 /* Ring Z_{2^l}                                                              */
 /* ------------------------------------------------------------------------- */
@@ -169,6 +186,7 @@ uint32_t orc_prime_above(int lx)
 
 void orc_encode(const double *x, size_t n, int f, int ell, uint64_t *out)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         double scaled = nearbyint(ldexp(x[i], f));
         int64_t v = (int64_t)scaled;
@@ -179,6 +197,7 @@ void orc_encode(const double *x, size_t n, int f, int ell, uint64_t *out)
 /* Signed value of a ring element: x in [0, 2^(l-1)) is positive. */
 void orc_to_signed(const uint64_t *v, size_t n, int ell, int64_t *out)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         uint64_t a = rmod(v[i], ell);
         if (ell < 64 && (a >> (ell - 1)))
@@ -203,6 +222,7 @@ static uint64_t elem_index(const uint64_t *idx, size_t i) { return idx ? idx[i] 
 void orc_share(int ell, const uint64_t *x, const uint64_t *idx, size_t n, uint64_t seed,
                uint32_t tid, uint64_t *s0, uint64_t *s1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         uint64_t R = stream_ring(seed, PAIR_DEALER, PUR_SHARE, tid, elem_index(idx, i), 0, ell);
         orc_share_with_r(ell, x[i], R, &s0[i], &s1[i]);
@@ -211,6 +231,7 @@ void orc_share(int ell, const uint64_t *x, const uint64_t *idx, size_t n, uint64
 
 void orc_reconstruct(int ell, const uint64_t *s0, const uint64_t *s1, size_t n, uint64_t *x)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) x[i] = rmod(s0[i] + s1[i], ell);
 }
 
@@ -231,6 +252,7 @@ static uint64_t smltrc_p1(uint64_t s1, int ell, int k)
 void orc_trunc_prob(int ell, int k, const uint64_t *s0, const uint64_t *s1, size_t n,
                     uint64_t *o0, uint64_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         o0[i] = smltrc_p0(s0[i], ell, k);
         o1[i] = smltrc_p1(s1[i], ell, k);
@@ -257,6 +279,7 @@ static uint64_t newtrc_p1(uint64_t s1, int ell, int k1, int k2)
 void orc_trunc_det(int ell, int k1, int k2, const uint64_t *s0, const uint64_t *s1, size_t n,
                    uint64_t *o0, uint64_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         o0[i] = newtrc_p0(s0[i], ell, k1, k2);
         o1[i] = newtrc_p1(s1[i], ell, k1, k2);
@@ -286,6 +309,7 @@ static uint32_t modswitch_p1(uint64_t b, int lp, uint32_t p)
 void orc_mod_switch(int lp, uint32_t p, const uint64_t *s0, const uint64_t *s1, size_t n,
                     uint32_t *o0, uint32_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         o0[i] = modswitch_p0(rmod(s0[i], lp), lp, p);
         o1[i] = modswitch_p1(rmod(s1[i], lp), lp, p);
@@ -331,6 +355,7 @@ void orc_trunc_aby3(int ell, int k, const uint64_t *s0, const uint64_t *s1, cons
                     size_t n, uint64_t seed, uint32_t tid, uint64_t fixed_r, uint64_t *o0,
                     uint64_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         uint64_t elem = elem_index(idx, i);
         uint64_t r0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 0, ell);
@@ -367,6 +392,7 @@ void orc_mul_beaver(int ell, const uint64_t *x0, const uint64_t *x1, const uint6
                     const uint64_t *y1, const uint64_t *idx, size_t n, uint64_t seed,
                     uint32_t tid, uint64_t *o0, uint64_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         triple_t T = draw_triple(seed, PUR_MUL_TRIPLE, tid, elem_index(idx, i), ell);
         /* openings: each party sends its share of x - a and of y - b */
@@ -385,6 +411,7 @@ void orc_trunc_then_mul(int ell, int kx, int ky, const uint64_t *x0, const uint6
                         const uint64_t *y0, const uint64_t *y1, const uint64_t *idx, size_t n,
                         uint64_t seed, uint32_t tid, uint64_t *o0, uint64_t *o1)
 {
+    ORC_PARALLEL_FOR
     for (size_t i = 0; i < n; i++) {
         uint64_t tx0 = smltrc_p0(x0[i], ell, kx), tx1 = smltrc_p1(x1[i], ell, kx);
         uint64_t ty0 = smltrc_p0(y0[i], ell, ky), ty1 = smltrc_p1(y1[i], ell, ky);
@@ -720,9 +747,11 @@ int orc_drelu_core_many(const orc_params *P, const uint64_t *s0, const uint64_t 
 {
     if (check_params(P)) return -1;
     const int L = P->lx + 1;
-    uint32_t msg0[MAXL], msg1[MAXL];
-    for (size_t i = 0; i < n; i++)
+    ORC_PARALLEL_FOR
+    for (size_t i = 0; i < n; i++) {
+        uint32_t msg0[MAXL], msg1[MAXL];
         dprime[i] = (uint8_t)orc_drelu_core(P, s0[i], s1[i], t[i], fy + i * L, r + i * L,
                                             z + i * L, msg0, msg1);
+    }
     return 0;
 }
