@@ -1,11 +1,21 @@
-"""Parity at the full sizes of the batched workloads, in the launch shapes the
-benchmark times: the VGG-16 32x32 ReLU set of 128 images (1,664 tensors,
-35,389,440 elements, l = 64) and the ResNet-18 224x224 set of 32 images in
-both rings (1,088 tensors, 147,718,144 elements; l = 64 with (lx, c) = (24, 0)
-and l = 32 with (14, 4)).  Sampled elements of many tensors are recomputed by
-the oracle one by one; every element is checked against a property that
-holds at any size (the reconstructed ReLU is x or 0, and max(x, 0) outside
-the predicted exception set)."""
+"""Parity at the full sizes of the workloads, element by element, in the launch
+shapes the benchmark times.
+
+  1. DReLU (and ReLU) of 65,536 reals U[-1000, 1000], f = 12, in Z_{2^32} with
+     (lx, c) = (9, 14), seed 0.
+  2. The fused step of a linear layer at l = 64, f = 16: Beaver product of two
+     share tensors of 2^22 Gaussian (sigma = 4) reals, Alg. smltrc and
+     Alg. newtrc by 16 bits, ReLU (lx = 24) of the Alg. smltrc output; seed 1.
+  3. The VGG-16 32x32 ReLU set of 128 images (1,664 tensors, 35,389,440
+     elements, l = 64), both batched schedules; seed 2.
+  4. The ResNet-18 224x224 ReLU set of 32 images in both rings (1,088 tensors,
+     147,718,144 elements; l = 64 with (lx, c) = (24, 0), l = 32 with (14, 4)),
+     one launch per parameter group; seed 3.
+
+Every share the dealer kernel writes and every output share is compared with
+the oracle, which recomputes them independently on all host cores.  The
+reconstructed outputs are also checked against the plaintext: ReLU(x) is x or
+0, and max(x, 0) outside the predicted exception set."""
 import numpy as np
 import pytest
 import torch
@@ -13,30 +23,34 @@ import torch
 import oracle as O
 from paper_2309_04909_gb300 import Context, Params, workloads as W
 from paper_2309_04909_gb300.batch import ReluBatch
-from tests._util import cuda_ok, masked, to_np
+from tests._util import cuda_ok, encode_np, masked, to_np
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
 
-SEED = 0x5EED_0000_0005
+
+def _threads():
+    return O.max_threads()
 
 
-def _check_sampled(ring, prm, allx, s0, s1, o0, o1, share_tid, spans, rng, tensors=40,
-                   per=64):
-    """spans: (tensor_id, offset, size) per tensor; checks `per` sampled
-    elements of `tensors` sampled tensors against the oracle."""
+def _u64(t):
+    return to_np(t).astype(np.uint64, copy=False)
+
+
+def _oracle_shares(ring, x, seed, tid):
+    O.set_threads(0)
+    return O.share(ring, masked(x, ring), seed, tid)
+
+
+def _oracle_relu_spans(ring, prm, es0, es1, seed, spans):
+    """The oracle's ReLU of every tensor (tensor id, offset, size) of a batch."""
     P = O.params(ring, prm.lx, prm.key_off)
-    s0n, s1n, o0n, o1n = to_np(s0), to_np(s1), to_np(o0), to_np(o1)
-    for k in rng.choice(len(spans), size=min(tensors, len(spans)), replace=False):
-        tid, off, size = spans[k]
-        j = np.sort(rng.choice(size, size=min(per, size), replace=False)).astype(np.uint64)
-        g = j + np.uint64(off)
-        es0, es1 = O.share(ring, masked(allx[g.astype(np.int64)], ring), SEED, share_tid, idx=g)
-        assert np.array_equal(s0n[g.astype(np.int64)].astype(np.uint64), es0)
-        assert np.array_equal(s1n[g.astype(np.int64)].astype(np.uint64), es1)
-        e0, e1 = O.relu(P, es0, es1, SEED, tid, idx=j, threads=8)
-        assert np.array_equal(o0n[g.astype(np.int64)].astype(np.uint64), e0), tid
-        assert np.array_equal(o1n[g.astype(np.int64)].astype(np.uint64), e1), tid
+    e0, e1 = np.empty_like(es0), np.empty_like(es1)
+    for tid, off, size in spans:
+        r0, r1 = O.relu(P, es0[off:off + size], es1[off:off + size], seed, tid,
+                        threads=_threads())
+        e0[off:off + size], e1[off:off + size] = r0, r1
+    return e0, e1
 
 
 def _check_property(ctx, ring, x_dev, o0, o1, min_exact):
@@ -48,63 +62,146 @@ def _check_property(ctx, ring, x_dev, o0, o1, min_exact):
     assert exact >= min_exact, exact
 
 
-@pytest.mark.parametrize("schedule", [1, 0])
-def test_vgg16_batch128_full_size(schedule):
-    ctx = Context(SEED)
-    dev = torch.device("cuda")
+def test_config1_uniform_l32_full():
+    n, ring, lx, c, seed = 65536, 32, 9, 14, 0
+    xi = encode_np(W.uniform_reals(n, -1000.0, 1000.0, seed=0), 12)
+    assert np.abs(xi).max() < 1 << 22
+    ctx = Context(seed)
+    s0, s1 = ctx.share(ring, torch.from_numpy(xi).cuda(), tensor_id=100)
+    prm, P = Params(ring, lx, c), O.params(ring, lx, c)
+    d0, d1 = ctx.drelu(prm, s0, s1, tensor_id=101)
+    r0, r1 = ctx.relu(prm, s0, s1, tensor_id=102)
+    es0, es1 = _oracle_shares(ring, xi, seed, 100)
+    assert np.array_equal(_u64(s0), es0) and np.array_equal(_u64(s1), es1)
+    ed0, ed1 = O.drelu(P, es0, es1, seed, 101, threads=_threads())
+    er0, er1 = O.relu(P, es0, es1, seed, 102, threads=_threads())
+    assert np.array_equal(_u64(d0), ed0) and np.array_equal(_u64(d1), ed1)
+    assert np.array_equal(_u64(r0), er0) and np.array_equal(_u64(r1), er1)
+    # every sign mismatch lies in the predicted set: |x| < 2^c or the band of
+    # half-width 2^c around xi* 2^c (xi* + ceil(xi*/2) in {2^lx - 1, 2^lx})
+    drelu = (ed0 + ed1) & np.uint64(0xFFFFFFFF)
+    bad = np.nonzero(drelu != (xi >= 0))[0]
+    mags = np.abs(xi[bad])
+    xs = [v for v in range(1, 1 << lx) if v + (v + 1) // 2 in ((1 << lx) - 1, 1 << lx)]
+    pred = (mags < (1 << c)) | np.any([np.abs(mags - e * (1 << c)) < (1 << c) for e in xs],
+                                      axis=0)
+    assert pred.all() and bad.size < 0.01 * n
+    _check_property(ctx, ring, torch.from_numpy(xi).cuda(), r0, r1, 0.99)
+    ctx.close()
+
+
+def test_config2_fused_step_l64_2p22_full():
+    n, f, seed = 1 << 22, 16, 1
+    xi = encode_np(W.gaussian_reals(n, 4.0, seed=1, stream=0), f)
+    yi = encode_np(W.gaussian_reals(n, 4.0, seed=1, stream=1), f)
+    ctx = Context(seed)
+    x0, x1 = ctx.share(64, torch.from_numpy(xi).cuda(), 1)
+    y0, y1 = ctx.share(64, torch.from_numpy(yi).cuda(), 2)
+    prm = Params(64, 24, 0)
+    w = ctx.linear_relu(64, f, prm, x0, x1, y0, y1, tensor_id=3)
+    ex0, ex1 = _oracle_shares(64, xi, seed, 1)
+    ey0, ey1 = _oracle_shares(64, yi, seed, 2)
+    for g, e in ((x0, ex0), (x1, ex1), (y0, ey0), (y1, ey1)):
+        assert np.array_equal(_u64(g), e)
+    p0, p1 = O.mul_beaver(64, ex0, ex1, ey0, ey1, seed, 3)
+    t0, t1 = O.trunc_prob(64, f, p0, p1)
+    d0, d1 = O.trunc_det(64, f, 0, p0, p1)
+    r0, r1 = O.relu(O.params(64, 24, 0), t0, t1, seed, 4, threads=_threads())
+    for name, want in (("prod0", p0), ("prod1", p1), ("trc0", t0), ("trc1", t1), ("det0", d0),
+                       ("det1", d1), ("relu0", r0), ("relu1", r1)):
+        assert np.array_equal(_u64(w[name]), want), name
+    # the benchmark's call writes only the ReLU and the deterministic truncation
+    only = ctx.linear_relu_buffers(64, f, n, names=("det0", "det1", "relu0", "relu1"))
+    ctx.linear_relu(64, f, prm, x0, x1, y0, y1, tensor_id=3, work=only)
+    for nm, t in only.items():
+        assert torch.equal(t, w[nm]), nm
+    # plaintext: Alg. newtrc gives exactly ((x >> 16) + carry) mod 2^48 with
+    # carry = [(x mod 2^16) + (R mod 2^16) >= 2^16], R = -[x]_1 (Thm. newtrc2);
+    # Alg. smltrc is within one of floor(x / 2^16) unless e1 occurs, whose
+    # probability is sum |xy| / 2^64 ~ 0.01 here
+    x = (xi * yi).view(np.uint64)
+    R = np.uint64(0) - p1
+    lo = np.uint64(0xFFFF)
+    carry = ((x & lo) + (R & lo)) >> np.uint64(16)
+    want_det = ((x >> np.uint64(16)) + carry) & np.uint64((1 << 48) - 1)
+    assert np.array_equal(O.reconstruct(48, d0, d1), want_det)
+    trc = O.to_signed(O.reconstruct(64, t0, t1), 64)
+    assert (np.abs(trc - (xi * yi >> f)) > 1).sum() <= 2
+    rel = O.to_signed(O.reconstruct(64, r0, r1), 64)
+    assert ((rel == trc) | (rel == 0)).all()
+    assert (rel == np.maximum(trc, 0)).mean() > 0.9999
+    ctx.close()
+
+
+def _batch_items(ctx, prm, s0, s1, o0, o1, sizes, tid0):
+    items, spans, off = [], [], 0
+    for t, sz in enumerate(sizes):
+        items.append((prm, s0[off:off + sz], s1[off:off + sz], o0[off:off + sz],
+                      o1[off:off + sz], tid0 + t))
+        spans.append((tid0 + t, off, sz))
+        off += sz
+    return items, spans
+
+
+def test_config3_vgg16_batch128_full():
+    seed = 2
+    ctx = Context(seed)
     ts = W.vgg16_batch(128, seed=2)
-    allx = np.concatenate([np.rint(np.ldexp(r, 16)).astype(np.int64) for r in ts.reals])
+    allx = np.concatenate([encode_np(r, 16) for r in ts.reals])
+    ts.reals = None
     assert allx.size == 35_389_440 and len(ts.sizes) == 1664
-    xd = torch.from_numpy(allx).to(dev)
+    xd = torch.from_numpy(allx).cuda()
     s0, s1 = ctx.share(64, xd, tensor_id=11)
     o0, o1 = torch.empty_like(s0), torch.empty_like(s1)
     prm = Params(64, 24, 0)
-    items, spans, off = [], [], 0
-    for t, sz in enumerate(ts.sizes):
-        items.append((prm, s0[off:off + sz], s1[off:off + sz], o0[off:off + sz],
-                      o1[off:off + sz], 20000 + t))
-        spans.append((20000 + t, off, sz))
-        off += sz
-    b = ReluBatch(ctx, items, schedule=schedule)
-    b.run()
-    torch.cuda.synchronize()
-    assert ctx.batch_status() == 0
-    _check_sampled(64, prm, allx, s0, s1, o0, o1, 11, spans, np.random.default_rng(schedule))
+    items, spans = _batch_items(ctx, prm, s0, s1, o0, o1, ts.sizes, 20000)
+    es0, es1 = _oracle_shares(64, allx, seed, 11)
+    assert np.array_equal(_u64(s0), es0) and np.array_equal(_u64(s1), es1)
+    e0, e1 = _oracle_relu_spans(64, prm, es0, es1, seed, spans)
+    for schedule in (1, 0):
+        o0.zero_()
+        o1.zero_()
+        ReluBatch(ctx, items, schedule=schedule).run()
+        torch.cuda.synchronize()
+        assert ctx.batch_status() == 0
+        assert np.array_equal(_u64(o0), e0), schedule
+        assert np.array_equal(_u64(o1), e1), schedule
     _check_property(ctx, 64, xd, o0, o1, 0.9999)
     ctx.close()
 
 
-def test_resnet18_batch32_mixed_rings_full_size():
-    ctx = Context(SEED)
-    dev = torch.device("cuda")
+def test_config4_resnet18_batch32_mixed_rings_full():
+    seed = 3
+    ctx = Context(seed)
     ts = W.resnet18_mixed_batch(32, seed=3)
     assert ts.total == 147_718_144 and len(ts.sizes) == 1088
     items, parts = [], []
     for ring, frac, prm in ((64, 16, Params(64, 24, 0)), (32, 12, Params(32, 14, 4))):
         idx = [i for i in range(len(ts.sizes)) if ts.ring_bits[i] == ring]
-        allx = np.concatenate([np.rint(np.ldexp(ts.reals[i], frac)).astype(np.int64)
-                               for i in idx])
-        xd = torch.from_numpy(allx).to(dev)
+        allx = np.concatenate([encode_np(ts.reals[i], frac) for i in idx])
+        for i in idx:
+            ts.reals[i] = None
+        xd = torch.from_numpy(allx).cuda()
         s0, s1 = ctx.share(ring, xd, tensor_id=30 + ring)
         dt = torch.int64 if ring > 32 else torch.int32
-        o0 = torch.empty(allx.size, dtype=dt, device=dev)
+        o0 = torch.empty(allx.size, dtype=dt, device="cuda")
         o1 = torch.empty_like(o0)
-        spans, off = [], 0
-        for i in idx:
-            sz = ts.sizes[i]
-            items.append((prm, s0[off:off + sz], s1[off:off + sz], o0[off:off + sz],
-                          o1[off:off + sz], 40000 + i))
-            spans.append((40000 + i, off, sz))
-            off += sz
+        its, spans = _batch_items(ctx, prm, s0, s1, o0, o1, [ts.sizes[i] for i in idx], 0)
+        # tensor ids as the benchmark numbers them: 40000 + index in the set
+        its = [it[:5] + (40000 + i,) for it, i in zip(its, idx)]
+        spans = [(40000 + i, off, sz) for (_, off, sz), i in zip(spans, idx)]
+        items += its
         parts.append((ring, prm, allx, xd, s0, s1, o0, o1, spans))
-    ts.reals = None
-    b = ReluBatch(ctx, items, schedule=1)   # one launch per parameter group
-    b.run()
+    ReluBatch(ctx, items, schedule=1).run()     # one launch per parameter group
     torch.cuda.synchronize()
     assert ctx.batch_status() == 0
-    rng = np.random.default_rng(7)
     for ring, prm, allx, xd, s0, s1, o0, o1, spans in parts:
-        _check_sampled(ring, prm, allx, s0, s1, o0, o1, 30 + ring, spans, rng)
+        es0, es1 = _oracle_shares(ring, allx, seed, 30 + ring)
+        assert np.array_equal(_u64(s0), es0) and np.array_equal(_u64(s1), es1), ring
+        e0, e1 = _oracle_relu_spans(ring, prm, es0, es1, seed, spans)
+        assert np.array_equal(_u64(o0), e0), ring
+        assert np.array_equal(_u64(o1), e1), ring
+        del es0, es1, e0, e1
         # l = 32, c = 4: |x| < 2^c may take either sign (reading 14), about 0.2 % here
         _check_property(ctx, ring, xd, o0, o1, 0.9999 if ring == 64 else 0.99)
     ctx.close()

@@ -1,8 +1,9 @@
 """Parity of the CUDA path (through the C-ABI) with the CPU oracle.
 
 Integer protocol: every comparison is bit-exact.  Sizes span many CTAs and
-end on a ragged tail; the large cases use the benchmark's launch shape and
-compare sampled elements the oracle computes one by one.
+end on a ragged tail.  The full-size workloads are compared element by element
+in test_gpu_configs.py, the exhaustive and boundary inputs in
+test_gpu_edge_cases.py.
 """
 import numpy as np
 import pytest
@@ -385,44 +386,6 @@ def test_batch_config_out_of_range_rejected(ctx):
                {"slot_unroll": 4}, {"slot_unroll": -1}):
         with pytest.raises(BicoptorError):
             ctx.relu_batch_plan(items, **kw)
-
-
-def test_full_size_step_l64_2p22_sampled(ctx):
-    """N = 2^22 at l = 64, the benchmark's launch configuration; 4,096 sampled
-    elements recomputed by the oracle."""
-    n = 1 << 22
-    X = W.gaussian_reals(n, 4.0, seed=1, stream=0)
-    Y = W.gaussian_reals(n, 4.0, seed=1, stream=1)
-    xi, yi = encode_np(X, 16), encode_np(Y, 16)
-    x0, x1 = _shares(ctx, 64, xi, 1)
-    y0, y1 = _shares(ctx, 64, yi, 2)
-    prm = Params(64, 24, 0)
-    w = ctx.linear_relu(64, 16, prm, x0, x1, y0, y1, tensor_id=3)
-    idx = np.sort(np.random.default_rng(4).choice(n, 4096, replace=False)).astype(np.uint64)
-    t0, t1 = to_np(w["trc0"])[idx], to_np(w["trc1"])[idx]
-    r0, r1 = O.relu(O.params(64, 24, 0), t0, t1, SEED, 4, idx=idx, threads=8)
-    assert np.array_equal(to_np(w["relu0"])[idx], r0)
-    assert np.array_equal(to_np(w["relu1"])[idx], r1)
-    ex0, ex1 = O.share(64, masked(xi[idx], 64), SEED, 1, idx=idx)
-    ey0, ey1 = O.share(64, masked(yi[idx], 64), SEED, 2, idx=idx)
-    p0, p1 = O.mul_beaver(64, ex0, ex1, ey0, ey1, SEED, 3, idx=idx)
-    assert np.array_equal(to_np(w["prod0"])[idx], p0)
-    assert np.array_equal(to_np(w["prod1"])[idx], p1)
-    d0, d1 = O.trunc_det(64, 16, 0, p0, p1)
-    assert np.array_equal(to_np(w["det0"])[idx], d0)
-    assert np.array_equal(to_np(w["det1"])[idx], d1)
-    # the benchmark's call writes only the ReLU and the deterministic truncation
-    only = ctx.linear_relu_buffers(64, 16, n, names=("det0", "det1", "relu0", "relu1"))
-    ctx.linear_relu(64, 16, prm, x0, x1, y0, y1, tensor_id=3, work=only)
-    for nm, t in only.items():
-        assert torch.equal(t, w[nm]), nm
-    # property at any size: reconstructed ReLU = product * DReLU bit, and it
-    # equals max(prod_trunc, 0) up to the exception set and e0
-    rel = O.to_signed(O.reconstruct(64, to_np(w["relu0"]), to_np(w["relu1"])), 64)
-    trc = O.to_signed(O.reconstruct(64, to_np(w["trc0"]), to_np(w["trc1"])), 64)
-    ok = (rel == trc) | (rel == 0)
-    assert ok.all()
-    assert ((rel == np.maximum(trc, 0)).mean()) > 0.9999
 
 
 @pytest.mark.parametrize("bits,k,fixed", [(64, 16, 0), (64, 26, 1 << 26), (32, 12, 0), (16, 4, 0)])
