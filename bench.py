@@ -1,10 +1,14 @@
 """Benchmark of the Bicoptor 2.0 hot path on GB300.
 
-Default workload (one "step" = every row of the hot path over one batch):
-  Z_{2^64}, f = 16: Beaver product of two share tensors of N = 2^22 Gaussian
-  (sigma = 4) reals -> SecureML and deterministic truncation by 16 bits ->
-  ReLU (lx = 24 key bits, c = 0) of the probabilistically truncated product.
-  Three parties simulated on one GPU; inputs resident in HBM.
+Default workload (one "step" = every ReLU tensor of one batch through the
+whole protocol): the ReLU set of a ResNet-18-shaped CNN on 224x224x3 inputs,
+32 images, once in Z_{2^64} (f = 16, lx = 24 key bits, c = 0) and once more
+in Z_{2^32} (f = 12, (lx, c) = (14, 4)) -- 1,088 tensors, 147,718,144
+elements, Laplace(0, 2) activations -- as one CUDA-graph-captured batched
+launch per parameter group.  Three parties simulated on one GPU; input shares
+resident in HBM.  The fused step of a linear layer at l = 64 (Beaver product
+-> SecureML and deterministic truncation -> ReLU, 2^22 elements) and the other
+workloads are reported beside it.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
 the host cores instead (bounded samples of the same workload).
@@ -26,8 +30,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ReLU elems/s on 1 GB300 (3 parties sim.), % roofline, batched vs plain; p99 ms"
-WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
-            "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated product")
+# headline: the ResNet-18 224x224 ReLU set in both rings
+RESNET_IMAGES = 32
+WORKLOAD = ("ResNet-18 224x224 ReLU set x{images} images, once in Z_2^64 (f=16, lx=24, c=0) "
+            "and once in Z_2^32 (f=12, lx=14, c=4): {tensors} tensors, {elems} elements, "
+            "Laplace(0, 2) activations; one CUDA-graph-captured batched launch per parameter "
+            "group")
+BASE_SEED = 0xB1C0_2309_0490_9000
+# DRAM bytes per element of the batched kernel over both rings: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of the two launches of one step
+# of a 4-image set, divided by its elements (None until captured)
+TRAFFIC_PER_ELEM_BATCH = None
+# the fused step of a linear layer (reported beside the headline)
+FUSED_WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
+                  "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated "
+                  "product")
 N_DEFAULT = 1 << 22
 RING, FRAC, K_TRUNC, LX, KEY_OFF = 64, 16, 16, 24, 0
 SEED = 1
@@ -39,21 +56,30 @@ TRAFFIC_PER_ELEM = 43.02
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="resnet18", choices=["resnet18", "fused"],
+                    help="resnet18: the batched ReLU set (default, the headline); fused: the "
+                         "fused linear-layer step alone (for profiling, with --step)")
+    ap.add_argument("--images", type=int, default=RESNET_IMAGES,
+                    help="images of the ResNet-18 set (32 in the workload; fewer for profiling)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--fused-steps", type=int, default=1000,
+                    help="timed steps of the fused linear-layer step")
     ap.add_argument("--step", default="fused", choices=["fused", "chain", "parties", "rss"],
-                    help="fused: one kernel per step (default); chain: the same step as four "
-                         "launches (product, two truncations, ReLU) through HBM, each timed; "
-                         "parties / rss: the ReLU of the step's truncated product by the "
-                         "party-separated launches / the RSS protocol (for profiling)")
+                    help="with --workload fused -- fused: one kernel per step; chain: the same "
+                         "step as four launches (product, two truncations, ReLU) through HBM, "
+                         "each timed; parties / rss: the ReLU of the step's truncated product "
+                         "by the party-separated launches / the RSS protocol")
     ap.add_argument("--no-extras", action="store_true",
-                    help="time the step alone (for profiling): skip e2e, the multiplier "
-                         "microbenchmark and the batched/serving/cpu extras")
+                    help="time the headline alone (for profiling): skip e2e, the CPU "
+                         "baseline, the multiplier microbenchmark and every extra")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
-                    help="arrival window of each serving run (60 s in the full trace)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="arrival window of the offered-load serving run (the full trace is "
+                         "60 s); the 90%% and 50%% load points use --serve-load-seconds")
+    ap.add_argument("--serve-load-seconds", type=float, default=8.0)
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving trace at the offered 2,000 req/s and print it")
     return ap.parse_args()
@@ -144,34 +170,71 @@ def cpu_configs(threads: int, min_elems: int = 10_000_000):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the headline's workload.  Each step
+    runs the oracle's ReLU on the first m elements of each ring's part of the
+    ResNet-18 set (whole tensors in order, with the tensor ids and shares of
+    the GPU run), m sized so that warm-up and timed steps take about two
+    minutes on all host cores."""
     import oracle as O
+    from paper_2309_04909_gb300 import workloads as W
+    from paper_2309_04909_gb300.replicas import rank_seed
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     threads = O.max_threads()
-    xi, yi = workload_inputs(min(args.n, 1 << 20))
-    # calibrate: elements per step so that warmup + steps take ~2 minutes
-    m = 1024
+    O.set_threads(0)
+    seed = rank_seed(BASE_SEED, 0)
+    ts = W.resnet18_mixed_batch(1, seed=3)        # image 0 of the set (per-image streams)
+    per_img = len(W.RESNET18_224_LAYERS)
+    parts = []
+    for s_idx, (ring, frac, lx, c) in enumerate(((64, 16, 24, 0), (32, 12, 14, 4))):
+        idx = [i for i in range(len(ts.sizes)) if ts.ring_bits[i] == ring]
+        x = np.concatenate([np.rint(np.ldexp(ts.reals[i], frac)).astype(np.int64) for i in idx])
+        mask = np.uint64((1 << ring) - 1) if ring < 64 else np.uint64(2**64 - 1)
+        s0, s1 = O.share(ring, x.astype(np.uint64) & mask, seed, 30 + ring)
+        spans, off = [], 0
+        for li, i in enumerate(idx):
+            # tensor id of layer li of image 0 in the full set's numbering
+            spans.append((40000 + s_idx * RESNET_IMAGES * per_img + li, off, ts.sizes[i]))
+            off += ts.sizes[i]
+        parts.append((O.params(ring, lx, c), s0, s1, spans))
+
+    def step(m):
+        for P, s0, s1, spans in parts:
+            for tid, off, size in spans:
+                if off >= m:
+                    break
+                e = min(off + size, m)
+                O.relu(P, s0[off:e], s1[off:e], seed, tid, threads=threads)
+        return 2 * m
+
+    m0 = 1 << 15
     t0 = time.perf_counter()
-    oracle_chain(xi[:m], yi[:m], 5, threads)
-    per = (time.perf_counter() - t0) / m
+    step(m0)
+    per = (time.perf_counter() - t0) / (2 * m0)
     total_steps = max(1, args.steps + args.warmup)
-    m_step = int(max(256, min(xi.size, 120.0 / (per * total_steps))))
-    for w in range(args.warmup):
-        oracle_chain(xi[:m_step], yi[:m_step], 1000 + w, threads)
+    cap = min(p[1].size for p in parts)
+    m = int(max(1 << 12, min(cap, 120.0 / (per * 2 * total_steps))))
+    for _ in range(args.warmup):
+        step(m)
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        oracle_chain(xi[:m_step], yi[:m_step], 2000 + s, threads)
+    for _ in range(args.steps):
+        step(m)
     dt = time.perf_counter() - t0
-    value = m_step * args.steps / dt
+    value = 2 * m * args.steps / dt
+    total = RESNET_IMAGES * sum(W.RESNET18_224_LAYERS) * 2
+    sample = (f"the oracle's ReLU on the first {m:,} elements of each ring's part of the set "
+              f"per step ({2 * m:,} of {total:,} elements)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "elems/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": args.n, "sample_per_step": m_step},
+        "config": {"workload": WORKLOAD.format(images=RESNET_IMAGES, tensors=2 * RESNET_IMAGES
+                                               * per_img, elems=f"{total:,}"),
+                   "images": RESNET_IMAGES, "elements": total, "sample_per_step": 2 * m},
         "cpu_baseline": {"value": value, "unit": "elems/s", "cores": threads, "kind": "oracle",
-                         "sample": f"first {m_step} elements of the workload per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -236,9 +299,6 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2309_04909_gb300 import Context, Params, costmodel
-    from paper_2309_04909_gb300.replicas import max_over_ranks, rank_seed
-
     if args.serving_only:
         serving_only(args)
         return
@@ -249,10 +309,386 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl")
+    try:
+        if args.workload == "fused":
+            fused_main(args, world, rank, local, dev)
+        else:
+            headline(args, world, rank, local, dev)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the headline: the batched ResNet-18 ReLU set in both rings
+# ---------------------------------------------------------------------------
+
+def resnet18_items(ctx, dev, images, seed, tid_base=40000):
+    """The ResNet-18 224x224 ReLU set of `images` images, shared on the device
+    (Laplace(0, 2) reals; l = 64 with f = 16 and l = 32 with f = 12).  Returns
+    the batch items (tensor id tid_base + index in the set), the
+    (elements, l, lx) of each parameter group, the device buffers, and the
+    tensor sizes in item order."""
+    import torch
+    from paper_2309_04909_gb300 import Params, workloads as W
+    ts = W.resnet18_mixed_batch(images, seed=seed)
+    items, parts, keep, sizes = [], [], [], []
+    for ring, frac, prm in ((64, 16, Params(64, 24, 0)), (32, 12, Params(32, 14, 4))):
+        idx = [i for i in range(len(ts.sizes)) if ts.ring_bits[i] == ring]
+        allx = np.concatenate([np.rint(np.ldexp(ts.reals[i], frac)).astype(np.int64) for i in idx])
+        for i in idx:
+            ts.reals[i] = None
+        s0, s1 = ctx.share(ring, torch.from_numpy(allx).to(dev), tensor_id=30 + ring)
+        dt = torch.int64 if ring > 32 else torch.int32
+        o0 = torch.empty(allx.size, dtype=dt, device=dev)
+        o1 = torch.empty_like(o0)
+        keep += [s0, s1, o0, o1]
+        off = 0
+        for i in idx:
+            sl = slice(off, off + ts.sizes[i])
+            items.append((prm, s0[sl], s1[sl], o0[sl], o1[sl], tid_base + i))
+            sizes.append(ts.sizes[i])
+            off += ts.sizes[i]
+        parts.append((int(allx.size), ring, prm.lx))
+        del allx
+    return items, parts, keep, sizes
+
+
+def batched_mul_ops(parts):
+    from paper_2309_04909_gb300 import costmodel
+    return sum(n * costmodel.mul_ops_per_element(lx, ring, relu=True) for n, ring, lx in parts)
+
+
+def timed_over_ranks(step, steps, warmup, world, timer):
+    """W untimed warm-up steps, then exactly `steps` timed steps bracketed by a
+    barrier and a synchronisation on both sides; returns (own ms, max over
+    ranks ms).  `timer` gives start()/stop() -> ms and sync() (CUDA events on
+    the launching stream on the GPU)."""
+    import torch.distributed as dist
+    from paper_2309_04909_gb300.replicas import max_over_ranks
+    for _ in range(max(3, warmup)):
+        step()
+    timer.sync()
+    if world > 1:
+        dist.barrier()
+    timer.sync()
+    timer.start()
+    for _ in range(steps):
+        step()
+    own = timer.stop()
+    if world > 1:
+        dist.barrier()
+    return own, max_over_ranks(own, device=timer.device)
+
+
+class CudaTimer:
+    """CUDA events on torch's current stream (the stream the library launches
+    on); stop() synchronises."""
+
+    def __init__(self, device):
+        import torch
+        self.device = device
+        self._t = torch
+        self.a = torch.cuda.Event(enable_timing=True)
+        self.b = torch.cuda.Event(enable_timing=True)
+
+    def sync(self):
+        self._t.cuda.synchronize()
+
+    def start(self):
+        self.a.record()
+
+    def stop(self):
+        self.b.record()
+        self._t.cuda.synchronize()
+        return self.a.elapsed_time(self.b)
+
+
+def headline(args, world, rank, local, dev):
+    import torch
+    from paper_2309_04909_gb300 import Context, costmodel
+    from paper_2309_04909_gb300.batch import ReluBatch, autotune
+    from paper_2309_04909_gb300.replicas import rank_seed, shard_by_size
+
+    ctx = Context(rank_seed(BASE_SEED, rank), device=local)
+    # each rank its own batch of the same shape (weak scaling: replicas)
+    items, parts, keep, sizes = resnet18_items(ctx, dev, args.images, seed=3 + rank)
+    total = sum(p[0] for p in parts)
+    torch.cuda.synchronize()
+    best = autotune(ctx, items, reps=1, use_cache=False)
+    cfg = (best["tile_elems"], best["ctas_per_sm"], best["schedule"], best["elems_per_thread"],
+           best["slot_unroll"])
+    b = ReluBatch(ctx, items, *cfg)
+    b.capture()
+    launches_per_step = len(parts)          # one batched kernel per parameter group
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    own_ms, total_ms = timed_over_ranks(b.run, args.steps, args.warmup, world, CudaTimer(dev))
+    ck = clocks.stop() if clocks else None
+    assert b.status() == 0, "batched kernel reported a malformed tile"
+    step_ms = own_ms / args.steps
+    value = total * args.steps * world / (total_ms / 1e3)
+    muls = batched_mul_ops(parts)
+    peak = costmodel.int_mul_peak_ops()
+    achieved = muls / (step_ms / 1e3)
+    hbm = sum(n * costmodel.hbm_bytes_per_element_relu(ring) for n, ring, _ in parts)
+    workload = WORKLOAD.format(images=args.images, tensors=len(items), elems=f"{total:,}")
+    line = {
+        "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": workload, "images": args.images, "tensors": len(items),
+                   "elements": total,
+                   "groups": [{"ring_bits": r, "lx": lx, "key_off": 0 if r == 64 else 4,
+                               "elements": n} for n, r, lx in parts],
+                   "schedule": "grid" if best["schedule"] == 1 else "persistent",
+                   "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
+                   "elems_per_thread": best["elems_per_thread"],
+                   "slot_unroll": best["slot_unroll"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"working set {hbm / 1e9:.1f} GB per step > 129 MB L2; no flush"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
+                     # DRAM bytes per step: ncu dram__bytes_read+write of both launches per
+                     # element of a smaller set of the same mix, scaled to this step
+                     "traffic": (TRAFFIC_PER_ELEM_BATCH * total
+                                 if TRAFFIC_PER_ELEM_BATCH else None),
+                     "kernel": "relu_batch_grid_kernel: the step's launches (l=64 lx=24, "
+                               "l=32 lx=14), timed together" if best["schedule"] == 1 else
+                               "relu_batch_kernel (persistent): the step's launches",
+                     "kernel_ms": step_ms, "mul_ops_per_step": muls,
+                     "peak_basis": "integer multiplier: 152 SM x 4 x 16-lane FMA-heavy pipe "
+                                   "x 2070 MHz (maximum SM clock)",
+                     "algorithmic_hbm_bytes_per_step": hbm,
+                     "hbm_frac_of_measured": hbm / (step_ms / 1e3) / 6796.5e9},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": ck,
+    }
+    if world > 1:
+        # strong scaling beside the weak replicas: the 1,088 tensors of ONE set
+        # split over the ranks by size (each tensor whole on one rank)
+        shard = shard_by_size(sizes, world)[rank]
+        mine = [items[i] for i in shard]
+        bs = ReluBatch(ctx, mine, *cfg)
+        bs.capture()
+        _, strong_ms = timed_over_ranks(bs.run, args.steps, args.warmup, world, CudaTimer(dev))
+        line["strong_scaling"] = {
+            "value": total * args.steps / (strong_ms / 1e3), "unit": "elems/s",
+            "ms_per_step": strong_ms / args.steps,
+            "split": "replicas.shard_by_size over the tensors of one set (largest first onto "
+                     "the least loaded rank)",
+            "tensors_on_rank0": len(shard)}
+    if not args.no_extras:
+        line["e2e"] = headline_e2e(ctx, items, cfg, min(args.steps, 20), world, dev)
+    if rank == 0 and world == 1 and not args.no_extras:
+        headline_extras(args, line, ctx, items, parts, cfg, step_ms, local, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    del b
+    ctx.close()
+
+
+def headline_e2e(ctx, items, cfg, steps, world, dev):
+    """The headline step through the host-buffer entry point
+    (bc_relu_batch_host): the input shares in page-locked host memory, the
+    output shares written back to page-locked host memory, every step; the
+    batched kernel reads and writes them across the host link.  Checked equal
+    to the device-resident run's outputs."""
+    import torch
+    from paper_2309_04909_gb300.replicas import max_over_ranks
+    # one page-locked array per ring and share (the batch's activations of a
+    # ring live in one buffer), sliced per tensor like the device arrays
+    host = []
+    h2d = d2h = 0
+    rings = sorted({it[0].ring_bits for it in items})
+    for ring in rings:
+        its = [it for it in items if it[0].ring_bits == ring]
+        n = sum(it[1].numel() for it in its)
+        dt = its[0][1].dtype
+        arrs = [torch.empty(n, dtype=dt).pin_memory() for _ in range(4)]
+        off = 0
+        for prm, s0, s1, o0, o1, tid in its:
+            m = s0.numel()
+            sl = [a[off:off + m] for a in arrs]
+            sl[0].copy_(s0)
+            sl[1].copy_(s1)
+            host.append((prm, sl[0], sl[1], sl[2], sl[3], tid))
+            off += m
+            h2d += 2 * m * s0.element_size()
+            d2h += 2 * m * o0.element_size()
+    ref = {it[5]: it for it in items}
+    # the descriptors name the buffers (addresses and sizes), built once like a
+    # C caller's bc_tensor_desc array; every step plans, runs and synchronises
+    descs, count = ctx.batch_descs(host)
+    run = lambda: ctx.relu_batch_host_descs(descs, count, *cfg)
+    for _ in range(3):
+        run()
+    equal = all(torch.equal(h[3], ref[h[5]][3].cpu()) and torch.equal(h[4], ref[h[5]][4].cpu())
+                for h in host)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run()
+    dt = max_over_ranks(time.perf_counter() - t0, device=dev)
+    total = sum(it[1].numel() for it in items)
+    link = 333.0   # GB/s both directions at once, measured on this pool's GB300 host link
+    value = total * steps * world / dt
+    return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": h2d * world,
+            "d2h_bytes_per_step": d2h * world, "steps": steps, "equal_to_device_run": equal,
+            "api": "bc_relu_batch_host on a prepared descriptor array: pinned host input and "
+                   "output shares (one page-locked array per ring and share, sliced per "
+                   "tensor); the batched kernel loads and stores them across the host link; "
+                   "plan + run + synchronise every step",
+            "link_roofline": {"bytes_per_step": h2d + d2h, "link_GBps": link,
+                              "bound_elems_per_s": world * link * 1e9 * total / (h2d + d2h),
+                              "frac": value / (world * link * 1e9 * total / (h2d + d2h))}}
+
+
+def oracle_relu_sample(ctx, items, per_ring, threads):
+    """The oracle's ReLU on the first `per_ring` elements of each ring's part
+    of the batch (whole tensors in order, the last one cut), on the device's
+    own input shares copied to the host, with `threads` OpenMP threads.
+    Returns (elements, seconds of oracle time)."""
+    import oracle as O
+    done = {}
+    elems, secs = 0, 0.0
+    for prm, s0, s1, o0, o1, tid in items:
+        left = per_ring - done.get(prm.ring_bits, 0)
+        if left <= 0:
+            continue
+        m = min(left, s0.numel())
+        a0 = s0[:m].cpu().numpy().view(np.uint64 if prm.ring_bits > 32 else np.uint32)
+        a1 = s1[:m].cpu().numpy().view(np.uint64 if prm.ring_bits > 32 else np.uint32)
+        P = O.params(prm.ring_bits, prm.lx, prm.key_off)
+        t0 = time.perf_counter()
+        O.relu(P, a0, a1, ctx.seed, tid, threads=threads)
+        secs += time.perf_counter() - t0
+        done[prm.ring_bits] = done.get(prm.ring_bits, 0) + m
+        elems += m
+    return elems, secs
+
+
+def headline_extras(args, line, ctx, items, parts, cfg, step_ms, local, dev):
+    """Single-GPU extras of the headline (each recorded under its key; a
+    failing extra records its error and the line still prints): the measured
+    multiplier rates, the CPU oracle on a sample of the same set, the
+    per-tensor launches it replaces, and then the fused linear-layer step and
+    the other workloads."""
+    import torch
+    from paper_2309_04909_gb300 import costmodel
+
+    def extra(key, fn, into=None):
+        try:
+            (into if into is not None else line)[key] = fn()
+        except Exception as exc:   # noqa: BLE001 - recorded, the headline stands
+            (into if into is not None else line)[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            try:
+                torch.cuda.synchronize()
+            except Exception:      # noqa: BLE001 - a sticky CUDA error is already recorded
+                pass
+
+    def measured_rates():
+        # the multiplier's rates measured by our own microbenchmark (after the
+        # timed region): the time the step's algorithmic products need at
+        # those rates, against the step's time
+        from paper_2309_04909_gb300 import measure_int_peaks
+        mp = measure_int_peaks(local)
+        w = lo = hi = 0
+        for n, ring, lx in parts:
+            a, b, c = costmodel.mul_counts_split(lx, ring, relu=True)
+            w, lo, hi = w + n * a, lo + n * b, hi + n * c
+        bound_ms = (w / mp["imad_wide_per_s"] + lo / mp["imad_per_s"]
+                    + hi / mp["imad_hi_per_s"]) * 1e3
+        return {"widening_products": w, "low_products": lo, "high_products": hi,
+                "imad_wide_per_s": mp["imad_wide_per_s"], "imad_per_s": mp["imad_per_s"],
+                "imad_hi_per_s": mp["imad_hi_per_s"], "alu_per_s": mp["alu_per_s"],
+                "sm_mhz": mp["sm_mhz"], "bound_ms": bound_ms, "frac": bound_ms / step_ms,
+                "basis": "widening products timed as Philox-4x32 rounds, low products as "
+                         "32-bit multiply-adds, high products as hi32(x k) chains; "
+                         "full-occupancy microbenchmark on this GPU"}
+
+    def cpu_baseline():
+        import oracle as O
+        total = sum(p[0] for p in parts)
+        cores = O.max_threads()
+        per = 1 << 23
+        m, dt = oracle_relu_sample(ctx, items, per, cores)
+        m1, dt1 = oracle_relu_sample(ctx, items, 1 << 18, 1)
+        return {"value": m / dt, "unit": "elems/s", "cores": cores, "kind": "oracle",
+                "sample": f"the oracle's ReLU on the first {per:,} elements of each ring's "
+                          f"part of the set ({m:,} elements, input shares from the device), "
+                          f"{dt:.1f} s; full set extrapolated to {total * dt / m:.0f} s",
+                "full_set_seconds_extrapolated": total * dt / m,
+                "single_thread": {"value": m1 / dt1, "sample_elems": m1, "seconds": dt1}}
+
+    def plain():
+        # one launch per tensor (the single-tensor kernel), replayed from a
+        # CUDA graph, against the batched graph; identical outputs
+        q = [(torch.empty_like(it[3]), torch.empty_like(it[4])) for it in items]
+
+        def run_plain():
+            for it, (a, b) in zip(items, q):
+                ctx.relu(it[0], it[1], it[2], it[5], out=(a, b))
+
+        run_plain()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run_plain()
+        plain_ms = median_ms(g.replay)
+        same = all(torch.equal(it[3], a) and torch.equal(it[4], b) for it, (a, b) in zip(items, q))
+        return {"plain_graph_ms": plain_ms, "batched_graph_ms": step_ms,
+                "speedup_vs_plain_graph": plain_ms / step_ms, "plain_launches": len(items),
+                "batched_launches": len(parts), "identical_to_plain": bool(same),
+                "timing": "plain: median of 20 graph replays, CUDA events per run; batched: the "
+                          "headline's timed steps"}
+
+    extra("measured_rates", measured_rates, into=line["roofline"])
+    extra("cpu_baseline", cpu_baseline)
+    extra("batched_vs_plain_resnet18", plain)
+    # the fused linear-layer step and the other workloads
+    try:
+        fl, state = fused_step(args, 1, 0, local, dev, steps=args.fused_steps)
+        line["fused_step_l64_2p22"] = fl
+        run_extras(args, line, *state)
+        state[0].close()
+    except Exception as exc:   # noqa: BLE001 - recorded, the headline stands
+        line["fused_step_l64_2p22"] = {"error": f"{type(exc).__name__}: {exc}"}
+
+
+# ---------------------------------------------------------------------------
+# the fused step of a linear layer (product -> truncations -> ReLU)
+# ---------------------------------------------------------------------------
+
+def fused_main(args, world, rank, local, dev):
+    """`--workload fused`: the fused step alone as the line (for profiling),
+    or its chain / party-separated / RSS variants with --step."""
+    line, state = fused_step(args, world, rank, local, dev, steps=args.steps)
+    if line is None:
+        return
+    if not args.no_extras:
+        ctx, prm, x0, x1, y0, y1 = state[:6]
+        n = state[9]
+        line["e2e"] = e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 100), world,
+                                    dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    state[0].close()
+
+
+def fused_step(args, world, rank, local, dev, steps):
+    """Times `steps` fused steps (one kernel each) at N = args.n; returns the
+    line of that step and the state the extras read."""
+    import torch
+    from paper_2309_04909_gb300 import Context, Params, costmodel
+    from paper_2309_04909_gb300.replicas import rank_seed
 
     n = args.n
     xi, yi = workload_inputs(n, seed=SEED + rank)   # each rank its own batch (replicas)
-    ctx = Context(rank_seed(0xB1C0_2309_0490_9000, rank), device=local)
+    ctx = Context(rank_seed(BASE_SEED, rank), device=local)
     x0, x1 = ctx.share(RING, torch.from_numpy(xi).to(dev), tensor_id=1)
     y0, y1 = ctx.share(RING, torch.from_numpy(yi).to(dev), tensor_id=2)
     prm = Params(RING, LX, KEY_OFF)
@@ -265,51 +701,35 @@ def main():
     def step():
         ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=work)
 
-    if args.step == "chain":
+    if args.workload == "fused" and args.step == "chain":
         chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev)
         ctx.close()
-        return
-    if args.step in ("parties", "rss"):
+        return None, None
+    if args.workload == "fused" and args.step in ("parties", "rss"):
         variant_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev)
         ctx.close()
-        return
+        return None, None
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
     # the step is exactly one launch of the fused kernel, so the start/end
     # events on its stream time the kernel back to back: no per-step events,
     # which would add their own gaps between launches
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    start.record()
-    for _ in range(args.steps):
-        step()
-    end.record()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    own_ms, total_ms = timed_over_ranks(step, steps, args.warmup, world, CudaTimer(dev))
     ck = clocks.stop() if clocks else None
-    own_ms = start.elapsed_time(end)
-    total_ms = max_over_ranks(own_ms, device=dev)
-    kern_ms = own_ms / args.steps        # average launch duration of the fused kernel
-    value = n * args.steps * world / (total_ms / 1e3)
+    kern_ms = own_ms / steps        # average launch duration of the fused kernel
+    value = n * steps * world / (total_ms / 1e3)
     ops = costmodel.linear_relu_int_ops_per_element(LX, RING)
     muls = costmodel.linear_relu_mul_ops_per_element(LX, RING)
     peak = costmodel.int_mul_peak_ops()
     achieved = muls * n / (kern_ms / 1e3)
     issue_frac = ops * n / (kern_ms / 1e3) / costmodel.int_issue_peak_ops()
-
     line = {
         "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "ring_bits": RING, "frac_bits": FRAC,
+        "config": {"workload": FUSED_WORKLOAD, "n": n, "ring_bits": RING, "frac_bits": FRAC,
                    "trunc_bits": K_TRUNC, "lx": LX, "key_off": KEY_OFF, "p": 16777259,
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 268 MB per step > 129 MB L2; no flush"},
@@ -325,13 +745,10 @@ def main():
                      "int_ops_per_element": ops,
                      "issue_frac": issue_frac,
                      "hbm_bytes_per_element": costmodel.hbm_bytes_per_element_linear_relu(RING)},
-        "gpu_launches": args.steps,
+        "gpu_launches": steps,
         "clocks": ck,
     }
     if rank == 0 and not args.no_extras:
-        # the multiplier's rates measured by our own microbenchmark (after the
-        # timed region): the time the step's algorithmic products need at
-        # those rates, against the kernel's time
         from paper_2309_04909_gb300 import measure_int_peaks
         mp = measure_int_peaks(local)
         w, lo, hi = costmodel.mul_counts_split(LX, RING, relu=True, product=True)
@@ -342,26 +759,9 @@ def main():
             "high_products_per_element": hi,
             "imad_wide_per_s": mp["imad_wide_per_s"], "imad_per_s": mp["imad_per_s"],
             "imad_hi_per_s": mp["imad_hi_per_s"], "alu_per_s": mp["alu_per_s"],
-            "sm_mhz": mp["sm_mhz"], "bound_ms": bound_ms, "frac": bound_ms / kern_ms,
-            "basis": "widening products timed as Philox-4x32 rounds, low products as 32-bit "
-                     "multiply-adds, high products as hi32(x k) chains; full-occupancy "
-                     "microbenchmark on this GPU"}
-
-    # end to end through the host-buffer entry point, every rank at once
-    # (--no-extras, used for profiling the step alone, skips it)
-    if not args.no_extras:
-        line["e2e"] = e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 100), world,
-                                    dev)
-
-    # the long extras run in the single-GPU run only (N > 1 runs measure the
-    # scaled step; every rank's GPU would otherwise be held for minutes)
-    if rank == 0 and world == 1 and not args.no_extras:
-        run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, dev)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+            "sm_mhz": mp["sm_mhz"], "bound_ms": bound_ms, "frac": bound_ms / kern_ms}
+    state = (ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, dev)
+    return line, state
 
 
 def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, dev):
@@ -387,28 +787,33 @@ def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, de
                           f"(share, product, both truncations, ReLU), {dt:.1f} s",
                 "single_thread": {"value": rate1, "sample_elems": m1, "seconds": dt1}}
 
+    # the fused linear-layer step's own extras go under its key
+    fl = line.setdefault("fused_step_l64_2p22", {})
+    extra("e2e", lambda: e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, 100, 1, dev), into=fl)
     # every intermediate of the step, for the extras that read them
     ctx.linear_relu(RING, K_TRUNC, prm, x0, x1, y0, y1, tensor_id=3, work=buf)
-    extra("unfused_chain", lambda: chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms))
+    extra("unfused_chain", lambda: chain_bench(ctx, prm, x0, x1, y0, y1, buf, n, kern_ms),
+          into=fl)
+    if "error" not in fl.get("e2e", {"error": 1}):
+        extra("paths", lambda: e2e_paths(ctx, prm, x0, x1, y0, y1, n, 30, buf), into=fl["e2e"])
+    extra("trunc_failures", lambda: trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev),
+          into=fl)
+    extra("cpu_baseline", cpu_baseline, into=fl)
+    relu_ms = fl["unfused_chain"].get("relu_ms", kern_ms)
+    extra("party_separated", lambda: parties_bench(ctx, prm, buf, n, relu_ms), into=fl)
+    extra("rss_relu", lambda: rss_bench(ctx, prm, buf, n), into=fl)
+    # the other workloads
     extra("hbm_kernels_isolated", lambda: hbm_isolated(ctx, dev))
-    if "e2e" in line:
-        extra("paths", lambda: e2e_paths(ctx, prm, x0, x1, y0, y1, n, min(args.steps, 30), buf),
-              into=line["e2e"])
-    extra("trunc_failures", lambda: trunc_failures(ctx, xi, yi, x0, x1, y0, y1, buf, dev))
     extra("linear_layer_truncation", lambda: linear_trunc_table(ctx, dev))
-    extra("cpu_baseline", cpu_baseline)
     extra("cpu_baseline_batched_configs", lambda: cpu_configs(_threads()))
-    relu_ms = line["unfused_chain"].get("relu_ms", kern_ms)
-    extra("party_separated", lambda: parties_bench(ctx, prm, buf, n, relu_ms))
-    extra("rss_relu", lambda: rss_bench(ctx, prm, buf, n))
     extra("drelu_l32_uniform", lambda: uniform_l32_drelu_check(ctx, dev))
     extra("size_sweep_l64", lambda: size_sweep(ctx, dev))
     extra("batched_vs_plain", lambda: vgg16_batched_vs_plain(ctx, dev))
-    extra("resnet18_mixed_batched", lambda: resnet18_batched(ctx, dev))
     bvp = line["batched_vs_plain"]
     if "batched_elems_per_s" in bvp:
         extra("serving", lambda: serving_bench(ctx, dev, bvp["batched_elems_per_s"],
-                                               args.serve_seconds, bvp))
+                                               args.serve_seconds, args.serve_load_seconds,
+                                               bvp))
 
 
 def _threads():
@@ -1010,7 +1415,7 @@ def serving_only(args):
     ctx.close()
 
 
-def serving_bench(ctx, dev, capacity, seconds, bvp, budget=40 << 30):
+def serving_bench(ctx, dev, capacity, seconds, load_seconds, bvp, budget=40 << 30):
     """Continuous-batching serving: Poisson arrivals of 1-64-image LeNet /
     VGG-16 ReLU requests (50/50), l = 64, under a 40 GB admission budget.
     Runs the offered 2,000 req/s and 50 % / 90 % of the measured batched
@@ -1021,15 +1426,17 @@ def serving_bench(ctx, dev, capacity, seconds, bvp, budget=40 << 30):
     setup = ServingSetup(ctx, prm, budget, seed=4, pool_images=64)
     mean_elems = 0.5 * 32.5 * (setup.per_image["vgg16"] + setup.per_image["lenet"])
     sched = 1 if bvp.get("schedule") == "grid" else 0
-    out = {"budget_bytes": budget, "arrival_window_s": seconds,
-           "mean_elems_per_request": mean_elems, "capacity_elems_per_s": capacity}
+    out = {"budget_bytes": budget, "mean_elems_per_request": mean_elems,
+           "capacity_elems_per_s": capacity}
     for label, rate in (("offered_2000_rps", 2000.0),
                         ("load_90pct", 0.9 * capacity / mean_elems),
                         ("load_50pct", 0.5 * capacity / mean_elems)):
-        trace = W.serving_trace(rate, seconds, seed=4)
+        window = seconds if label.startswith("offered") else load_seconds
+        trace = W.serving_trace(rate, window, seed=4)
         reqs = setup.requests_from_trace(trace)
         st = Engine(setup.executor(schedule=sched), budget, max_iter_elems=1 << 24).run(reqs)
         s = st.summary()
+        s["arrival_window_s"] = window
         s["rate_rps"] = rate
         s["offered_elems_per_s"] = rate * mean_elems
         out[label] = s

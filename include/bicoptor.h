@@ -301,6 +301,20 @@ int bc_relu_batch(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
  * synchronises the context's stream. */
 int bc_batch_status(bc_ctx *ctx);
 
+/* The batched DReLU/ReLU of bc_relu_batch (Alg. drelu / Alg. relu per tensor,
+ * Sec. 6 per-network ReLU sets) on HOST buffers: sh0, sh1, o0 and o1 of every
+ * descriptor are host pointers into page-locked memory mapped for the device
+ * (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with the mapped flag;
+ * a torch pin_memory() tensor qualifies).  The batched kernel loads the input
+ * shares and stores the output shares across the host link itself, so no
+ * device copy of the data is made; the tables are planned as by
+ * bc_relu_batch_plan (into the context's workspace, replacing any earlier
+ * plan).  Returns after the outputs are in host memory.  BC_EINVAL if a
+ * buffer (n lanes of the descriptor's ring) is not mapped page-locked memory;
+ * nothing is launched then.  Same results as bc_relu_batch on device copies. */
+int bc_relu_batch_host(bc_ctx *ctx, const bc_tensor_desc *descs, int count,
+                       const bc_batch_config *cfg);
+
 /* Batched ReLU/DReLU that allocates nothing.  The paper has no counterpart:
  * this serves callers that may not call cudaMalloc -- code running inside a
  * host engine that owns all device memory through its own pool, or a loop
@@ -314,11 +328,16 @@ int bc_batch_status(bc_ctx *ctx);
  *   - At most BC_STATIC_MAX_TENSORS tensors and BC_STATIC_MAX_TILES tiles of
  *     `tile_elems` elements (0 = 4096) per call; larger requests return
  *     BC_ELIMIT before anything is launched.
- *   - The first call on a device looks up the array's device address (set-up);
- *     make that first call before any stream capture.
+ *   - Every call first looks up the array's device address on `device`, with
+ *     that device current (its set-up; the runtime resolves the address of a
+ *     loaded module without allocating).
+ *   - A call on a stream that is being captured returns BC_EINVAL and does
+ *     nothing: the tables are copied from host staging that the next call
+ *     overwrites, so a captured copy would read another call's tables when
+ *     replayed.
  *   - Calls share the array, which keeps the last call's contents; each call
- *     clears the counter and status word it needs.  Calls that overlap on the
- *     GPU (e.g. on two streams) race on the array.
+ *     clears the counters and the status word before its launch.  Calls that
+ *     overlap on the GPU (e.g. on two streams) race on the array.
  *   - The tables are copied from pageable host staging, which orders the copy
  *     after work already queued on `cuda_stream`.
  *   - No communication is counted (there is no context).
@@ -327,6 +346,12 @@ int bc_batch_status(bc_ctx *ctx);
 #define BC_STATIC_MAX_TILES 16384
 int bc_relu_batch_static(uint64_t seed, int device, void *cuda_stream,
                          const bc_tensor_desc *descs, int count, int tile_elems);
+/* Status word of the last bc_relu_batch_static launch on `device`: BC_OK, or
+ * BC_ECHECK if the kernel met a tile that does not fit its tensor (what two
+ * overlapping calls could leave in the shared tables) and skipped it.  Reads
+ * and clears the word in stream order on `cuda_stream`, then synchronises
+ * that stream; allocates nothing.  BC_EINVAL on a capturing stream. */
+int bc_relu_batch_static_status(int device, void *cuda_stream);
 
 /* ---- fused product -> truncation -> ReLU (Sec. 4, Alg. smltrc/newtrc, Alg. relu) */
 

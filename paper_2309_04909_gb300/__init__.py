@@ -365,6 +365,54 @@ class Context:
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_plan(self._h, descs, count, ctypes.byref(cfg)))
 
+    def relu_batch_host(self, items: Sequence[Tuple], tile_elems: int = 0, ctas_per_sm: int = 0,
+                        schedule: int = 0, elems_per_thread: int = 0, slot_unroll: int = 0):
+        """The batched DReLU/ReLU on pinned HOST tensors (bc_relu_batch_host):
+        items as for relu_batch_plan, with page-locked CPU tensors (e.g.
+        pin_memory()); the kernel reads and writes them across the host link.
+        Returns once the outputs are in host memory."""
+        arr = (TensorDesc * max(1, len(items)))()
+        for i, it in enumerate(items):
+            prm, s0, s1, o0, o1, tid = it[:6]
+            op = it[6] if len(it) > 6 else OP_RELU
+            off = it[7] if len(it) > 7 else 0
+            for t, nm in ((s0, "s0"), (s1, "s1"), (o0, "o0"), (o1, "o1")):
+                if (t.dtype is not lane_dtype(prm.ring_bits) or t.is_cuda or not t.is_contiguous()
+                        or (t.numel() and not t.is_pinned())):
+                    raise BicoptorError(f"{nm}: expected a contiguous pinned CPU "
+                                        f"{lane_dtype(prm.ring_bits)} tensor")
+            arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
+                                s0.numel(), tid, op, prm.c_struct(), off)
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule, elems_per_thread, slot_unroll)
+        self._sync_stream()
+        self._check(self._lib.bc_relu_batch_host(self._h, arr, len(items), ctypes.byref(cfg)))
+
+    @staticmethod
+    def batch_descs(items: Sequence[Tuple]):
+        """A prepared ctypes array of bc_tensor_desc for `items` (tuples as for
+        relu_batch_plan; device or pinned host tensors).  It records the
+        buffers' addresses and sizes only, so it stays valid while the tensors
+        live and may be passed to relu_batch_plan_descs / relu_batch_host_descs
+        call after call.  Returns (array, count)."""
+        arr = (TensorDesc * max(1, len(items)))()
+        for i, it in enumerate(items):
+            prm, s0, s1, o0, o1, tid = it[:6]
+            op = it[6] if len(it) > 6 else OP_RELU
+            off = it[7] if len(it) > 7 else 0
+            arr[i] = TensorDesc(s0.data_ptr(), s1.data_ptr(), o0.data_ptr(), o1.data_ptr(),
+                                s0.numel(), tid, op, prm.c_struct(), off)
+        return arr, len(items)
+
+    def relu_batch_host_descs(self, descs, count: int, tile_elems: int = 0, ctas_per_sm: int = 0,
+                              schedule: int = 0, elems_per_thread: int = 0,
+                              slot_unroll: int = 0):
+        """bc_relu_batch_host on a prepared descriptor array (batch_descs) of
+        pinned host buffers; the library checks that every buffer is mapped
+        page-locked memory.  Returns once the outputs are in host memory."""
+        cfg = BatchConfig(tile_elems, ctas_per_sm, schedule, elems_per_thread, slot_unroll)
+        self._sync_stream()
+        self._check(self._lib.bc_relu_batch_host(self._h, descs, count, ctypes.byref(cfg)))
+
     def relu_batch_run(self):
         self._sync_stream()
         self._check(self._lib.bc_relu_batch_run(self._h))
@@ -482,9 +530,18 @@ def relu_batch_static(seed: int, items: Sequence[Tuple], tile_elems: int = 0,
                                   tile_elems)
     if rc == -6:
         raise BicoptorError("bc_relu_batch_static: batch exceeds the fixed scratch capacity "
-                            "(256 tensors, 16384 tiles)")
+                            "(256 tensors, 16384 tiles, 32 parameter groups)")
     if rc != 0:
         raise BicoptorError(f"bc_relu_batch_static failed: {lib.bc_strerror(rc).decode()}")
+
+
+def relu_batch_static_status(device: int = 0, stream: Optional[torch.cuda.Stream] = None) -> int:
+    """Status word of the last relu_batch_static launch on `device` (0, or -5
+    = BC_ECHECK for a skipped malformed tile); read and cleared in stream
+    order, then the stream is synchronised."""
+    lib = _native.lib()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return int(lib.bc_relu_batch_static_status(device, ctypes.c_void_p(s.cuda_stream)))
 
 
 def to_unsigned_numpy(t: torch.Tensor):

@@ -158,6 +158,7 @@ SIGNATURES = {
     "bc_relu_batch_plan": (c_int, [c_void_p, P(TensorDesc), c_int, P(BatchConfig)]),
     "bc_relu_batch_run": (c_int, [c_void_p]),
     "bc_relu_batch": (c_int, [c_void_p, P(TensorDesc), c_int, P(BatchConfig)]),
+    "bc_relu_batch_host": (c_int, [c_void_p, P(TensorDesc), c_int, P(BatchConfig)]),
     "bc_batch_status": (c_int, [c_void_p]),
     "bc_linear_relu": (c_int, [c_void_p, P(LinearReluArgs)]),
     "bc_linear_relu_host": (c_int, [c_void_p, P(LinearReluArgs)]),
@@ -168,6 +169,7 @@ SIGNATURES = {
     "bc_count_trunc_failures": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                         c_size, c_void_p]),
     "bc_relu_batch_static": (c_int, [c_u64, c_int, c_void_p, P(TensorDesc), c_int, c_int]),
+    "bc_relu_batch_static_status": (c_int, [c_int, c_void_p]),
     "bc_party_msg_words": (c_size, [c_int, c_size]),
     "bc_parties_status": (c_int, [c_void_p]),
     "bc_test_drop_p2_copies": (c_int, [c_void_p, c_int]),

@@ -26,16 +26,13 @@ struct bc_ctx {
   bc::AuditPtrs audit{};
   char last_err[256] = {0};
   // validated (lx, p) pairs
-  uint32_t ok_p[4] = {0, 0, 0, 0};
-  int ok_lx[4] = {0, 0, 0, 0};
-  int ok_next = 0;
+  bc::PrimeCache primes;
   // batched launch plan
   bc::BatchTensor* d_tensors = nullptr;
   bc::BatchTile* d_tiles = nullptr;
-  // pinned host staging of the tables, double-buffered: buffer i may be
+  // pinned host staging of the tensor table, double-buffered: buffer i may be
   // refilled once the copy recorded by plan_ev[i] has finished
   bc::BatchTensor* h_tensors[2] = {nullptr, nullptr};
-  bc::BatchTile* h_tiles[2] = {nullptr, nullptr};
   cudaEvent_t plan_ev[2] = {nullptr, nullptr};
   bool plan_ev_live[2] = {false, false};
   int plan_next = 0;
@@ -82,41 +79,11 @@ struct Trace {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-bool is_prime32(uint64_t q) {
-  if (q < 2) return false;
-  if (q % 2 == 0) return q == 2;
-  for (uint64_t d = 3; d * d <= q; d += 2)
-    if (q % d == 0) return false;
-  return true;
-}
-
 size_t lane_bytes(int bits) { return bits > 32 ? 8 : 4; }
 
-bc::RoundKeys make_round_keys(uint64_t seed) {
-  bc::RoundKeys rk;
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  for (int r = 0; r < 10; ++r) {
-    rk.k0[r] = k0;
-    rk.k1[r] = k1;
-    k0 += bc::kPhiloxW0;
-    k1 += bc::kPhiloxW1;
-  }
-  return rk;
-}
-
-bc::ModP make_modp(uint32_t p) {
-  bc::ModP m;
-  m.p = p;
-  uint32_t inv = p;                      // Newton: inv = p^{-1} mod 2^32
-  for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
-  m.pinv = 0u - inv;
-  const uint64_t r1 = ((uint64_t)1 << 32) % p;
-  m.r2 = (uint32_t)((r1 * r1) % p);
-  m.pm1 = p - 1;
-  return m;
-}
-
-uint64_t ring_mask(int bits) { return bits >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1); }
+using bc::is_prime_u32;
+using bc::make_round_keys;
+using bc::ring_mask;
 
 // Checked mode: count, on the context stream, the lanes of the given arrays
 // that have bits at or above ring_bits, wait, and refuse the call if any do.
@@ -136,32 +103,7 @@ int check_canonical(bc_ctx* ctx, int ring_bits, std::initializer_list<const void
 // Checks of Alg. drelu's parameters; fills the kernel constants.
 int make_consts(bc_ctx* ctx, const bc_drelu_params* prm, uint32_t tensor_id,
                 bc::ReluConsts* k) {
-  if (!prm) return BC_EINVAL;
-  const int ell = prm->ring_bits, lx = prm->lx, c = prm->key_off;
-  if (ell < 2 || ell > 64 || lx < 1 || lx > 31 || c < 0 || c + 2 * lx > ell) return BC_EINVAL;
-  uint32_t p = prm->p ? prm->p : bc_prime_above(lx);
-  const uint64_t lo = (uint64_t)1 << lx, hi = (uint64_t)1 << (lx + 1);
-  if ((uint64_t)p <= lo || (uint64_t)p >= hi) return BC_EINVAL;
-  bool known = false;
-  for (int i = 0; i < 4; ++i) known |= (ctx->ok_p[i] == p && ctx->ok_lx[i] == lx);
-  if (!known) {
-    if (!is_prime32(p)) return BC_EINVAL;
-    ctx->ok_p[ctx->ok_next] = p;
-    ctx->ok_lx[ctx->ok_next] = lx;
-    ctx->ok_next = (ctx->ok_next + 1) & 3;
-  }
-  k->rk = ctx->rk;
-  k->mp = make_modp(p);
-  k->ring_mask = ring_mask(ell);
-  k->ring_bits = (uint32_t)ell;
-  k->lx = (uint32_t)lx;
-  k->c = (uint32_t)c;
-  k->mx = (uint32_t)(lo - 1);
-  k->two_lx = (uint32_t)lo;
-  k->p_minus_2lx = p - (uint32_t)lo;
-  k->tensor_id = tensor_id;
-  k->elem_base = 0;
-  return BC_OK;
+  return bc::make_relu_consts(prm, ctx->rk, tensor_id, ctx->primes, k);
 }
 
 // Communication of one protocol call over n elements (bits).
@@ -253,7 +195,7 @@ uint32_t bc_prime_above(int lx) {
   const uint32_t known = found[lx].load(std::memory_order_relaxed);
   if (known) return known;
   uint64_t q = ((uint64_t)1 << lx) + 1;
-  while (!is_prime32(q)) ++q;
+  while (!is_prime_u32(q)) ++q;
   found[lx].store((uint32_t)q, std::memory_order_relaxed);
   return (uint32_t)q;
 }
@@ -303,7 +245,6 @@ int bc_destroy(bc_ctx* ctx) {
   cudaFree(ctx->d_tiles);
   for (int i = 0; i < 2; ++i) {
     cudaFreeHost(ctx->h_tensors[i]);
-    cudaFreeHost(ctx->h_tiles[i]);
     if (ctx->plan_ev[i]) cudaEventDestroy(ctx->plan_ev[i]);
   }
   cudaFree(ctx->d_counter);
@@ -374,7 +315,7 @@ int bc_trunc_det(bc_ctx* ctx, int ring_bits, int k1, int k2, const void* sh0, co
 int bc_mod_switch(bc_ctx* ctx, int lp, uint32_t p, const void* sh0, const void* sh1, size_t n,
                   uint32_t* o0, uint32_t* o1) {
   if (!ctx || lp < 1 || lp > 31) return BC_EINVAL;
-  if ((uint64_t)p <= ((uint64_t)1 << lp) || !is_prime32(p)) return BC_EINVAL;
+  if ((uint64_t)p <= ((uint64_t)1 << lp) || !is_prime_u32(p)) return BC_EINVAL;
   if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
   BC_TRACE();
   if (int rc = check_canonical(ctx, lp, {sh0, sh1}, n)) return rc;
@@ -624,17 +565,14 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
     ctx->d_tiles = nullptr;
     for (int i = 0; i < 2; ++i) {
       cudaFreeHost(ctx->h_tensors[i]);
-      cudaFreeHost(ctx->h_tiles[i]);
       ctx->h_tensors[i] = nullptr;
-      ctx->h_tiles[i] = nullptr;
       ctx->plan_ev_live[i] = false;
     }
     ctx->cap_tensors = ctx->cap_tiles = 0;
     bool ok = cudaMalloc(&ctx->d_tensors, capt * sizeof(bc::BatchTensor)) == cudaSuccess &&
               cudaMalloc(&ctx->d_tiles, capl * sizeof(bc::BatchTile)) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i)
-      ok = cudaMallocHost(&ctx->h_tensors[i], capt * sizeof(bc::BatchTensor)) == cudaSuccess &&
-           cudaMallocHost(&ctx->h_tiles[i], capl * sizeof(bc::BatchTile)) == cudaSuccess;
+      ok = cudaMallocHost(&ctx->h_tensors[i], capt * sizeof(bc::BatchTensor)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       return BC_ENOMEM;
@@ -646,36 +584,32 @@ int bc_relu_batch_plan(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
   const int sb = ctx->plan_next;
   if (ctx->plan_ev_live[sb]) CK(cudaEventSynchronize(ctx->plan_ev[sb]));
   bc::BatchTensor* h_tensors = ctx->h_tensors[sb];
-  bc::BatchTile* h_tiles = ctx->h_tiles[sb];
-  if (count) memcpy(h_tensors, tens.data(), sizeof(bc::BatchTensor) * count);
-  // Tiles grouped by parameter group; within a group the largest tensors come
-  // first so the long ones start early and short ones fill the tail.
+  // Tensors grouped by parameter group; within a group the largest come first
+  // so that the long ones start early and short ones fill the tail.  The
+  // table holds them in that order with the index of each one's first tile;
+  // the tile table itself is written on the device.
   std::vector<int> order(count);
   for (int t = 0; t < count; ++t) order[t] = t;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return grp[a] != grp[b] ? grp[a] < grp[b] : descs[a].n > descs[b].n;
   });
-  size_t w = 0;
+  uint32_t w = 0;
   for (int oi = 0; oi < count; ++oi) {
     const int t = order[oi];
-    if (oi == 0 || grp[order[oi - 1]] != grp[t]) groups[grp[t]].begin = (uint32_t)w;
-    for (uint64_t s = 0; s < descs[t].n; s += tile) {
-      bc::BatchTile bt;
-      bt.tensor = (uint32_t)t;
-      bt.start = s;
-      bt.count = (uint32_t)std::min<uint64_t>(tile, descs[t].n - s);
-      h_tiles[w++] = bt;
-    }
-    groups[grp[t]].end = (uint32_t)w;
+    if (oi == 0 || grp[order[oi - 1]] != grp[t]) groups[grp[t]].begin = w;
+    h_tensors[oi] = tens[t];
+    h_tensors[oi].first_tile = w;
+    w += (uint32_t)((descs[t].n + tile - 1) / tile);
+    groups[grp[t]].end = w;
   }
-  // Stream order puts these copies after every kernel already queued, so a
-  // batch still running keeps reading the previous tables until it is done.
+  // Stream order puts the copy and the expansion after every kernel already
+  // queued, so a batch still running keeps reading the previous tables until
+  // it is done.
   if (count)
     CK(cudaMemcpyAsync(ctx->d_tensors, h_tensors, sizeof(bc::BatchTensor) * count,
                        cudaMemcpyHostToDevice, ctx->stream));
-  if (w)
-    CK(cudaMemcpyAsync(ctx->d_tiles, h_tiles, sizeof(bc::BatchTile) * w,
-                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(bc::launch_expand_tiles(ctx->d_tensors, (uint32_t)count, w, (uint32_t)tile, ctx->d_tiles,
+                             ctx->stream));
   CK(cudaEventRecord(ctx->plan_ev[sb], ctx->stream));
   ctx->plan_ev_live[sb] = true;
   ctx->plan_next = sb ^ 1;
@@ -711,6 +645,118 @@ int bc_batch_status(bc_ctx* ctx) {
   CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device address of a host pointer that the GPU can load from and store to
+// (page-locked memory of the CUDA allocator or registered with it), else NULL.
+void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Driver query of a pointer's allocation, reached through the runtime's entry
+// point table (no link-time dependence on the driver library): memory type,
+// device address and the extent of the allocation it belongs to.
+typedef int (*PointerGetAttributesFn)(unsigned int, int*, void**, unsigned long long);
+PointerGetAttributesFn pointer_query() {
+  static PointerGetAttributesFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PointerGetAttributesFn>(f);
+  }();
+  return fn;
+}
+
+// Device addresses of many host pointers.  The pointers of a batch are mostly
+// slices of a few large page-locked allocations, so each allocation is looked
+// up once: the driver reports the allocation's extent with its device address,
+// and every later buffer that lies inside a known allocation maps by the same
+// offset without another query.  Without the extent (an older driver), each
+// buffer's first and last byte are checked separately.
+struct HostMap {
+  struct Span {
+    uintptr_t lo, hi;   // host range [lo, hi) of one mapped allocation
+    intptr_t delta;     // device address - host address
+  };
+  std::vector<Span> spans;
+  void* map(const void* p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    for (const Span& s : spans)
+      if (a >= s.lo && a + bytes <= s.hi) return reinterpret_cast<void*>(a + s.delta);
+    if (PointerGetAttributesFn q = pointer_query()) {
+      // CU_POINTER_ATTRIBUTE_MEMORY_TYPE (2), _DEVICE_POINTER (3),
+      // _RANGE_START_ADDR (11), _RANGE_SIZE (12); CU_MEMORYTYPE_HOST = 1
+      int attrs[4] = {2, 3, 11, 12};
+      unsigned int type = 0;
+      unsigned long long dptr = 0, start = 0;
+      size_t size = 0;
+      void* data[4] = {&type, &dptr, &start, &size};
+      if (q(4, attrs, data, (unsigned long long)a) == 0 && type == 1 && dptr && size &&
+          start <= a && a - start < size) {
+        const Span s{(uintptr_t)start, (uintptr_t)start + size, (intptr_t)dptr - (intptr_t)a};
+        spans.push_back(s);
+        return a + bytes <= s.hi ? reinterpret_cast<void*>(a + s.delta) : nullptr;
+      }
+    }
+    void* d = mapped_host(p);
+    if (!d) return nullptr;
+    // the last byte must belong to the same mapping (same offset)
+    if (bytes > 1 && mapped_host(static_cast<const char*>(p) + bytes - 1) !=
+                         static_cast<char*>(d) + bytes - 1)
+      return nullptr;
+    spans.push_back({a, a + bytes, reinterpret_cast<intptr_t>(d) - (intptr_t)a});
+    return d;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int bc_relu_batch_host(bc_ctx* ctx, const bc_tensor_desc* descs, int count,
+                       const bc_batch_config* cfg) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return BC_EINVAL;
+  if (count == 0) return BC_OK;
+  BC_TRACE();
+  std::vector<bc_tensor_desc> dev(descs, descs + count);
+  HostMap hm;
+  for (bc_tensor_desc& d : dev) {
+    if (d.n == 0) continue;
+    if (d.params.ring_bits < 2 || d.params.ring_bits > 64) return BC_EINVAL;
+    const size_t bytes = d.n * lane_bytes(d.params.ring_bits);
+    const void* in[2] = {d.sh0, d.sh1};
+    void* out[2] = {d.o0, d.o1};
+    for (int q = 0; q < 2; ++q) {
+      if (!in[q] || !out[q]) return BC_EINVAL;
+      in[q] = hm.map(in[q], bytes);
+      out[q] = hm.map(out[q], bytes);
+      if (!in[q] || !out[q]) return BC_EINVAL;   // not page-locked mapped memory
+    }
+    d.sh0 = in[0];
+    d.sh1 = in[1];
+    d.o0 = out[0];
+    d.o1 = out[1];
+  }
+  int rc = bc_relu_batch_plan(ctx, dev.data(), count, cfg);
+  if (rc) return rc;
+  if ((rc = bc_relu_batch_run(ctx))) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BC_OK;
 }
 
 // ---- product -> truncations -> ReLU ---------------------------------------
@@ -756,17 +802,6 @@ bool host_canonical(const void* a, size_t n, int ring_bits) {
   return true;
 }
 
-// Device address of a host pointer that the GPU can load from and store to
-// (page-locked memory of the CUDA allocator or registered with it), else NULL.
-void* mapped_host(const void* p) {
-  if (!p) return nullptr;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
-}
 
 }  // namespace
 

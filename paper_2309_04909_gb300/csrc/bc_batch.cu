@@ -183,7 +183,37 @@ cudaError_t launch_tuned(const BatchGroup& g, const BatchTensor* tensors, const 
   }
 }
 
+// One thread per tile: the tile's tensor is the last one whose first tile is
+// at or before it (binary search over the table; empty tensors own no tiles).
+__global__ void __launch_bounds__(kBlock)
+    expand_tiles_kernel(const BatchTensor* __restrict__ tensors, uint32_t count,
+                        uint32_t ntiles, uint32_t tile, BatchTile* __restrict__ tiles) {
+  const uint32_t w = blockIdx.x * kBlock + threadIdx.x;
+  if (w >= ntiles) return;
+  uint32_t lo = 0, hi = count;   // tensors[lo].first_tile <= w < tensors[hi].first_tile
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tensors[mid].first_tile <= w) lo = mid;
+    else hi = mid;
+  }
+  const uint64_t start = (uint64_t)(w - tensors[lo].first_tile) * tile;
+  const uint64_t n = tensors[lo].n;
+  BatchTile bt;
+  bt.tensor = lo;
+  bt.start = start;
+  bt.count = (uint32_t)(n - start < (uint64_t)tile ? n - start : (uint64_t)tile);
+  tiles[w] = bt;
+}
+
 }  // namespace
+
+cudaError_t launch_expand_tiles(const BatchTensor* tensors, uint32_t count, uint32_t ntiles,
+                                uint32_t tile, BatchTile* tiles, cudaStream_t s) {
+  if (ntiles == 0 || count == 0) return cudaSuccess;
+  expand_tiles_kernel<<<(ntiles + kBlock - 1) / kBlock, kBlock, 0, s>>>(tensors, count, ntiles,
+                                                                        tile, tiles);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,
                               const BatchGroup* groups, int ngroups, unsigned int* counters,

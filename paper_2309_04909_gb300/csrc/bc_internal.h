@@ -57,6 +57,7 @@ struct BatchTensor {
   uint32_t tensor_id;
   int op;              // BC_OP_RELU / BC_OP_DRELU
   uint64_t elem_offset;  // Philox element index of element 0
+  uint32_t first_tile;   // index of the tensor's first tile in the tile table
 };
 
 struct BatchTile {
@@ -73,6 +74,90 @@ struct BatchGroup {
   uint32_t begin, end;
 };
 
+// ---- host helpers shared by the context path (bc_api.cu) and the
+// allocation-free path (bc_noalloc.cu) ----------------------------------------
+
+inline bool is_prime_u32(uint64_t q) {
+  if (q < 2) return false;
+  if (q % 2 == 0) return q == 2;
+  for (uint64_t d = 3; d * d <= q; d += 2)
+    if (q % d == 0) return false;
+  return true;
+}
+
+inline uint64_t ring_mask(int bits) {
+  return bits >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << bits) - 1);
+}
+
+// Philox-4x32-10 round keys of a 64-bit seed: key (lo32, hi32) plus the
+// Weyl increments of each round.
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return rk;
+}
+
+// Montgomery constants of p (R = 2^32).
+inline ModP make_modp(uint32_t p) {
+  ModP m;
+  m.p = p;
+  uint32_t inv = p;                      // Newton: inv = p^{-1} mod 2^32
+  for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+  m.pinv = 0u - inv;
+  const uint64_t r1 = ((uint64_t)1 << 32) % p;
+  m.r2 = (uint32_t)((r1 * r1) % p);
+  m.pm1 = p - 1;
+  return m;
+}
+
+// The last (lx, p) pairs whose p passed the primality test, so that a call
+// does not repeat the trial division (up to 2^15.5 divisions at lx = 31).
+struct PrimeCache {
+  uint32_t p[4] = {0, 0, 0, 0};
+  int lx[4] = {0, 0, 0, 0};
+  int next = 0;
+  bool prime(uint32_t q, int l) {
+    for (int i = 0; i < 4; ++i)
+      if (p[i] == q && lx[i] == l) return true;
+    if (!is_prime_u32(q)) return false;
+    p[next] = q;
+    lx[next] = l;
+    next = (next + 1) & 3;
+    return true;
+  }
+};
+
+// Checks of Alg. drelu's parameters (c + 2 lx <= l, p a prime in
+// (2^lx, 2^(lx+1)); p = 0 takes the smallest one) and the kernel constants of
+// a tensor.  BC_OK or BC_EINVAL.
+inline int make_relu_consts(const bc_drelu_params* prm, const RoundKeys& rk, uint32_t tensor_id,
+                            PrimeCache& primes, ReluConsts* k) {
+  if (!prm) return BC_EINVAL;
+  const int ell = prm->ring_bits, lx = prm->lx, c = prm->key_off;
+  if (ell < 2 || ell > 64 || lx < 1 || lx > 31 || c < 0 || c + 2 * lx > ell) return BC_EINVAL;
+  const uint32_t p = prm->p ? prm->p : bc_prime_above(lx);
+  const uint64_t lo = (uint64_t)1 << lx, hi = (uint64_t)1 << (lx + 1);
+  if ((uint64_t)p <= lo || (uint64_t)p >= hi || !primes.prime(p, lx)) return BC_EINVAL;
+  k->rk = rk;
+  k->mp = make_modp(p);
+  k->ring_mask = ring_mask(ell);
+  k->ring_bits = (uint32_t)ell;
+  k->lx = (uint32_t)lx;
+  k->c = (uint32_t)c;
+  k->mx = (uint32_t)(lo - 1);
+  k->two_lx = (uint32_t)lo;
+  k->p_minus_2lx = p - (uint32_t)lo;
+  k->tensor_id = tensor_id;
+  k->elem_base = 0;
+  return BC_OK;
+}
+
 // Host-side launchers (return cudaError_t of the launch).
 cudaError_t launch_relu(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
                         uint64_t n, void* o0, void* o1, const AuditPtrs& aud, int num_sms,
@@ -86,6 +171,12 @@ struct BatchLaunch {
   int elems_per_thread;
   int slot_unroll;
 };
+// Writes the tile table of a planned batch on the device: tiles of `tile`
+// elements, tensor by tensor in table order, tensor t's tiles starting at
+// tensors[t].first_tile (non-decreasing, tensors[0].first_tile = 0), ntiles in
+// all.  The host plans O(tensors) work; the table itself is built here.
+cudaError_t launch_expand_tiles(const BatchTensor* tensors, uint32_t count, uint32_t ntiles,
+                                uint32_t tile, BatchTile* tiles, cudaStream_t s);
 // Launches one kernel per non-empty group; for the persistent schedule
 // `counters` holds one zeroed work counter per group.
 cudaError_t launch_relu_batch(const BatchTensor* tensors, const BatchTile* tiles,

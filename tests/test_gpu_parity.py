@@ -464,3 +464,55 @@ def test_calls_follow_torch_current_stream(ctx):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(o0, want0) and torch.equal(o1, want1)
+
+
+def test_batch_host_buffers_match_device_batch(ctx):
+    """bc_relu_batch_host: the batched kernel reads and writes pinned host
+    buffers across the host link; the outputs equal the device-resident
+    batch's.  Tensors are slices of a few pinned arrays (and one tensor of its
+    own); pageable buffers are refused before anything is launched."""
+    import ctypes
+    from paper_2309_04909_gb300 import BicoptorError
+    from paper_2309_04909_gb300._native import BatchConfig, TensorDesc
+    specs = [(64, 24, 0, 23), (32, 14, 4, 17), (64, 7, 0, 6), (16, 5, 2, 6)]
+    rng = np.random.default_rng(11)
+    dev_items, host_items = [], []
+    for ring, lx, c, mag in specs:
+        sizes = [int(v) for v in rng.integers(1, 30_000, size=5)]
+        total = sum(sizes)
+        x = W.magnitude_bounded_ints(total, mag, seed=ring + lx)
+        s0, s1 = _shares(ctx, ring, x, 300 + lx)
+        h0, h1 = s0.cpu().pin_memory(), s1.cpu().pin_memory()
+        o0, o1 = ctx._empty(total, ring), ctx._empty(total, ring)
+        ho0 = torch.zeros(total, dtype=o0.dtype).pin_memory()
+        ho1 = torch.zeros(total, dtype=o0.dtype).pin_memory()
+        off = 0
+        for j, sz in enumerate(sizes):
+            sl = slice(off, off + sz)
+            tid, op = 400 + lx * 10 + j, j % 2
+            dev_items.append((Params(ring, lx, c), s0[sl], s1[sl], o0[sl], o1[sl], tid, op))
+            host_items.append((Params(ring, lx, c), h0[sl], h1[sl], ho0[sl], ho1[sl], tid, op))
+            off += sz
+    lone = torch.zeros(1000, dtype=torch.int64)
+    lone_in = lone.pin_memory()
+    lone_out0, lone_out1 = torch.zeros(1000, dtype=torch.int64).pin_memory(), \
+        torch.zeros(1000, dtype=torch.int64).pin_memory()
+    host_items.append((Params(64, 24, 0), lone_in, lone_in, lone_out0, lone_out1, 999))
+    dz = lone.cuda()
+    dev_items.append((Params(64, 24, 0), dz, dz, torch.empty_like(dz), torch.empty_like(dz), 999))
+    for sched in (1, 0):
+        ctx.relu_batch_plan(dev_items, schedule=sched)
+        ctx.relu_batch_run()
+        assert ctx.batch_status() == 0
+        ctx.relu_batch_host(host_items, schedule=sched)
+        for d, h in zip(dev_items, host_items):
+            assert torch.equal(d[3].cpu(), h[3]) and torch.equal(d[4].cpu(), h[4])
+    # a pageable buffer: the binding refuses it, and so does the C-ABI itself
+    with pytest.raises(BicoptorError):
+        ctx.relu_batch_host([(Params(64, 24, 0), lone, lone, lone_out0, lone_out1, 1)])
+    page = np.zeros(1000, dtype=np.uint64)
+    arr = (TensorDesc * 1)()
+    arr[0] = TensorDesc(page.ctypes.data, page.ctypes.data, lone_out0.data_ptr(),
+                        lone_out1.data_ptr(), 1000, 1, 0, Params(64, 24, 0).c_struct(), 0)
+    rc = ctx._lib.bc_relu_batch_host(ctx._h, arr, 1, ctypes.byref(BatchConfig(0, 0, 0, 0, 0)))
+    assert rc == -1
