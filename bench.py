@@ -39,8 +39,8 @@ WORKLOAD = ("ResNet-18 224x224 ReLU set x{images} images, once in Z_2^64 (f=16, 
 BASE_SEED = 0xB1C0_2309_0490_9000
 # DRAM bytes per element of the batched kernel over both rings: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the two launches of one step
-# of a 4-image set, divided by its elements (None until captured)
-TRAFFIC_PER_ELEM_BATCH = None
+# of a 4-image set (358.6 MB), divided by its 18,464,768 elements
+TRAFFIC_PER_ELEM_BATCH = 19.42
 # the fused step of a linear layer (reported beside the headline)
 FUSED_WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
                   "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated "
@@ -72,6 +72,10 @@ def parse():
                          "step as four launches (product, two truncations, ReLU) through HBM, "
                          "each timed; parties / rss: the ReLU of the step's truncated product "
                          "by the party-separated launches / the RSS protocol")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run the headline in the schedule the autotuner picks on GB300 (grid, "
+                         "one element per thread, key-bit unroll 2) without timing the others "
+                         "first (for profiling: no other launches precede the step's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline alone (for profiling): skip e2e, the CPU "
                          "baseline, the multiplier microbenchmark and every extra")
@@ -415,7 +419,9 @@ def headline(args, world, rank, local, dev):
     items, parts, keep, sizes = resnet18_items(ctx, dev, args.images, seed=3 + rank)
     total = sum(p[0] for p in parts)
     torch.cuda.synchronize()
-    best = autotune(ctx, items, reps=1, use_cache=False)
+    best = ({"schedule": 1, "tile_elems": 256, "ctas_per_sm": 0, "elems_per_thread": 1,
+             "slot_unroll": 2} if args.no_autotune else autotune(ctx, items, reps=1,
+                                                                  use_cache=False))
     cfg = (best["tile_elems"], best["ctas_per_sm"], best["schedule"], best["elems_per_thread"],
            best["slot_unroll"])
     b = ReluBatch(ctx, items, *cfg)
@@ -1330,67 +1336,6 @@ def uniform_l32_drelu_check(ctx, dev):
             "kernel_ms": ms, "elems_per_s": n / (ms / 1e3),
             "oracle_mismatches": parity_mismatch, "sign_mismatches": int(bad.size),
             "sign_mismatches_outside_predicted_set": int((~predicted).sum()) if bad.size else 0}
-
-
-def resnet18_batched(ctx, dev, batch=32):
-    """The ResNet-18 224x224 ReLU set for `batch` images, once at
-    l = 64 (f = 16, lx = 24) and once at l = 32 (f = 12, (lx, c) = (14, 4)),
-    Laplace(0, 2) activations: 1,088 tensors, 147,718,144 elements.  One
-    CUDA-graph-captured batched run (one launch per parameter group) vs one
-    launch per tensor (graph-replayed)."""
-    import torch
-    from paper_2309_04909_gb300 import Params, workloads as W
-    from paper_2309_04909_gb300.batch import ReluBatch, autotune
-    ts = W.resnet18_mixed_batch(batch, seed=3)
-    items, plain, keep = [], [], []
-    for ring, frac, prm in ((64, 16, Params(64, 24, 0)), (32, 12, Params(32, 14, 4))):
-        idx = [i for i in range(len(ts.sizes)) if ts.ring_bits[i] == ring]
-        allx = np.concatenate([np.rint(np.ldexp(ts.reals[i], frac)).astype(np.int64) for i in idx])
-        s0, s1 = ctx.share(ring, torch.from_numpy(allx).to(dev), tensor_id=30 + ring)
-        dt = torch.int64 if ring > 32 else torch.int32
-        o0 = torch.empty(allx.size, dtype=dt, device=dev)
-        o1 = torch.empty_like(o0)
-        q0, q1 = torch.empty_like(o0), torch.empty_like(o0)
-        keep += [s0, s1, o0, o1, q0, q1]
-        off = 0
-        for i in idx:
-            sl = slice(off, off + ts.sizes[i])
-            items.append((prm, s0[sl], s1[sl], o0[sl], o1[sl], 40000 + i))
-            plain.append((prm, s0[sl], s1[sl], q0[sl], q1[sl], 40000 + i))
-            off += ts.sizes[i]
-        del allx
-    total = ts.total
-    ts.reals = None
-
-    def run_plain():
-        for it in plain:
-            ctx.relu(it[0], it[1], it[2], it[5], out=(it[3], it[4]))
-
-    run_plain()
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        run_plain()
-    plain_ms = median_ms(g.replay)
-    best = autotune(ctx, items, reps=1, use_cache=False)
-    b = ReluBatch(ctx, items, best["tile_elems"], best["ctas_per_sm"], best["schedule"],
-                  best["elems_per_thread"], best["slot_unroll"])
-    b.capture()
-    batched_ms = median_ms(b.run)
-    identical = all(torch.equal(a[3], p[3]) and torch.equal(a[4], p[4])
-                    for a, p in zip(items, plain))
-    return {"workload": f"ResNet-18 224x224 ReLU set x{batch} at l=64 and l=32: "
-                        f"{len(items)} tensors, {total} elements",
-            "plain_graph_ms": plain_ms, "batched_graph_ms": batched_ms,
-            "speedup_vs_plain_graph": plain_ms / batched_ms,
-            "batched_elems_per_s": total / (batched_ms / 1e3),
-            "batched_roofline_frac": batched_frac([(total // 2, 64, 24), (total // 2, 32, 14)],
-                                                  batched_ms),
-            "schedule": "grid" if best["schedule"] == 1 else "persistent",
-            "tile_elems": best["tile_elems"], "ctas_per_sm": best["ctas_per_sm"],
-            "elems_per_thread": best["elems_per_thread"], "slot_unroll": best["slot_unroll"],
-            "timing": "median of 20 runs, CUDA events per run, after 3 warm-up runs",
-            "status": b.status(), "identical_to_plain": bool(identical)}
 
 
 def serving_only(args):
