@@ -227,6 +227,36 @@ int bc_drelu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, c
                      size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
 int bc_relu_parties(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
                     size_t n, uint32_t tensor_id, void *o0, void *o1, const bc_party_msgs *msgs);
+/* One party's stage of the same protocol, for callers that run P0, P1 and P2
+ * as separate processes (each with its own context, possibly on its own GPU)
+ * and move the messages between them (Alg. drelu steps 8-10, Alg. relu).
+ * Every buffer is a device pointer in the memory of the party that runs the
+ * stage; a message written by the sender's stage must be copied into the
+ * receiver's buffer before the receiver's stage runs.  Layouts as in
+ * bc_party_msgs (w: bc_party_msg_words(lx, n) words, 16-byte aligned for P2).
+ *   bc_party_local   P0 (party 0) or P1 (party 1): steps 1-8 from its own share
+ *                    [x]_party, expanding seed01 itself; writes its packed w
+ *                    message to P2 and, for ReLU (relu != 0), its opening
+ *                    [x]_party - [a]_party to the other party (`open`)
+ *   bc_party_helper  P2: step 9 on both w messages; writes `reply` ([DReLU']_1
+ *                    for P1 in DReLU, e = DReLU' - b for P0 and P1 in ReLU) and,
+ *                    for ReLU, the preprocessing [c]_1 for P1 (`pre_c1`)
+ *   bc_party_finish  P0 or P1: step 11 (DReLU: P0 needs no message, P1 the
+ *                    reply) or the Beaver finish (ReLU: its own share, e,
+ *                    both openings and, for P1, [c]_1); writes its output share
+ * The outputs equal bc_drelu_parties / bc_relu_parties.  Each stage counts in
+ * bc_comm the bits its party sends; P2's stage also counts the call's rounds,
+ * elements and calls, so that the three contexts' counters add up to the
+ * single-process call's. */
+int bc_party_local(bc_ctx *ctx, int party, const bc_drelu_params *prm, int relu,
+                   const void *share, size_t n, uint32_t tensor_id, uint32_t *w, void *open);
+int bc_party_helper(bc_ctx *ctx, const bc_drelu_params *prm, int relu, size_t n,
+                    uint32_t tensor_id, const uint32_t *w0, const uint32_t *w1, void *reply,
+                    void *pre_c1);
+int bc_party_finish(bc_ctx *ctx, int party, const bc_drelu_params *prm, int relu,
+                    const void *share, size_t n, uint32_t tensor_id, const void *reply,
+                    const void *open0, const void *open1, const void *pre_c1, void *out);
+
 /* P2's kernel waits (at most 50 ms) for the bulk copies of its messages.
  * BC_OK, or BC_ETIMEOUT if that wait gave up in a party-separated call since
  * the last read (that call's outputs are then undefined).  Synchronises the

@@ -327,6 +327,51 @@ class Context:
     def relu_parties(self, prm: Params, s0, s1, tensor_id: int, out=None, msgs=None):
         return self._parties(self._lib.bc_relu_parties, prm, s0, s1, tensor_id, out, msgs)
 
+    # -- one party's stage (parties in separate processes; see parties.py) -------
+    def party_stage_buffers(self, prm: Params, n: int) -> Dict[str, torch.Tensor]:
+        """This party's buffers for one party-separated call: its packed w
+        message ("w", also the size of a received one), its opening, the
+        reply and [c]_1 it receives, and its output share."""
+        words = int(self._lib.bc_party_msg_words(prm.lx, n))
+        d = {"w": torch.empty(words, dtype=torch.int32, device=self.device)}
+        for k in ("open", "reply", "pre_c1", "out"):
+            d[k] = self._empty(n, prm.ring_bits)
+        return d
+
+    def party_local(self, party: int, prm: Params, relu: bool, share, tensor_id: int, buf):
+        """bc_party_local: P0 (party 0) or P1 (party 1), steps 1-8 from its own
+        share; returns (its packed w message, its opening or None)."""
+        self._need(share, prm.ring_bits, "share")
+        w, opn = buf["w"], (buf["open"] if relu else None)
+        self._sync_stream()
+        self._check(self._lib.bc_party_local(self._h, party, ctypes.byref(prm.c_struct()),
+                                             int(relu), _ptr(share), share.numel(), tensor_id,
+                                             _ptr(w), _ptr(opn)))
+        return w, opn
+
+    def party_helper(self, prm: Params, relu: bool, tensor_id: int, w0, w1, buf):
+        """bc_party_helper: P2's step 9 on the two received w messages;
+        returns (reply, [c]_1 or None)."""
+        n = buf["reply"].numel()
+        reply, pre = buf["reply"], (buf["pre_c1"] if relu else None)
+        self._sync_stream()
+        self._check(self._lib.bc_party_helper(self._h, ctypes.byref(prm.c_struct()), int(relu), n,
+                                              tensor_id, _ptr(w0), _ptr(w1), _ptr(reply),
+                                              _ptr(pre)))
+        return reply, pre
+
+    def party_finish(self, party: int, prm: Params, relu: bool, share, tensor_id: int, reply,
+                     open0, open1, pre_c1, buf):
+        """bc_party_finish: P0 or P1 finishes from the messages it received;
+        returns its output share."""
+        out = buf["out"]
+        self._sync_stream()
+        self._check(self._lib.bc_party_finish(self._h, party, ctypes.byref(prm.c_struct()),
+                                              int(relu), _ptr(share), out.numel(), tensor_id,
+                                              _ptr(reply), _ptr(open0), _ptr(open1),
+                                              _ptr(pre_c1), _ptr(out)))
+        return out
+
     def parties_status(self) -> int:
         """0, or BC_ETIMEOUT (-4) if P2's bounded wait for its messages gave up
         in a party-separated call since the last read; synchronises, clears."""

@@ -155,6 +155,12 @@ SIGNATURES = {
     "bc_set_audit": (c_int, [c_void_p, P(Audit)]),
     "bc_get_comm": (c_int, [c_void_p, P(Comm)]),
     "bc_reset_comm": (c_int, [c_void_p]),
+    "bc_party_local": (c_int, [c_void_p, c_int, P(DreluParams), c_int, c_void_p, c_size, c_u32,
+                               c_void_p, c_void_p]),
+    "bc_party_helper": (c_int, [c_void_p, P(DreluParams), c_int, c_size, c_u32, c_void_p,
+                                c_void_p, c_void_p, c_void_p]),
+    "bc_party_finish": (c_int, [c_void_p, c_int, P(DreluParams), c_int, c_void_p, c_size, c_u32,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bc_relu_batch_plan": (c_int, [c_void_p, P(TensorDesc), c_int, P(BatchConfig)]),
     "bc_relu_batch_run": (c_int, [c_void_p]),
     "bc_relu_batch": (c_int, [c_void_p, P(TensorDesc), c_int, P(BatchConfig)]),

@@ -470,6 +470,93 @@ int bc_relu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, co
   return run_parties(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, m, true);
 }
 
+// ---- one party's stage --------------------------------------------------------
+
+static int stage_consts(bc_ctx* ctx, const bc_drelu_params* prm, uint32_t tensor_id,
+                        bc::ReluConsts* k) {
+  if (!ctx) return BC_EINVAL;
+  return make_consts(ctx, prm, tensor_id, k);
+}
+
+int bc_party_local(bc_ctx* ctx, int party, const bc_drelu_params* prm, int relu,
+                   const void* share, size_t n, uint32_t tensor_id, uint32_t* w, void* open) {
+  bc::ReluConsts k;
+  int rc = stage_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  if (party != 0 && party != 1) return BC_EINVAL;
+  if (n && (!share || !w || (relu && !open))) return BC_EINVAL;
+  BC_TRACE();
+  if ((rc = check_canonical(ctx, prm->ring_bits, {share}, n))) return rc;
+  bc::PartyIo io{};
+  io.sh[party] = share;
+  io.w[party] = w;
+  io.open[party] = open;
+  if (n)
+    CK(bc::launch_party_stage(k, relu != 0, 1, party, io, n, ctx->d_party_status,
+                              ctx->drop_p2_copies, ctx->stream));
+  const bc_comm full = relu_comm(prm->ring_bits, prm->lx, n, relu != 0);
+  bc_comm mine{};
+  (party == 0 ? mine.p0_to_p2 : mine.p1_to_p2) = full.p0_to_p2;
+  if (relu) (party == 0 ? mine.p0_to_p1 : mine.p1_to_p0) = full.p0_to_p1;
+  add_comm(&ctx->comm, mine);
+  return BC_OK;
+}
+
+int bc_party_helper(bc_ctx* ctx, const bc_drelu_params* prm, int relu, size_t n,
+                    uint32_t tensor_id, const uint32_t* w0, const uint32_t* w1, void* reply,
+                    void* pre_c1) {
+  bc::ReluConsts k;
+  int rc = stage_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  if (n && (!w0 || !w1 || !reply || (relu && !pre_c1))) return BC_EINVAL;
+  // P2 fetches the packed messages with bulk copies: 16-byte aligned buffers
+  if (n && ((((uintptr_t)w0) | ((uintptr_t)w1)) & 15u)) return BC_EINVAL;
+  BC_TRACE();
+  bc::PartyIo io{};
+  io.w[0] = const_cast<uint32_t*>(w0);
+  io.w[1] = const_cast<uint32_t*>(w1);
+  io.reply = reply;
+  io.pre_c1 = pre_c1;
+  if (n)
+    CK(bc::launch_party_stage(k, relu != 0, 2, 2, io, n, ctx->d_party_status,
+                              ctx->drop_p2_copies, ctx->stream));
+  const bc_comm full = relu_comm(prm->ring_bits, prm->lx, n, relu != 0);
+  bc_comm mine{};
+  mine.p2_to_p0 = full.p2_to_p0;
+  mine.p2_to_p1 = full.p2_to_p1;
+  mine.pre_p2_to_p1 = full.pre_p2_to_p1;
+  mine.rounds = full.rounds;     // the call's rounds, elements and calls are counted once,
+  mine.elements = full.elements; // by P2, so that the three parties' counters add up to
+  mine.calls = full.calls;       // the single-process call's
+  add_comm(&ctx->comm, mine);
+  return BC_OK;
+}
+
+int bc_party_finish(bc_ctx* ctx, int party, const bc_drelu_params* prm, int relu,
+                    const void* share, size_t n, uint32_t tensor_id, const void* reply,
+                    const void* open0, const void* open1, const void* pre_c1, void* out) {
+  bc::ReluConsts k;
+  int rc = stage_consts(ctx, prm, tensor_id, &k);
+  if (rc) return rc;
+  if (party != 0 && party != 1) return BC_EINVAL;
+  if (n && !out) return BC_EINVAL;
+  if (n && !relu && party == 1 && !reply) return BC_EINVAL;
+  if (n && relu && (!share || !reply || !open0 || !open1 || (party == 1 && !pre_c1)))
+    return BC_EINVAL;
+  BC_TRACE();
+  bc::PartyIo io{};
+  io.sh[party] = share;
+  io.out[party] = out;
+  io.open[0] = const_cast<void*>(open0);
+  io.open[1] = const_cast<void*>(open1);
+  io.reply = const_cast<void*>(reply);
+  io.pre_c1 = const_cast<void*>(pre_c1);
+  if (n)
+    CK(bc::launch_party_stage(k, relu != 0, 3, party, io, n, ctx->d_party_status,
+                              ctx->drop_p2_copies, ctx->stream));
+  return BC_OK;
+}
+
 int bc_parties_status(bc_ctx* ctx) {
   if (!ctx) return BC_EINVAL;
   int st = 0;

@@ -218,6 +218,22 @@ cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, cons
                            void* open0, void* open1, void* reply, void* pre_c1, int* status,
                            bool drop_copies, cudaStream_t s);
 
+// One stage of a party-separated call run by one party (P0 or P1 for stages
+// 1 and 3, P2 for stage 2), for callers that keep the parties in separate
+// processes and move the messages between the stages themselves.  Only the
+// buffers of that party's stage are read or written.
+struct PartyIo {
+  const void* sh[2];
+  void* out[2];
+  uint32_t* w[2];
+  void* open[2];
+  void* reply;
+  void* pre_c1;
+};
+cudaError_t launch_party_stage(const ReluConsts& k, bool relu, int stage, int party,
+                               const PartyIo& io, uint64_t n, int* status, bool drop_copies,
+                               cudaStream_t s);
+
 cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
                          uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,
                          cudaStream_t s);

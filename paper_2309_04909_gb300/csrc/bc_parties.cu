@@ -175,6 +175,8 @@ __device__ __forceinline__ void pack_group(const uint32_t* vals, uint32_t L, uin
   }
 }
 
+constexpr uint32_t kBothParties = 0xffffffffu;   // PartyArgs::party0: P0 and P1 in one launch
+
 struct PartyArgs {
   ReluConsts k;
   const void* sh[2];        // [x]_0 (P0's input), [x]_1 (P1's input)
@@ -187,6 +189,8 @@ struct PartyArgs {
   int* status;              // set to BC_ETIMEOUT if P2 gives up waiting
   uint32_t drop_copies;     // test hook: P2 issues no copies, so its wait runs out
   uint64_t wait_ns;         // P2's wait limit
+  uint32_t party0;          // launches 1 and 3: party of blockIdx.y = 0 (grid y = 2 - party0
+                            // for both parties from 0, 1 for one party alone)
 };
 
 // ---- launch 1: P0 and P1, steps 1-8 (+ opening of x - a) --------------------
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kPB)
   __shared__ uint32_t perm_s[kMaxSlots * kPB];
   __shared__ uint64_t r2_s[kMaxSlots];
   fill_round2(r2_s, a.k.tensor_id, a.k.rk);
-  const uint32_t party = blockIdx.y;
+  const uint32_t party = a.party0 + blockIdx.y;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
   const bool valid = i < a.n;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(kPB)
   __shared__ uint64_t r2_s[2];
   if (threadIdx.x < 2) r2_s[threadIdx.x] = round2_product(a.k.tensor_id, threadIdx.x, a.k.rk);
   __syncthreads();
-  const uint32_t party = blockIdx.y;
+  const uint32_t party = a.party0 + blockIdx.y;
   const uint64_t i = (uint64_t)blockIdx.x * kPB + threadIdx.x;
   if (i >= a.n) return;
   const ReluConsts& k = a.k;
@@ -395,26 +399,37 @@ inline size_t helper_smem_bytes(uint32_t lx) {
 }
 
 template <typename Lane, bool RELU>
-cudaError_t launch_parties_t(const PartyArgs& a, cudaStream_t s) {
+cudaError_t launch_stage_t(const PartyArgs& a, int stage, cudaStream_t s) {
   const uint64_t blocks = (a.n + kPB - 1) / kPB;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-  // above 48 KB (lx >= 27) the kernel needs the opt-in, which is per device:
-  // set it on the current device at each such launch
-  const size_t smem = helper_smem_bytes(a.k.lx);
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        helper_kernel<Lane, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  const unsigned parties = a.party0 == kBothParties ? 2u : 1u;
+  PartyArgs b = a;
+  if (a.party0 == kBothParties) b.party0 = 0;
+  if (stage == 1) {
+    parties_local_kernel<Lane, RELU><<<dim3((unsigned)blocks, parties), kPB, 0, s>>>(b);
+  } else if (stage == 2) {
+    // above 48 KB (lx >= 27) the kernel needs the opt-in, which is per device:
+    // set it on the current device at each such launch
+    const size_t smem = helper_smem_bytes(a.k.lx);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          helper_kernel<Lane, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, smem, s>>>(b);
+  } else {
+    parties_finish_kernel<Lane, RELU><<<dim3((unsigned)blocks, parties), kPB, 0, s>>>(b);
   }
-  parties_local_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  helper_kernel<Lane, RELU><<<(unsigned)blocks, kPB, smem, s>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  parties_finish_kernel<Lane, RELU><<<dim3((unsigned)blocks, 2), kPB, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const PartyArgs& a, bool relu, int stage, cudaStream_t s) {
+  if (a.k.ring_bits > 32)
+    return relu ? launch_stage_t<uint64_t, true>(a, stage, s)
+                : launch_stage_t<uint64_t, false>(a, stage, s);
+  return relu ? launch_stage_t<uint32_t, true>(a, stage, s)
+              : launch_stage_t<uint32_t, false>(a, stage, s);
 }
 
 }  // namespace
@@ -428,7 +443,7 @@ cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, cons
                            uint64_t n, void* o0, void* o1, uint32_t* w0, uint32_t* w1,
                            void* open0, void* open1, void* reply, void* pre_c1, int* status,
                            bool drop_copies, cudaStream_t s) {
-  PartyArgs a;
+  PartyArgs a{};
   a.k = k;
   a.sh[0] = sh0;
   a.sh[1] = sh1;
@@ -444,9 +459,35 @@ cudaError_t launch_parties(const ReluConsts& k, bool relu, const void* sh0, cons
   a.status = status;
   a.drop_copies = drop_copies ? 1u : 0u;
   a.wait_ns = drop_copies ? kTestWaitNs : kWaitNs;
-  if (k.ring_bits > 32)
-    return relu ? launch_parties_t<uint64_t, true>(a, s) : launch_parties_t<uint64_t, false>(a, s);
-  return relu ? launch_parties_t<uint32_t, true>(a, s) : launch_parties_t<uint32_t, false>(a, s);
+  a.party0 = kBothParties;
+  for (int stage = 1; stage <= 3; ++stage) {
+    const cudaError_t e = launch_stage(a, relu, stage, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_party_stage(const ReluConsts& k, bool relu, int stage, int party,
+                               const PartyIo& io, uint64_t n, int* status, bool drop_copies,
+                               cudaStream_t s) {
+  PartyArgs a{};
+  a.k = k;
+  a.sh[0] = io.sh[0];
+  a.sh[1] = io.sh[1];
+  a.out[0] = io.out[0];
+  a.out[1] = io.out[1];
+  a.w[0] = io.w[0];
+  a.w[1] = io.w[1];
+  a.open[0] = io.open[0];
+  a.open[1] = io.open[1];
+  a.reply = io.reply;
+  a.pre_c1 = io.pre_c1;
+  a.n = n;
+  a.status = status;
+  a.drop_copies = drop_copies ? 1u : 0u;
+  a.wait_ns = drop_copies ? kTestWaitNs : kWaitNs;
+  a.party0 = (uint32_t)party;
+  return launch_stage(a, relu, stage, s);
 }
 
 }  // namespace bc

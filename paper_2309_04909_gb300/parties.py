@@ -1,0 +1,140 @@
+"""P0, P1 and P2 as separate processes (Alg. drelu, Alg. relu of the UBL
+protocol, each party on its own context and, with NCCL, its own GPU).
+
+Every party runs only its own stages of the party-separated protocol
+(bc_party_local / bc_party_helper / bc_party_finish) and every message is
+moved into the receiver's own memory before the receiver's stage reads it:
+
+  round 1   P0 -> P2  w0 (packed, (lx+1)^2 bits per element)
+            P1 -> P2  w1
+            P0 <-> P1 the openings [x]_j - [a]_j                     (ReLU)
+  round 2   P2 -> P1  reply: [DReLU']_1 (DReLU) / e = DReLU' - b (ReLU)
+            P2 -> P0  e                                              (ReLU)
+            P2 -> P1  [c]_1, the preprocessing of the triple         (ReLU)
+
+The transport is torch.distributed point-to-point: with NCCL (one process per
+GPU) device tensors go straight into the receiver's device memory; with gloo
+they travel through host memory (sender copies to the host, receiver copies
+its received host buffer to its device).  No kernel of one party waits on
+another party: each stage is launched only once its inputs have arrived.
+The pre-shared seeds of Sec. 2.1 are the contexts' common 64-bit seed.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, Optional, Tuple
+
+import torch
+import torch.distributed as dist
+
+P0, P1, P2 = 0, 1, 2
+# message tags (one per message kind, so that the order of different kinds
+# between the same two parties never matters)
+TAG_W, TAG_OPEN, TAG_REPLY, TAG_PRE = 11, 12, 13, 14
+
+
+class Transport:
+    """Point-to-point messages between the parties' ranks.  `direct`: the
+    backend carries device tensors (NCCL); otherwise (gloo) messages are
+    staged through host memory.  Bytes are counted per (sender, receiver)."""
+
+    def __init__(self, device: torch.device, direct: bool, ranks=(0, 1, 2)):
+        self.device = device
+        self.direct = direct
+        self.ranks = ranks
+        self.sent: Dict[Tuple[int, int], int] = {}
+
+    def _rank(self, party: int) -> int:
+        return self.ranks[party]
+
+    def isend(self, t: torch.Tensor, src: int, dst: int, tag: int):
+        self.sent[(src, dst)] = self.sent.get((src, dst), 0) + t.numel() * t.element_size()
+        payload = t if self.direct else t.cpu()
+        return dist.isend(payload.contiguous(), self._rank(dst), tag=tag), payload
+
+    def irecv(self, like: torch.Tensor, src: int, tag: int):
+        buf = torch.empty_like(like) if self.direct else torch.empty(like.shape, dtype=like.dtype)
+        return dist.irecv(buf, self._rank(src), tag=tag), buf
+
+    def to_device(self, buf: torch.Tensor) -> torch.Tensor:
+        return buf if self.direct else buf.to(self.device, non_blocking=False)
+
+
+def wait_all(reqs):
+    for r in reqs:
+        r.wait()
+
+
+@dataclasses.dataclass
+class Stages:
+    """The three stage calls of one party (a Context's bc_party_* entry
+    points); tests may substitute their own."""
+    local: object
+    helper: object
+    finish: object
+    buffers: object
+
+
+def context_stages(ctx) -> Stages:
+    return Stages(ctx.party_local, ctx.party_helper, ctx.party_finish, ctx.party_stage_buffers)
+
+
+class PartyProcess:
+    """One party of the protocol.  run() is called by all three processes
+    with the same parameters; P0 and P1 pass their own share, P2 passes
+    None.  Returns the party's output share (None for P2)."""
+
+    def __init__(self, party: int, stages: Stages, transport: Transport):
+        if party not in (P0, P1, P2):
+            raise ValueError("party must be 0, 1 or 2")
+        self.party = party
+        self.s = stages
+        self.tr = transport
+
+    def run(self, prm, relu: bool, share: Optional[torch.Tensor], n: int,
+            tensor_id: int) -> Optional[torch.Tensor]:
+        buf = self.s.buffers(prm, n)
+        if self.party == P2:
+            return self._helper(prm, relu, n, tensor_id, buf)
+        return self._p01(prm, relu, share, n, tensor_id, buf)
+
+    def _p01(self, prm, relu, share, n, tid, buf):
+        me, other = self.party, 1 - self.party
+        w, opn = self.s.local(me, prm, relu, share, tid, buf)
+        # round 1: w to P2; the openings between P0 and P1
+        reqs = [self.tr.isend(w, me, P2, TAG_W)[0]]
+        keep = []
+        opens = [None, None]
+        if relu:
+            r, payload = self.tr.isend(opn, me, other, TAG_OPEN)
+            reqs.append(r)
+            keep.append(payload)
+            rr, ob = self.tr.irecv(opn, other, TAG_OPEN)
+            reqs.append(rr)
+        # round 2: what P2 sends back
+        rrep, rep = self.tr.irecv(buf["reply"], P2, TAG_REPLY) if (relu or me == P1) else (None,
+                                                                                          None)
+        rpre, pre = self.tr.irecv(buf["pre_c1"], P2, TAG_PRE) if (relu and me == P1) else (None,
+                                                                                          None)
+        wait_all([r for r in reqs + [rrep, rpre] if r is not None])
+        if relu:
+            opens[me], opens[other] = opn, self.tr.to_device(ob)
+        reply = self.tr.to_device(rep) if rep is not None else None
+        pre_c1 = self.tr.to_device(pre) if pre is not None else None
+        return self.s.finish(me, prm, relu, share, tid, reply, opens[0], opens[1], pre_c1, buf)
+
+    def _helper(self, prm, relu, n, tid, buf):
+        r0, w0 = self.tr.irecv(buf["w"], P0, TAG_W)
+        r1, w1 = self.tr.irecv(buf["w"], P1, TAG_W)
+        wait_all([r0, r1])
+        reply, pre_c1 = self.s.helper(prm, relu, tid, self.tr.to_device(w0),
+                                      self.tr.to_device(w1), buf)
+        reqs, keep = [], []
+        for dst, t, tag in ([(P1, reply, TAG_REPLY)] if not relu else
+                            [(P0, reply, TAG_REPLY), (P1, reply, TAG_REPLY),
+                             (P1, pre_c1, TAG_PRE)]):
+            r, payload = self.tr.isend(t, P2, dst, tag)
+            reqs.append(r)
+            keep.append(payload)
+        wait_all(reqs)
+        return None

@@ -117,3 +117,81 @@ def test_parties_empty_input():
     assert p0.numel() == 0 and p1.numel() == 0
     assert ctx.parties_status() == 0
     ctx.close()
+
+
+# ---- P0, P1 and P2 as three processes (gloo through host memory, one GPU) ----
+
+THREE_SEED = 0x3B0C_E550
+
+
+def _three_worker(rank, port, out_dir, cases):
+    import os as _os
+    import torch.distributed as dist
+    from paper_2309_04909_gb300 import Context, Params, workloads as W
+    from paper_2309_04909_gb300.parties import PartyProcess, Transport, context_stages
+    _os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=3)
+    torch.cuda.set_device(0)
+    ctx = Context(THREE_SEED)
+    res = {}
+    for ci, (ring, lx, c, mag, n, relu) in enumerate(cases):
+        prm = Params(ring, lx, c)
+        # the dealer's shares (every process derives the same ones; each party
+        # keeps its own)
+        x = W.magnitude_bounded_ints(n, mag, seed=ci)
+        s0, s1 = ctx.share(ring, torch.from_numpy(x).cuda(), 50 + ci)
+        share = (s0, s1, None)[rank]
+        tr = Transport(torch.device("cuda", 0), direct=False)
+        ctx.reset_comm()
+        out = PartyProcess(rank, context_stages(ctx), tr).run(prm, relu, share, n, 60 + ci)
+        torch.cuda.synchronize()
+        res[ci] = (None if out is None else out.cpu().numpy(), dict(tr.sent), ctx.comm())
+    np.save(_os.path.join(out_dir, f"p{rank}.npy"), np.array([res], dtype=object),
+            allow_pickle=True)
+    dist.barrier()
+    dist.destroy_process_group()
+    ctx.close()
+
+
+def test_three_processes_match_fused_and_oracle(tmp_path):
+    """Each party in its own process and context: P0 and P1 send their
+    packed w messages to P2 (and their openings to each other), P2 replies;
+    every message moves through the transport into the receiver's memory.
+    The output shares equal the fused kernel's and the oracle's bit for bit,
+    and the three contexts' bit counters add up to the fused call's."""
+    import socket
+    import torch.multiprocessing as mp
+    cases = [(64, 24, 0, 23, 10_007, True), (64, 24, 0, 23, 5_000, False),
+             (32, 14, 4, 17, 3_001, True), (32, 9, 14, 22, 777, False), (64, 7, 0, 6, 1, True)]
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    mp.start_processes(_three_worker, args=(port, str(tmp_path), cases), nprocs=3, join=True,
+                       start_method="spawn")
+    r = [np.load(tmp_path / f"p{k}.npy", allow_pickle=True)[0] for k in range(3)]
+    ctx = Context(THREE_SEED)
+    for ci, (ring, lx, c, mag, n, relu) in enumerate(cases):
+        prm = Params(ring, lx, c)
+        x = W.magnitude_bounded_ints(n, mag, seed=ci)
+        s0, s1 = ctx.share(ring, torch.from_numpy(x).cuda(), 50 + ci)
+        ctx.reset_comm()
+        f0, f1 = (ctx.relu if relu else ctx.drelu)(prm, s0, s1, tensor_id=60 + ci)
+        fused_comm = ctx.comm()
+        assert np.array_equal(r[0][ci][0], f0.cpu().numpy()), ci
+        assert np.array_equal(r[1][ci][0], f1.cpu().numpy()), ci
+        es0, es1 = O.share(ring, masked(x, ring), THREE_SEED, 50 + ci)
+        e0, e1 = (O.relu if relu else O.drelu)(O.params(ring, lx, c), es0, es1, THREE_SEED,
+                                                60 + ci, threads=8)
+        assert np.array_equal(r[0][ci][0].view(np.uint64 if ring > 32 else np.uint32)
+                              .astype(np.uint64), e0)
+        assert np.array_equal(r[1][ci][0].view(np.uint64 if ring > 32 else np.uint32)
+                              .astype(np.uint64), e1)
+        total = {k: sum(r[p][ci][2][k] for p in range(3)) for k in fused_comm}
+        assert total == fused_comm, (ci, total, fused_comm)
+        # bytes moved: the padded packed w buffers to P2, the ring lanes back
+        wbytes = 4 * ctx._lib.bc_party_msg_words(lx, n)
+        lane = 8 if ring > 32 else 4
+        assert r[0][ci][1][(0, 2)] == wbytes and r[1][ci][1][(1, 2)] == wbytes
+        assert r[2][ci][1][(2, 1)] == (2 if relu else 1) * n * lane
+    ctx.close()
