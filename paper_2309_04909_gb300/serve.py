@@ -146,6 +146,11 @@ class ServeStats:
     rejected: int = 0
     expired: int = 0
     cancelled: int = 0
+    # the queue when the last request arrives: requests waiting for admission
+    # or admitted and unfinished, and the elements finished by then
+    arrival_end_s: float = 0.0
+    backlog_at_arrival_end: int = 0
+    elements_by_arrival_end: int = 0
 
     def summary(self) -> Dict[str, float]:
         lat = sorted(self.latencies_s)
@@ -173,14 +178,22 @@ class ServeStats:
                 "latency_histogram_ms": hist,
                 "iterations": self.iterations, "peak_bytes": self.peak_bytes,
                 "max_waiting": self.max_waiting, "rejected": self.rejected,
-                "expired": self.expired, "cancelled": self.cancelled}
+                "expired": self.expired, "cancelled": self.cancelled,
+                "arrival_end_s": self.arrival_end_s,
+                "backlog_at_arrival_end": self.backlog_at_arrival_end,
+                "queue_growth_per_s": (self.backlog_at_arrival_end / self.arrival_end_s
+                                       if self.arrival_end_s > 0 else 0.0),
+                "elems_per_s_during_arrivals": (self.elements_by_arrival_end
+                                                / self.arrival_end_s
+                                                if self.arrival_end_s > 0 else 0.0),
+                "drain_s": self.wall_s - self.arrival_end_s}
 
 
 class Engine:
     """Continuous-batching scheduler (host side; the executor runs the GPU)."""
 
     def __init__(self, executor: Executor, budget_bytes: int, max_iter_elems: int = 1 << 24,
-                 max_inflight: int = 2, min_chunk: int = 1 << 16, max_share: int = 32):
+                 max_inflight: int = 2, min_chunk: int = 1 << 16, max_share: int = 8):
         self.ex = executor
         self.arena = Arena(budget_bytes)
         self.max_iter_elems = max_iter_elems
@@ -231,6 +244,7 @@ class Engine:
         inflight: Deque[Tuple[object, List[Chunk]]] = collections.deque()
         out_b = self.ex.bytes_per_element
         iterations, max_waiting, done_elems, rejected = 0, 0, 0, 0
+        arrival_end, backlog_end, elems_end = 0.0, 0, 0
         t0 = self.ex.now()
         while pending or waiting or active or inflight:
             now = self.ex.now() - t0
@@ -241,6 +255,11 @@ class Engine:
                     rejected += 1
                 else:
                     waiting.append(r)
+                if not pending:          # the last arrival: note the queue
+                    arrival_end = r.arrival_s
+                    backlog_end = len(waiting) + sum(1 for a in active
+                                                     if a.finished_s is None)
+                    elems_end = done_elems
             max_waiting = max(max_waiting, len(waiting))
             # client limits: drop queued requests at once; an admitted one
             # stops getting chunks and is freed when its chunks in flight retire
@@ -301,7 +320,8 @@ class Engine:
         expired = sum(1 for r in requests if r.dropped == "expired" and r.finished_s is None)
         cancelled = sum(1 for r in requests if r.dropped == "cancelled" and r.finished_s is None)
         return ServeStats(len(requests), len(lat), done_elems, wall, lat, iterations,
-                          self.arena.peak, max_waiting, rejected, expired, cancelled)
+                          self.arena.peak, max_waiting, rejected, expired, cancelled,
+                          arrival_end, backlog_end, elems_end)
 
 
 # ---------------------------------------------------------------------------

@@ -151,6 +151,13 @@ def test_engine_under_load_simulated():
     assert abs(half["elems_per_s"] / (0.5 * cap) - 1) < 0.15
     assert over["elems_per_s"] > 0.95 * cap                   # saturated
     assert over["p50_ms"] > 20 * half["p50_ms"] and over["max_waiting"] > 100
+    # the queue at the last arrival: it grows at about the excess arrival
+    # rate above capacity, and finishing it takes a while; below capacity it
+    # stays a handful of requests and drains at once
+    excess = (1.2 - 1.0) * cap / mean                        # requests per second
+    assert 0.5 * excess < over["queue_growth_per_s"] < 1.5 * excess
+    assert over["drain_s"] > 0.1 and over["elems_per_s_during_arrivals"] > 0.95 * cap
+    assert half["backlog_at_arrival_end"] < 20 and half["drain_s"] < 0.05
 
 
 def test_latency_histogram():
