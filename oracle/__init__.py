@@ -29,6 +29,7 @@ _lib = None
 PAIR_01, PAIR_02, PAIR_12, PAIR_DEALER, PAIR_012, PAIR_2 = 0x01, 0x02, 0x12, 0xDE, 0x03, 0x20
 PUR_SHARE, PUR_PERM, PUR_MASK, PUR_REPLY, PUR_RELU_TRIPLE, PUR_MUL_TRIPLE, PUR_ABY3 = (
     1, 2, 3, 4, 5, 6, 7)
+PUR_B1_MASK = 12
 
 
 def build(force: bool = False) -> str:
@@ -292,3 +293,41 @@ def rss_drelu(P, x0, x1, x2, seed, tid, relu=False, idx=None, threads=1):
     if rc != 0:
         raise ValueError("oracle rejected the parameters")
     return y0, y1, y2, dp
+
+
+def b1(P, s0, s1, seed, tid, relu=False, idx=None, msgs=False, threads=1):
+    """The Bicoptor 1.0-style DReLU (relu=False) or ReLU: SecureML truncations
+    in Z_{2^l}, recursive sums, masking by odd units and the zero test in
+    Z_{2^l}.  Returns (o0, o1) or, with msgs, (o0, o1, w0, w1, dprime) where
+    w0/w1 are (n, lx+1) ring elements."""
+    s0, s1 = _u64(s0), _u64(s1)
+    n = s0.size
+    idx = None if idx is None else _u64(idx)
+    o0, o1 = np.empty_like(s0), np.empty_like(s1)
+    L = P.lx + 1
+    w0 = np.empty((n, L), np.uint64) if msgs else None
+    w1 = np.empty((n, L), np.uint64) if msgs else None
+    dp = np.empty(n, np.uint8) if msgs else None
+    rc = lib().orc_b1(ctypes.byref(P), int(relu), _p(s0), _p(s1), _p(idx), ctypes.c_size_t(n),
+                      ctypes.c_uint64(seed), ctypes.c_uint32(tid), _p(o0), _p(o1), _p(w0), _p(w1),
+                      _p(dp), threads)
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters")
+    return (o0, o1, w0, w1, dp) if msgs else (o0, o1)
+
+
+def drelu_b1_core_many(P: _Params, s0, s1, t, fy, r, z):
+    """Steps 1-9 of the 1.0-style protocol with explicit randomness: fy
+    (n, lx+1) uint32 (fy[:, 0] unused), r and z (n, lx+1) ring elements (r
+    odd).  Returns DReLU' per row."""
+    s0, s1 = _u64(s0), _u64(s1)
+    n = s0.size
+    t = np.ascontiguousarray(t, dtype=np.uint8)
+    fy = np.ascontiguousarray(fy, dtype=np.uint32)
+    r, z = _u64(r), _u64(z)
+    out = np.empty(n, np.uint8)
+    rc = lib().orc_drelu_b1_core_many(ctypes.byref(P), _p(s0), _p(s1), _p(t), _p(fy), _p(r),
+                                      _p(z), ctypes.c_size_t(n), _p(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the parameters")
+    return out

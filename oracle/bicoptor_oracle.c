@@ -129,7 +129,8 @@ enum {
     PUR_RSS_T = 8,      /* seed012: alpha_0..2 (sharing of t)            */
     PUR_RSS_S = 9,      /* seed2: s / seed012: [s]_1 / seed12: [s]_2     */
     PUR_RSS_Z = 10,     /* seed012: gamma_0..2, zero sharing of [s][t]   */
-    PUR_RSS_ZR = 11     /* seed012: zero sharing of the ReLU product     */
+    PUR_RSS_ZR = 11,    /* seed012: zero sharing of the RSS ReLU product */
+    PUR_B1_MASK = 12    /* seed01: r_k, z_k of slot k, Bicoptor 1.0-style */
 };
 
 uint32_t orc_stream_word(uint64_t seed, int pair, int purpose, uint32_t tensor_id,
@@ -724,6 +725,160 @@ int orc_rss_drelu(const orc_params *P, const uint64_t *x0, const uint64_t *x1, c
         }
         y0[i] = Y[0]; y1[i] = Y[1]; y2[i] = Y[2];
         if (dprime_out) dprime_out[i] = (uint8_t)dprime;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The Bicoptor 1.0-style DReLU that this paper improves on, as it describes */
+/* it by contrast (Table "compare"; Sec. "sub:cmp"; the notes on steps 3 and */
+/* 4 of Alg. drelu):                                                          */
+/*   step 3  SecureML truncations (Alg. smltrc) in Z_{2^l}, not Z_{2^lx}, at  */
+/*           every key-bit position c + i, i = 0..lx                          */
+/*   step 4  recursive sums S_i = sum_{k=i..lx} u_k, v_i = S_i - 1 (P0 holds  */
+/*           the constant), instead of adjacent pairs                         */
+/*   no modulo switch: masking, shuffling, resharing and P2's zero test stay  */
+/*   in Z_{2^l}; each party sends lx+1 ring elements, (lx+1) l bits          */
+/*   no u* term (DReLU(0) is t, as in Bicoptor 2.0)                           */
+/* READING: the mask r_k must keep zero <=> zero in Z_{2^l}, so it is a       */
+/* random odd element (a unit); r_k = (W | 1) mod 2^l and z_k = W' mod 2^l   */
+/* from the two 64-bit words of slot k's seed01 block (purpose PUR_B1_MASK). */
+/* The shuffle, t, the reply and the ReLU triple are drawn as in Bicoptor    */
+/* 2.0.  The paper's table counts l_x l bits per party; its text (2,048 and  */
+/* 512 bits at l_x = 31 and 7) counts the l_x + 1 values sent here.           */
+/* ------------------------------------------------------------------------- */
+
+/* Steps 1-9 for one element with the randomness passed in (r[k] odd). */
+int orc_drelu_b1_core(const orc_params *P, uint64_t s0, uint64_t s1, int t, const uint32_t *fy,
+                      const uint64_t *r, const uint64_t *z, uint64_t *msg0, uint64_t *msg1)
+{
+    const int ell = P->ell, lx = P->lx, c = P->c;
+    const int L = lx + 1;
+    uint64_t u0[MAXL], u1[MAXL], v0[MAXL], v1[MAXL], sh0[MAXL], sh1[MAXL];
+    int perm[MAXL];
+
+    /* Steps 1-2: flip by (-1)^t. */
+    if (t != 0) { s0 = rneg(s0, ell); s1 = rneg(s1, ell); }
+
+    /* Step 3: Alg. smltrc of each party's share by c + i bits, in Z_{2^l}. */
+    for (int i = 0; i <= lx; i++) {
+        u0[i] = smltrc_p0(s0, ell, c + i);
+        u1[i] = smltrc_p1(s1, ell, c + i);
+    }
+
+    /* Step 4: recursive sums from the top, minus one (P0). */
+    uint64_t acc0 = 0, acc1 = 0;
+    for (int i = lx; i >= 0; i--) {
+        acc0 = rmod(acc0 + u0[i], ell);
+        acc1 = rmod(acc1 + u1[i], ell);
+        v0[i] = rmod(acc0 - 1, ell);
+        v1[i] = acc1;
+    }
+
+    /* Step 6: the shuffle of Bicoptor 2.0 (Fisher-Yates from the identity). */
+    for (int k = 0; k < L; k++) perm[k] = k;
+    for (int j = lx; j >= 1; j--) {
+        uint64_t word = fy[lx - j + 1];
+        int q = (int)((word * (uint64_t)(j + 1)) >> 32);
+        int tmp = perm[j]; perm[j] = perm[q]; perm[q] = tmp;
+    }
+    for (int k = 0; k < L; k++) { sh0[k] = v0[perm[k]]; sh1[k] = v1[perm[k]]; }
+
+    /* Steps 7-8: mask by the unit r_k, reshare with z_k (P0 adds, P1
+       subtracts), all in Z_{2^l}. */
+    for (int k = 0; k < L; k++) {
+        msg0[k] = rmod(sh0[k] * r[k] + z[k], ell);
+        msg1[k] = rmod(sh1[k] * r[k] - z[k], ell);
+    }
+
+    /* Step 9: P2 reconstructs every w_k in Z_{2^l}; DReLU' = 1 if one is 0. */
+    int dprime = 0;
+    for (int k = 0; k < L; k++)
+        if (rmod(msg0[k] + msg1[k], ell) == 0) dprime = 1;
+    return dprime;
+}
+
+static void draw_b1(const orc_params *P, uint64_t seed, uint32_t tid, uint64_t elem, int *t,
+                    uint32_t *fy, uint64_t *r, uint64_t *z)
+{
+    const int L = P->lx + 1;
+    *t = (int)(orc_stream_word(seed, PAIR_01, PUR_PERM, tid, elem, 0) & 1u);
+    for (int j = 1; j < L; j++) fy[j] = orc_stream_word(seed, PAIR_01, PUR_PERM, tid, elem, j);
+    for (int k = 0; k < L; k++) {
+        uint64_t wr = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_B1_MASK, tid, elem, 4 * k) |
+                      ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_B1_MASK, tid, elem, 4 * k + 1) << 32);
+        uint64_t wz = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_B1_MASK, tid, elem, 4 * k + 2) |
+                      ((uint64_t)orc_stream_word(seed, PAIR_01, PUR_B1_MASK, tid, elem, 4 * k + 3) << 32);
+        r[k] = rmod(wr | 1u, P->ell);
+        z[k] = rmod(wz, P->ell);
+    }
+}
+
+/* The parameters of the 1.0-style protocol: no prime (p is ignored). */
+static int check_params_b1(const orc_params *P)
+{
+    if (P->ell < 2 || P->ell > 64) return -1;
+    if (P->lx < 1 || P->lx > 31 || P->lx + 1 > MAXL) return -1;
+    if (P->c < 0 || P->c + P->lx >= P->ell) return -1;
+    return 0;
+}
+
+/* DReLU (relu = 0) or ReLU (relu = 1) of the 1.0-style protocol; steps 10-11
+   and Alg. relu's Beaver finish exactly as in Bicoptor 2.0.  msgs (optional):
+   w0 then w1, each n * (lx+1) ring elements, slot-major per element. */
+int orc_b1(const orc_params *P, int relu, const uint64_t *s0, const uint64_t *s1,
+           const uint64_t *idx, size_t n, uint64_t seed, uint32_t tid, uint64_t *o0,
+           uint64_t *o1, uint64_t *w0, uint64_t *w1, uint8_t *dprime_out, int threads)
+{
+    if (check_params_b1(P)) return -1;
+    const int ell = P->ell, L = P->lx + 1;
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (long long ii = 0; ii < (long long)n; ii++) {
+        size_t i = (size_t)ii;
+        uint64_t elem = elem_index(idx, i);
+        int t;
+        uint32_t fy[MAXL];
+        uint64_t r[MAXL], z[MAXL], msg0[MAXL], msg1[MAXL];
+        draw_b1(P, seed, tid, elem, &t, fy, r, z);
+        int dprime = orc_drelu_b1_core(P, s0[i], s1[i], t, fy, r, z, msg0, msg1);
+        uint64_t one_m2t = rmod((uint64_t)1 - 2 * (uint64_t)t, ell);
+        if (!relu) {
+            uint64_t d0 = stream_ring(seed, PAIR_02, PUR_REPLY, tid, elem, 0, ell);
+            uint64_t d1 = rmod((uint64_t)dprime - d0, ell);
+            o0[i] = rmod((uint64_t)t + one_m2t * d0, ell);
+            o1[i] = rmod(one_m2t * d1, ell);
+        } else {
+            triple_t T = draw_triple(seed, PUR_RELU_TRIPLE, tid, elem, ell);
+            uint64_t e = rmod((uint64_t)dprime - (T.b0 + T.b1), ell);
+            uint64_t d = rmod((s0[i] - T.a0) + (s1[i] - T.a1), ell);
+            uint64_t xd0 = rmod(d * e + d * T.b0 + e * T.a0 + T.c0, ell);
+            uint64_t xd1 = rmod(d * T.b1 + e * T.a1 + T.c1, ell);
+            o0[i] = rmod(one_m2t * xd0 + (uint64_t)t * s0[i], ell);   /* unflip */
+            o1[i] = rmod(one_m2t * xd1 + (uint64_t)t * s1[i], ell);
+        }
+        if (w0) memcpy(w0 + i * L, msg0, sizeof(uint64_t) * L);
+        if (w1) memcpy(w1 + i * L, msg1, sizeof(uint64_t) * L);
+        if (dprime_out) dprime_out[i] = (uint8_t)dprime;
+    }
+    return 0;
+}
+
+/* Steps 1-9 of the 1.0-style protocol over many elements with explicit
+   randomness (row i: t[i], fy[i*L ..], r[i*L ..], z[i*L ..]); for the pins. */
+int orc_drelu_b1_core_many(const orc_params *P, const uint64_t *s0, const uint64_t *s1,
+                           const uint8_t *t, const uint32_t *fy, const uint64_t *r,
+                           const uint64_t *z, size_t n, uint8_t *dprime)
+{
+    if (check_params_b1(P)) return -1;
+    const int L = P->lx + 1;
+    ORC_PARALLEL_FOR
+    for (size_t i = 0; i < n; i++) {
+        uint64_t msg0[MAXL], msg1[MAXL];
+        dprime[i] = (uint8_t)orc_drelu_b1_core(P, s0[i], s1[i], t[i], fy + i * L, r + i * L,
+                                               z + i * L, msg0, msg1);
     }
     return 0;
 }

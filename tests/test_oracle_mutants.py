@@ -53,6 +53,14 @@ MUTANTS = {
                                "uint64_t ty0 = smltrc_p0(y0[i], ell, kx), ty1 = smltrc_p1(y1[i], ell, kx);"),
     "aby3_signed_division": ("if (ell < 128 && (v >> (ell - 1)) & 1) v -= ((__int128)1 << ell);",
                              "if (0) v -= ((__int128)1 << ell);"),
+    # the Bicoptor 1.0-style protocol
+    "b1_sums_not_recursive": ("acc0 = rmod(acc0 + u0[i], ell);", "acc0 = rmod(u0[i], ell);"),
+    "b1_p0_constant_dropped": ("v0[i] = rmod(acc0 - 1, ell);", "v0[i] = acc0;"),
+    "b1_mask_may_be_even": ("r[k] = rmod(wr | 1u, P->ell);", "r[k] = rmod(wr, P->ell);"),
+    "b1_reshare_wrong_sign": ("msg1[k] = rmod(sh1[k] * r[k] - z[k], ell);",
+                              "msg1[k] = rmod(sh1[k] * r[k] + z[k], ell);"),
+    "b1_trunc_in_small_ring": ("u1[i] = smltrc_p1(s1, ell, c + i);",
+                               "u1[i] = rmod(smltrc_p1(s1, ell, c + i), lx);"),
 }
 
 

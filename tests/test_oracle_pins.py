@@ -592,3 +592,123 @@ def test_rss_relu_exact_product():
         signed = O.to_signed((r0 + r1 + r2) & mk, ell)
         miss = np.abs(xs[signed != np.maximum(xs, 0)])
         assert all(_predicted_miss(int(v), lx, c) for v in miss)
+
+
+# ---- the Bicoptor 1.0-style DReLU (the baseline the paper improves on) ----------
+
+def _smltrc_ints(ell, s0, s1, k):
+    """Alg. smltrc of each party's share, from its definition (Python ints):
+    P0 cut([x]_0, k), P1 2^l - cut(2^l - [x]_1, k), both mod 2^l."""
+    m = (1 << ell) - 1
+    return (s0 >> k) & m, (-(((-s1) & m) >> k)) & m
+
+
+def _b1_closed_form(ell, lx, c, fs0, fs1):
+    """DReLU' of the 1.0-style protocol from its definition: some recursive
+    sum S_i = sum_{k=i..lx} trc(x', c + k), reconstructed, equals 1 (the
+    masks are units, the shuffle and the reshare keep the zero set)."""
+    m = (1 << ell) - 1
+    out = []
+    for a, b in zip(fs0.tolist(), fs1.tolist()):
+        u = [sum(_smltrc_ints(ell, a, b, c + k)) & m for k in range(lx + 1)]
+        out.append(any(((sum(u[i:]) - 1) & m) == 0 for i in range(lx + 1)))
+    return np.array(out)
+
+
+B1_BRUTE = [(8, 2, 0), (8, 3, 0), (8, 4, 0), (8, 3, 1), (8, 2, 2), (10, 5, 0), (10, 4, 2)]
+
+
+@pytest.mark.parametrize("ell,lx,c", B1_BRUTE)
+def test_b1_bruteforce(ell, lx, c):
+    """Every x, every R, t in {0, 1}: DReLU' equals the closed form, and a
+    sign is wrong only where one of the SecureML truncations makes its large
+    error e1 (|trc(x', k) - floor(x' / 2^k)| > 1, probability |x| / 2^l each,
+    Cor. 2) or, with key offset c > 0, for |x| < 2^c.  That is the failure
+    Bicoptor 2.0's deterministic truncation removes."""
+    m = (1 << ell) - 1
+    L = lx + 1
+    X, RR, T = np.meshgrid(np.arange(1 << ell, dtype=np.uint64),
+                           np.arange(1 << ell, dtype=np.uint64),
+                           np.array([0, 1], dtype=np.uint64), indexing="ij")
+    X, RR, T = X.ravel(), RR.ravel(), T.ravel()
+    s0 = (X + RR) & np.uint64(m)
+    s1 = (np.uint64(0) - RR) & np.uint64(m)
+    n = X.size
+    rng = np.random.default_rng(ell * 1000 + lx * 10 + c)
+    fy = rng.integers(0, 2**32, size=(n, L), dtype=np.uint64).astype(np.uint32)
+    r = (rng.integers(0, 2**63, size=(n, L), dtype=np.uint64) * np.uint64(2) + np.uint64(1)) \
+        & np.uint64(m)
+    z = rng.integers(0, 2**63, size=(n, L), dtype=np.uint64) & np.uint64(m)
+    P = O.params(ell, lx, c)
+    d = O.drelu_b1_core_many(P, s0, s1, T.astype(np.uint8), fy, r, z).astype(bool)
+    neg = lambda a: (np.uint64(0) - a) & np.uint64(m)
+    fs0 = np.where(T == 1, neg(s0), s0)
+    fs1 = np.where(T == 1, neg(s1), s1)
+    assert (d == _b1_closed_form(ell, lx, c, fs0, fs1)).all()
+    xs = X.astype(np.int64)
+    xs = np.where(xs >= 1 << (ell - 1), xs - (1 << ell), xs)
+    xp = ((fs0 + fs1) & np.uint64(m)).astype(np.int64)
+    xp = np.where(xp >= 1 << (ell - 1), xp - (1 << ell), xp)
+    e1 = np.zeros(n, dtype=bool)
+    for k in range(lx + 1):
+        a, b = _smltrc_ints(ell, fs0.astype(object), fs1.astype(object), c + k)
+        uk = ((a + b) & m).astype(np.int64)
+        uk = np.where(uk >= 1 << (ell - 1), uk - (1 << ell), uk)
+        e1 |= np.abs(uk - (xp >> (c + k))) > 1
+    got = d.astype(np.int64) ^ T.astype(np.int64)
+    dom = (np.abs(xs) < (1 << (lx + c))) & (xs != 0)
+    bad = dom & (got != (xs >= 0))
+    above = np.abs(xs) >= (1 << c)
+    assert not (bad & ~e1 & above).any()
+    assert bad.sum() > 0 and (bad & above).sum() <= (e1 & dom).sum()
+
+
+def test_b1_messages_recomputed():
+    """The messages of the 1.0-style protocol recomputed with Python ints
+    from the oracle's Philox stream words: t and the shuffle, then for every
+    slot k w0 = (S0_{perm k} - 1) r_k + z_k and w1 = S1_{perm k} r_k - z_k in
+    Z_{2^l}, with r_k the odd unit and z_k the reshare of slot k."""
+    seed, tid = 0xB1B1, 9
+    for ell, lx, c in ((64, 24, 0), (64, 7, 24), (32, 14, 4)):
+        m = (1 << ell) - 1
+        P = O.params(ell, lx, c)
+        rng = np.random.default_rng(ell + lx)
+        x = rng.integers(-(1 << (lx + c - 1)), 1 << (lx + c - 1), size=40)
+        s0, s1 = O.share(ell, (x.astype(np.uint64) & np.uint64(m)), seed, 1)
+        o0, o1, w0, w1, dp = O.b1(P, s0, s1, seed, tid, msgs=True)
+        L = lx + 1
+        for e in range(x.size):
+            word = lambda pur, j: O.stream_word(seed, O.PAIR_01, pur, tid, e, j)
+            t = word(O.PUR_PERM, 0) & 1
+            a, b = int(s0[e]), int(s1[e])
+            if t:
+                a, b = (-a) & m, (-b) & m
+            perm = list(range(L))
+            for j in range(lx, 0, -1):
+                q = (word(O.PUR_PERM, lx - j + 1) * (j + 1)) >> 32
+                perm[j], perm[q] = perm[q], perm[j]
+            u = [_smltrc_ints(ell, a, b, c + k) for k in range(L)]
+            S0 = [sum(u0 for u0, _ in u[i:]) & m for i in range(L)]
+            S1 = [sum(u1 for _, u1 in u[i:]) & m for i in range(L)]
+            for k in range(L):
+                w64 = lambda j: word(O.PUR_B1_MASK, 4 * k + j) | (word(O.PUR_B1_MASK, 4 * k + j + 1) << 32)
+                rk, zk = (w64(0) | 1) & m, w64(2) & m
+                assert int(w0[e, k]) == ((S0[perm[k]] - 1) * rk + zk) & m
+                assert int(w1[e, k]) == (S1[perm[k]] * rk - zk) & m
+            assert int(dp[e]) == int(any(((int(w0[e, k]) + int(w1[e, k])) & m) == 0
+                                         for k in range(L)))
+
+
+def test_b1_sign_at_l64():
+    """At l = 64 a SecureML failure has probability |x| / 2^64 per
+    truncation, so for |x| < 2^23 the 1.0-style DReLU gives the exact sign
+    and its ReLU is exactly max(x, 0) (x = 0 aside)."""
+    P = O.params(64, 24, 0)
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(20000, 23, seed=5)
+    xs = xs[xs != 0]
+    s0, s1 = O.share(64, xs.astype(np.uint64), seed=1, tid=2)
+    o0, o1 = O.b1(P, s0, s1, 3, 4, threads=8)
+    assert (O.reconstruct(64, o0, o1) == (xs >= 0)).all()
+    r0, r1 = O.b1(P, s0, s1, 3, 4, relu=True, threads=8)
+    assert (O.to_signed(O.reconstruct(64, r0, r1), 64) == np.maximum(xs, 0)).all()
