@@ -808,6 +808,7 @@ def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, de
     relu_ms = fl["unfused_chain"].get("relu_ms", kern_ms)
     extra("party_separated", lambda: parties_bench(ctx, prm, buf, n, relu_ms), into=fl)
     extra("rss_relu", lambda: rss_bench(ctx, prm, buf, n), into=fl)
+    extra("bicoptor1_vs_2", lambda: b1_bench(ctx, x0, x1, n))
     # the other workloads
     extra("hbm_kernels_isolated", lambda: hbm_isolated(ctx, dev))
     extra("linear_layer_truncation", lambda: linear_trunc_table(ctx, dev))
@@ -1224,6 +1225,36 @@ def rss_bench(ctx, prm, buf, n):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 20
     return {"kernel_ms": ms, "elems_per_s": n / (ms / 1e3)}
+
+
+def b1_bench(ctx, x0, x1, n, reps=20):
+    """The Bicoptor 1.0-style protocol (SecureML truncations, recursive sums
+    and masks in Z_{2^l}) against Bicoptor 2.0 on the same 2^22 shares at
+    l = 64, at lx = 24 and at the paper's key bits lx = 7 (c = 24): kernel time
+    and the bits each of P0 and P1 sends P2 per element."""
+    import torch
+    from paper_2309_04909_gb300 import Params
+    out = {}
+    o = (torch.empty_like(x0), torch.empty_like(x1))
+    for lx, c in ((24, 0), (7, 24)):
+        prm = Params(64, lx, c)
+        row = {}
+        for name, fn in (("b2_drelu", ctx.drelu), ("b2_relu", ctx.relu),
+                         ("b1_drelu", ctx.drelu_b1), ("b1_relu", ctx.relu_b1)):
+            for _ in range(3):
+                fn(prm, x0, x1, 5, out=o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn(prm, x0, x1, 5, out=o)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[name] = {"kernel_ms": ms, "elems_per_s": n / (ms / 1e3)}
+        row["bits_per_element_p0_to_p2"] = {"b2": (lx + 1) ** 2, "b1": (lx + 1) * 64}
+        out[f"lx{lx}_c{c}"] = row
+    return out
 
 
 def parties_bench(ctx, prm, buf, n, fused_ms):

@@ -195,6 +195,25 @@ int bc_rss_drelu(bc_ctx *ctx, const bc_drelu_params *prm, const void *x0, const 
 int bc_rss_relu(bc_ctx *ctx, const bc_drelu_params *prm, const void *x0, const void *x1,
                 const void *x2, size_t n, uint32_t tensor_id, void *y0, void *y1, void *y2);
 
+/* ---- the Bicoptor 1.0-style DReLU / ReLU (the baseline) ------------------ */
+
+/* The protocol Bicoptor 2.0 improves on, as the paper describes it by
+ * contrast (Table "compare"; Sec. "sub:cmp"; the notes on steps 3-4 of
+ * Alg. drelu), for comparing communication and speed on the same GPU:
+ * Alg. smltrc truncations in Z_{2^l} at key-bit positions c + i (i = 0..lx),
+ * recursive sums S_i = sum_{k >= i} u_k with v_i = S_i - 1, masks by random
+ * odd units r_k and reshares z_k in Z_{2^l}, P2's zero test in Z_{2^l}; the
+ * flip, shuffle, reply and ReLU triple as in Bicoptor 2.0.  Each party sends
+ * (lx+1) l bits per element (counted in bc_comm).  Needs c + lx < l; p is
+ * ignored.  w0, w1 (optional, both or neither): the messages, n * (lx+1)
+ * lanes each, slot-major per element.  Correct outside the SecureML
+ * truncation's large-error events (probability |x| / 2^l per truncation),
+ * which is what Alg. newtrc2 removes. */
+int bc_drelu_b1(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+                size_t n, uint32_t tensor_id, void *o0, void *o1, void *w0, void *w1);
+int bc_relu_b1(bc_ctx *ctx, const bc_drelu_params *prm, const void *sh0, const void *sh1,
+               size_t n, uint32_t tensor_id, void *o0, void *o1, void *w0, void *w1);
+
 /* ---- party-separated DReLU / ReLU --------------------------------------- */
 
 /* The message buffers of one party-separated call (device memory owned by

@@ -275,6 +275,32 @@ class Context:
     def relu(self, prm: Params, s0, s1, tensor_id: int, out=None, audit: bool = False):
         return self._protocol(self._lib.bc_relu, prm, s0, s1, tensor_id, out, audit)
 
+    # -- the Bicoptor 1.0-style baseline ---------------------------------------------
+    def _b1(self, fn, prm: Params, s0, s1, tensor_id, out, messages):
+        self._need(s0, prm.ring_bits, "s0")
+        self._need(s1, prm.ring_bits, "s1")
+        n = s0.numel()
+        o0, o1 = out if out is not None else (self._empty(n, prm.ring_bits),
+                                              self._empty(n, prm.ring_bits))
+        w = None
+        if messages:
+            w = (self._empty(n * prm.slots, prm.ring_bits), self._empty(n * prm.slots,
+                                                                          prm.ring_bits))
+        self._sync_stream()
+        self._check(fn(self._h, ctypes.byref(prm.c_struct()), _ptr(s0), _ptr(s1), n, tensor_id,
+                       _ptr(o0), _ptr(o1), _ptr(w[0]) if w else None,
+                       _ptr(w[1]) if w else None))
+        return (o0, o1, w[0], w[1]) if messages else (o0, o1)
+
+    def drelu_b1(self, prm: Params, s0, s1, tensor_id: int, out=None, messages: bool = False):
+        """The Bicoptor 1.0-style DReLU (bc_drelu_b1): SecureML truncations,
+        recursive sums and masks in Z_{2^l}; (lx+1) l bits per party.  With
+        messages, also returns the two parties' messages to P2 (n * (lx+1))."""
+        return self._b1(self._lib.bc_drelu_b1, prm, s0, s1, tensor_id, out, messages)
+
+    def relu_b1(self, prm: Params, s0, s1, tensor_id: int, out=None, messages: bool = False):
+        return self._b1(self._lib.bc_relu_b1, prm, s0, s1, tensor_id, out, messages)
+
     # -- RSS (Alg. drelu2) -----------------------------------------------------------
     def _rss(self, fn, prm: Params, x0, x1, x2, tensor_id, out):
         for t, nm in ((x0, "x0"), (x1, "x1"), (x2, "x2")):

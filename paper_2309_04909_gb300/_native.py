@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libbicoptor.so")
 SOURCES = ["bc_relu.cu", "bc_batch.cu", "bc_elementwise.cu", "bc_api.cu", "bc_noalloc.cu",
-           "bc_parties.cu", "bc_peaks.cu"]
+           "bc_parties.cu", "bc_peaks.cu", "bc_b1.cu"]
 HEADERS = ["bc_device.cuh", "bc_element.cuh", "bc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -155,6 +155,10 @@ SIGNATURES = {
     "bc_set_audit": (c_int, [c_void_p, P(Audit)]),
     "bc_get_comm": (c_int, [c_void_p, P(Comm)]),
     "bc_reset_comm": (c_int, [c_void_p]),
+    "bc_drelu_b1": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_size, c_u32,
+                            c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bc_relu_b1": (c_int, [c_void_p, P(DreluParams), c_void_p, c_void_p, c_size, c_u32,
+                           c_void_p, c_void_p, c_void_p, c_void_p]),
     "bc_party_local": (c_int, [c_void_p, c_int, P(DreluParams), c_int, c_void_p, c_size, c_u32,
                                c_void_p, c_void_p]),
     "bc_party_helper": (c_int, [c_void_p, P(DreluParams), c_int, c_size, c_u32, c_void_p,

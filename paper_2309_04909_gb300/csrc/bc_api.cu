@@ -470,6 +470,44 @@ int bc_relu_parties(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, co
   return run_parties(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, m, true);
 }
 
+// ---- the Bicoptor 1.0-style DReLU / ReLU ---------------------------------------
+
+static int run_b1(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+                  size_t n, uint32_t tensor_id, void* o0, void* o1, void* w0, void* w1,
+                  bool relu) {
+  if (!ctx || !prm) return BC_EINVAL;
+  const int ell = prm->ring_bits, lx = prm->lx, c = prm->key_off;
+  if (ell < 2 || ell > 64 || lx < 1 || lx > 31 || c < 0 || c + lx >= ell) return BC_EINVAL;
+  if (n && (!sh0 || !sh1 || !o0 || !o1)) return BC_EINVAL;
+  if (!w0 != !w1) return BC_EINVAL;
+  BC_TRACE();
+  int rc;
+  if ((rc = check_canonical(ctx, ell, {sh0, sh1}, n))) return rc;
+  bc::ReluConsts k{};
+  k.rk = ctx->rk;
+  k.ring_mask = ring_mask(ell);
+  k.ring_bits = (uint32_t)ell;
+  k.lx = (uint32_t)lx;
+  k.c = (uint32_t)c;
+  k.tensor_id = tensor_id;
+  k.elem_base = 0;
+  if (n) CK(bc::launch_b1(k, relu, sh0, sh1, n, o0, o1, w0, w1, ctx->stream));
+  bc_comm d = relu_comm(ell, lx, n, relu);
+  d.p0_to_p2 = d.p1_to_p2 = (uint64_t)n * (uint64_t)(lx + 1) * (uint64_t)ell;   // ring elements
+  add_comm(&ctx->comm, d);
+  return BC_OK;
+}
+
+int bc_drelu_b1(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+                size_t n, uint32_t tensor_id, void* o0, void* o1, void* w0, void* w1) {
+  return run_b1(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, w0, w1, false);
+}
+
+int bc_relu_b1(bc_ctx* ctx, const bc_drelu_params* prm, const void* sh0, const void* sh1,
+               size_t n, uint32_t tensor_id, void* o0, void* o1, void* w0, void* w1) {
+  return run_b1(ctx, prm, sh0, sh1, n, tensor_id, o0, o1, w0, w1, true);
+}
+
 // ---- one party's stage --------------------------------------------------------
 
 static int stage_consts(bc_ctx* ctx, const bc_drelu_params* prm, uint32_t tensor_id,

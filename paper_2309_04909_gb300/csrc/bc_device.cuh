@@ -99,6 +99,7 @@ enum : uint32_t {
   kPurRssS = 9,         // seed2: s / seed012: [s]_1 / seed12: [s]_2 (RSS)
   kPurRssZ = 10,        // seed012: zero sharing of [s][t] (RSS)
   kPurRssZr = 11,       // seed012: zero sharing of the RSS ReLU product
+  kPurB1Mask = 12,      // seed01: (r_k, z_k) of slot k, the Bicoptor 1.0-style protocol
 };
 
 __device__ __forceinline__ uint32_t stream_tag(uint32_t pair, uint32_t purpose, uint64_t elem) {

@@ -234,6 +234,11 @@ cudaError_t launch_party_stage(const ReluConsts& k, bool relu, int stage, int pa
                                const PartyIo& io, uint64_t n, int* status, bool drop_copies,
                                cudaStream_t s);
 
+// The Bicoptor 1.0-style DReLU / ReLU (bc_b1.cu); w0, w1 (optional) receive
+// the messages, n * (lx + 1) lanes each, slot-major per element.
+cudaError_t launch_b1(const ReluConsts& k, bool relu, const void* sh0, const void* sh1,
+                      uint64_t n, void* o0, void* o1, void* w0, void* w1, cudaStream_t s);
+
 cudaError_t launch_share(int ring_bits, const RoundKeys& rk, const int64_t* x, uint64_t n,
                          uint32_t tensor_id, uint64_t elem_base, void* sh0, void* sh1, int num_sms,
                          cudaStream_t s);

@@ -105,7 +105,8 @@ def _check_sign(ell, lx, c, X, rec_drelu, exhaustive):
     """The reconstructed DReLU against the plaintext sign on the domain
     |x| < 2^(lx+c), x != 0, outside the predicted exception set."""
     xs = _signed(X, ell)
-    dom = (np.abs(xs) < (1 << (lx + c))) & (xs != 0)
+    lim = 1 << (lx + c)
+    dom = (xs > -lim) & (xs < lim) & (xs != 0)        # (abs() of -2^63 wraps in int64)
     bad = dom & (rec_drelu != (xs >= 0))
     mags = set(np.abs(xs[bad]).tolist())
     if exhaustive and c == 0 and lx >= 3:
