@@ -59,9 +59,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="resnet18", choices=["resnet18", "fused"],
+    ap.add_argument("--workload", default="resnet18", choices=["resnet18", "fused", "b1-pair"],
                     help="resnet18: the batched ReLU set (default, the headline); fused: the "
-                         "fused linear-layer step alone (for profiling, with --step)")
+                         "fused linear-layer step alone (for profiling, with --step); b1-pair: "
+                         "one Bicoptor 1.0-style DReLU and one Bicoptor 2.0 DReLU launch on the "
+                         "same --n shares at l = 64, lx = 24 (for profiling)")
     ap.add_argument("--images", type=int, default=RESNET_IMAGES,
                     help="images of the ResNet-18 set (32 in the workload; fewer for profiling)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -314,7 +316,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     try:
-        if args.workload == "fused":
+        if args.workload == "b1-pair":
+            b1_pair(args, local, dev)
+        elif args.workload == "fused":
             fused_main(args, world, rank, local, dev)
         else:
             headline(args, world, rank, local, dev)
@@ -1225,6 +1229,23 @@ def rss_bench(ctx, prm, buf, n):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 20
     return {"kernel_ms": ms, "elems_per_s": n / (ms / 1e3)}
+
+
+def b1_pair(args, local, dev):
+    """`--workload b1-pair`: one launch of each DReLU kernel on the same
+    shares (magnitudes below 2^21, l = 64, lx = 24, c = 0), for profiling."""
+    import torch
+    from paper_2309_04909_gb300 import Context, Params, workloads as W
+    ctx = Context(5, device=local)
+    x = W.magnitude_bounded_ints(args.n, 21, seed=1)
+    x0, x1 = ctx.share(64, torch.from_numpy(x).to(dev), 1)
+    prm = Params(64, 24, 0)
+    o = (torch.empty_like(x0), torch.empty_like(x1))
+    ctx.drelu_b1(prm, x0, x1, 5, out=o)
+    ctx.drelu(prm, x0, x1, 5, out=o)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "b1-pair", "n": args.n}), flush=True)
+    ctx.close()
 
 
 def b1_bench(ctx, x0, x1, n, reps=20):

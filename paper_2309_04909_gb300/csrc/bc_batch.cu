@@ -16,6 +16,12 @@
 // unroll.
 #include "bc_element.cuh"
 
+// Tuning knob of the grid-schedule kernel (compile-time): the minimum resident
+// CTAs per SM requested from the register allocator (0 = let it choose).
+#ifndef BC_BATCH_MIN_CTAS
+#define BC_BATCH_MIN_CTAS 0
+#endif
+
 namespace bc {
 namespace {
 
@@ -103,7 +109,7 @@ __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor
 }
 
 template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, BC_BATCH_MIN_CTAS)
     relu_batch_grid_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
                            const BatchTile* __restrict__ tiles, uint32_t begin,
                            int* __restrict__ status) {
