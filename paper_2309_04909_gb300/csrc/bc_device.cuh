@@ -266,6 +266,14 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const ModP&
   return (carry || r >= m.p) ? r - m.p : r;
 }
 
+// The Montgomery quotient (a b + q p) / 2^32 in [0, 2p), before the final
+// subtraction, for p < 2^31 (the 64-bit sum cannot overflow).
+__device__ __forceinline__ uint32_t mont_mul_raw(uint32_t a, uint32_t b, const ModP& m) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t q = (uint32_t)t * m.pinv;
+  return (uint32_t)((t + (uint64_t)q * m.p) >> 32);
+}
+
 // a + b mod p and a - b mod p for a, b < p (p < 2^32 so the sum may wrap
 // 32 bits only when p > 2^31; handled through 64-bit compare).
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t p) {

@@ -26,6 +26,19 @@
 #define BC_SLOT_UNROLL 2
 #endif
 
+// The slot loop's Z_p sums as three-input adds (1) or in their plain form (0).
+// The loop is bound by the FMA-heavy pipe, which executes the integer
+// multiplies; the compiler issues every two-input integer add there too (as a
+// multiply-add by one), while a three-input add exists only on the integer
+// ALU, which has room.  So each sum gets a third operand that is always 0 but
+// comes from the kernel parameters (zero1, zero2: the compiler cannot fold
+// them), a reduction x mod p of x < 2p is min(x, x - p + 0), and each
+// reduction is chained on the sum it reduces so that no two-input partial
+// sum is shared.  The values are unchanged.
+#ifndef BC_ALU_ADDS
+#define BC_ALU_ADDS 1
+#endif
+
 namespace bc {
 
 
@@ -131,6 +144,27 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0,
   // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
   const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
   const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
+#if BC_ALU_ADDS
+  if (!kWide) {
+    // the same steps 5-9 with every sum in three-input form (p < 2^31, so
+    // every sum below stays under 2^32; a value in [0, 2p) reduces to the
+    // minimum of itself and itself minus p, which wraps above it when < p)
+    const uint32_t z1 = k.zero1, z2 = k.zero2, negp = k.neg_p;
+    const uint32_t m0 = v0 ? v0 : k.two_lx;
+    const uint32_t m1 = v1 + k.p_minus_2lx + z1;
+    const uint32_t rho = mulhi_64x32(rz.x, rz.y, k.mp.pm1) + 1u + z2;
+    const uint32_t zk = mulhi_64x32(rz.z, rz.w, p);
+    const uint32_t q0 = mont_mul_raw(m0, rho, k.mp), q1 = mont_mul_raw(m1, rho, k.mp);
+    const uint32_t u0 = min(q0, q0 + negp + z1);
+    const uint32_t u1 = min(q1, q1 + negp + z2);
+    const uint32_t a0 = u0 + zk + z1;                  // step 8: P0 adds z_k
+    w0 = min(a0, a0 + negp + z2);
+    const uint32_t a1 = u1 - zk + z1;                  // P1 subtracts it
+    w1 = min(a1, a1 + p + z2);
+    const uint32_t s = w0 + w1 + z1;                   // step 9: below 2p
+    return ((s == 0u) | (s == p)) ? 1u : 0u;
+  }
+#endif
   // step 5: Alg. modswitch
   const uint32_t m0 = v0 ? v0 : k.two_lx;
   const uint32_t m1 = v1 + k.p_minus_2lx;

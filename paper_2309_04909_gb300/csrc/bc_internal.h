@@ -31,6 +31,9 @@ struct ReluConsts {
   uint32_t p_minus_2lx; // p - 2^lx
   uint32_t tensor_id;
   uint64_t elem_base;   // element index of the launch's first element
+  // Always 0 and 2^32 - p: operands the compiler cannot fold, which keep the
+  // slot loop's sums in three-input form (see BC_ALU_ADDS in bc_element.cuh).
+  uint32_t zero1, zero2, neg_p;
 };
 
 struct AuditPtrs {
@@ -155,6 +158,8 @@ inline int make_relu_consts(const bc_drelu_params* prm, const RoundKeys& rk, uin
   k->p_minus_2lx = p - (uint32_t)lo;
   k->tensor_id = tensor_id;
   k->elem_base = 0;
+  k->zero1 = k->zero2 = 0;
+  k->neg_p = 0u - p;
   return BC_OK;
 }
 
