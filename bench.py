@@ -235,7 +235,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "elems/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "u64+u32", "data": "synthetic",
         "config": {"workload": WORKLOAD.format(images=RESNET_IMAGES, tensors=2 * RESNET_IMAGES
                                                * per_img, elems=f"{total:,}"),
                    "images": RESNET_IMAGES, "elements": total, "sample_per_step": 2 * m},
@@ -446,7 +446,7 @@ def headline(args, world, rank, local, dev):
     line = {
         "metric": METRIC, "value": value, "unit": "elems/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+u32",
         "data": "synthetic",
         "config": {"workload": workload, "images": args.images, "tensors": len(items),
                    "elements": total,
