@@ -22,7 +22,6 @@ product -> truncation -> ReLU step and the audited messages.
 """
 import numpy as np
 import pytest
-import torch
 
 import oracle as O
 from paper_2309_04909_gb300 import Context, Params
