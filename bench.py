@@ -59,11 +59,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="resnet18", choices=["resnet18", "fused", "b1-pair"],
+    ap.add_argument("--workload", default="resnet18",
+                    choices=["resnet18", "fused", "b1-pair", "parties3"],
                     help="resnet18: the batched ReLU set (default, the headline); fused: the "
                          "fused linear-layer step alone (for profiling, with --step); b1-pair: "
                          "one Bicoptor 1.0-style DReLU and one Bicoptor 2.0 DReLU launch on the "
-                         "same --n shares at l = 64, lx = 24 (for profiling)")
+                         "same --n shares at l = 64, lx = 24 (for profiling); parties3: the "
+                         "ReLU of --n elements with P0, P1 and P2 as three processes on GPU 0, "
+                         "messages through host memory (gloo), per-party compute and transport "
+                         "time")
     ap.add_argument("--images", type=int, default=RESNET_IMAGES,
                     help="images of the ResNet-18 set (32 in the workload; fewer for profiling)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -301,6 +305,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "parties3":
+        parties3(args)              # spawns its own three processes; no CUDA in this one
         return
     import torch
     import torch.distributed as dist
@@ -1246,6 +1253,86 @@ def b1_pair(args, local, dev):
     torch.cuda.synchronize()
     print(json.dumps({"workload": "b1-pair", "n": args.n}), flush=True)
     ctx.close()
+
+
+def _parties3_worker(rank, port, out_dir, n, steps, warmup):
+    """One party of `--workload parties3` (rank = party)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2309_04909_gb300 import Context, Params, workloads as W
+    from paper_2309_04909_gb300.parties import PartyProcess, Transport, context_stages
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=3)
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = Context(BASE_SEED)
+    prm = Params(64, 24, 0)
+    x = W.magnitude_bounded_ints(n, 21, seed=1)
+    s0, s1 = ctx.share(64, torch.from_numpy(x).to(dev), 1)
+    share = (s0, s1, None)[rank]
+
+    def clock():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    tr = Transport(dev, direct=False)
+    pp = PartyProcess(rank, context_stages(ctx), tr, clock=clock)
+    walls, out = [], None
+    for i in range(warmup + steps):
+        if i == warmup:
+            pp.timing = {"compute": 0.0, "transport": 0.0}
+            tr.sent = {}
+        dist.barrier()
+        t0 = time.perf_counter()
+        out = pp.run(prm, True, share, n, 7)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            walls.append(time.perf_counter() - t0)
+    wall = torch.tensor(walls, dtype=torch.float64)
+    dist.all_reduce(wall, op=dist.ReduceOp.MAX)          # each step: its slowest party
+    same = None
+    if out is not None:
+        f = ctx.relu(prm, s0, s1, tensor_id=7)
+        same = bool(torch.equal(out, f[rank]))
+    res = {"party": rank, "step_s": wall.tolist(), "compute_s": pp.timing["compute"] / steps,
+           "transport_s": pp.timing["transport"] / steps,
+           "sent_bytes_per_step": {f"{a}->{b}": v // steps for (a, b), v in tr.sent.items()},
+           "identical_to_fused": same}
+    with open(os.path.join(out_dir, f"p{rank}.json"), "w") as fh:
+        json.dump(res, fh)
+    dist.barrier()
+    dist.destroy_process_group()
+    ctx.close()
+
+
+def parties3(args):
+    """`--workload parties3`: the ReLU of --n elements (l = 64, lx = 24) with
+    P0, P1 and P2 as three processes, each with its own context on GPU 0, every
+    message moved through host memory by gloo into the receiver's memory.  One
+    JSON line: elements/s over the slowest party's step time, each party's
+    compute and transport time per step, the bytes each sent, and whether P0's
+    and P1's outputs equal the fused kernel's."""
+    import socket
+    import torch.multiprocessing as mp
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_parties3_worker, nprocs=3, join=True, start_method="spawn",
+                           args=(port, d, args.n, args.steps, args.warmup))
+        r = [json.load(open(os.path.join(d, f"p{k}.json"))) for k in range(3)]
+    step_s = statistics.median(r[0]["step_s"])
+    print(json.dumps({
+        "metric": "relu elems/s, three party processes", "workload": "parties3",
+        "value": args.n / step_s, "unit": "elems/s", "ms_per_step": step_s * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        "config": {"workload": f"ReLU, l=64 lx=24, n={args.n}, P0/P1/P2 as processes on one "
+                               "GPU, gloo through host memory"},
+        "parties": {f"P{x['party']}": {k: x[k] for k in ("compute_s", "transport_s",
+                                                          "sent_bytes_per_step",
+                                                          "identical_to_fused")} for x in r},
+    }), flush=True)
 
 
 def b1_bench(ctx, x0, x1, n, reps=20):

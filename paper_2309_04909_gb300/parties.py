@@ -84,12 +84,24 @@ class PartyProcess:
     with the same parameters; P0 and P1 pass their own share, P2 passes
     None.  Returns the party's output share (None for P2)."""
 
-    def __init__(self, party: int, stages: Stages, transport: Transport):
+    def __init__(self, party: int, stages: Stages, transport: Transport, clock=None):
         if party not in (P0, P1, P2):
             raise ValueError("party must be 0, 1 or 2")
         self.party = party
         self.s = stages
         self.tr = transport
+        # optional: clock() -> seconds after the device finished its queued
+        # work; with it, run() accumulates the party's own computing time
+        # ("compute") and its time waiting for and moving messages ("transport")
+        self.clock = clock
+        self.timing = {"compute": 0.0, "transport": 0.0}
+
+    def _lap(self, key: str, t0: float) -> float:
+        if self.clock is None:
+            return 0.0
+        t = self.clock()
+        self.timing[key] += t - t0
+        return t
 
     def run(self, prm, relu: bool, share: Optional[torch.Tensor], n: int,
             tensor_id: int) -> Optional[torch.Tensor]:
@@ -100,7 +112,9 @@ class PartyProcess:
 
     def _p01(self, prm, relu, share, n, tid, buf):
         me, other = self.party, 1 - self.party
+        t = self.clock() if self.clock else 0.0
         w, opn = self.s.local(me, prm, relu, share, tid, buf)
+        t = self._lap("compute", t)
         # round 1: w to P2; the openings between P0 and P1
         reqs = [self.tr.isend(w, me, P2, TAG_W)[0]]
         keep = []
@@ -121,20 +135,27 @@ class PartyProcess:
             opens[me], opens[other] = opn, self.tr.to_device(ob)
         reply = self.tr.to_device(rep) if rep is not None else None
         pre_c1 = self.tr.to_device(pre) if pre is not None else None
-        return self.s.finish(me, prm, relu, share, tid, reply, opens[0], opens[1], pre_c1, buf)
+        t = self._lap("transport", t)
+        out = self.s.finish(me, prm, relu, share, tid, reply, opens[0], opens[1], pre_c1, buf)
+        self._lap("compute", t)
+        return out
 
     def _helper(self, prm, relu, n, tid, buf):
+        t = self.clock() if self.clock else 0.0
         r0, w0 = self.tr.irecv(buf["w"], P0, TAG_W)
         r1, w1 = self.tr.irecv(buf["w"], P1, TAG_W)
         wait_all([r0, r1])
-        reply, pre_c1 = self.s.helper(prm, relu, tid, self.tr.to_device(w0),
-                                      self.tr.to_device(w1), buf)
+        d0, d1 = self.tr.to_device(w0), self.tr.to_device(w1)
+        t = self._lap("transport", t)
+        reply, pre_c1 = self.s.helper(prm, relu, tid, d0, d1, buf)
+        t = self._lap("compute", t)
         reqs, keep = [], []
-        for dst, t, tag in ([(P1, reply, TAG_REPLY)] if not relu else
-                            [(P0, reply, TAG_REPLY), (P1, reply, TAG_REPLY),
-                             (P1, pre_c1, TAG_PRE)]):
-            r, payload = self.tr.isend(t, P2, dst, tag)
+        for dst, msg, tag in ([(P1, reply, TAG_REPLY)] if not relu else
+                              [(P0, reply, TAG_REPLY), (P1, reply, TAG_REPLY),
+                               (P1, pre_c1, TAG_PRE)]):
+            r, payload = self.tr.isend(msg, P2, dst, tag)
             reqs.append(r)
             keep.append(payload)
         wait_all(reqs)
+        self._lap("transport", t)
         return None

@@ -4,6 +4,7 @@ Alg. relu send them, from the right sender, and every message is counted per
 direction.  The stages here are stand-ins that write known values; the GPU
 test of the real stages is in test_gpu_parties.py."""
 import os
+import time
 import socket
 
 import numpy as np
@@ -60,10 +61,11 @@ def _worker(rank, port, out_dir):
     res = {}
     for relu in (False, True):
         tr = Transport(torch.device("cpu"), direct=False)
-        pp = PartyProcess(rank, _stages(), tr)
+        pp = PartyProcess(rank, _stages(), tr, clock=time.perf_counter)
         share = None if rank == 2 else torch.full((N,), 10 + rank, dtype=torch.int64)
         out = pp.run(None, relu, share, N, 7)
-        res[relu] = (None if out is None else out[:4].clone().numpy(), dict(tr.sent))
+        res[relu] = (None if out is None else out[:4].clone().numpy(), dict(tr.sent),
+                     dict(pp.timing))
     np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array([res], dtype=object),
             allow_pickle=True)
     dist.barrier()
@@ -88,3 +90,9 @@ def test_three_party_schedule_gloo(tmp_path):
     assert r[1][True][1] == {(1, 2): wb, (1, 0): lb}
     assert r[2][True][1] == {(2, 0): lb, (2, 1): 2 * lb}
     assert r[2][True][0] is None
+    # with a clock, each party's time splits into its stages and its messages
+    for k in range(3):
+        for relu in (False, True):
+            tm = r[k][relu][2]
+            assert set(tm) == {"compute", "transport"}
+            assert tm["compute"] >= 0 and tm["transport"] > 0
