@@ -80,7 +80,8 @@ def parse():
                          "by the party-separated launches / the RSS protocol")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run the headline in the schedule the autotuner picks on GB300 (grid, "
-                         "one element per thread, key-bit unroll 2) without timing the others "
+                         "one element per thread, the key-bit loop unrolled whole) without timing "
+                         "the others "
                          "first (for profiling: no other launches precede the step's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the headline alone (for profiling): skip e2e, the CPU "
@@ -431,7 +432,7 @@ def headline(args, world, rank, local, dev):
     total = sum(p[0] for p in parts)
     torch.cuda.synchronize()
     best = ({"schedule": 1, "tile_elems": 256, "ctas_per_sm": 0, "elems_per_thread": 1,
-             "slot_unroll": 2} if args.no_autotune else autotune(ctx, items, reps=1,
+             "slot_unroll": 0} if args.no_autotune else autotune(ctx, items, reps=1,
                                                                   use_cache=False))
     cfg = (best["tile_elems"], best["ctas_per_sm"], best["schedule"], best["elems_per_thread"],
            best["slot_unroll"])

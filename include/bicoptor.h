@@ -318,9 +318,9 @@ typedef struct {
  *   ctas_per_sm       resident CTAs per SM of the persistent grid (0 = occupancy)
  *   elems_per_thread  grid schedule: 1, 2 or 4 elements per thread (default 1)
  *   slot_unroll       unroll of the per-element key-bit loop over the lx + 1
- *                     message slots: 1, 2 or 3 (0 = default 2); honoured for
- *                     lx = 24 at l = 64 and lx = 14, 9 at l <= 32, other key
- *                     widths use the default
+ *                     message slots: 1, 2 or 3, or 0 = the default, the whole
+ *                     loop; honoured for lx = 24 at l = 64 and lx = 14, 9 at
+ *                     l <= 32, other key widths run the loop unrolled by 2
  * Results do not depend on any of these (randomness is keyed by tensor id and
  * element index). Values out of range give BC_EINVAL. */
 #define BC_SCHED_PERSISTENT 0

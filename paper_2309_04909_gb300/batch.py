@@ -23,7 +23,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 TILE_CANDIDATES = (128, 256, 512, 1024, 2048)
 EPT_CANDIDATES = (1, 2, 4)
-UNROLL_CANDIDATES = (1, 2, 3)
+UNROLL_CANDIDATES = (0, 2, 3)   # 0: the whole key-bit loop
 
 
 class ReluBatch:
@@ -92,7 +92,7 @@ def time_ms(fn, reps: int = 5, warmup: int = 2) -> float:
 def _mix_key(items) -> str:
     rings = sorted({(it[0].ring_bits, it[0].lx) for it in items})
     total = sum(it[1].numel() for it in items)
-    return (f"v2|{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}"
+    return (f"v3|{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}"
             f"|t{len(items)}")
 
 

@@ -16,10 +16,16 @@
 // unroll.
 #include "bc_element.cuh"
 
-// Tuning knob of the grid-schedule kernel (compile-time): the minimum resident
-// CTAs per SM requested from the register allocator (0 = let it choose).
+// The minimum resident CTAs per SM requested from the register allocator for
+// the one-element-per-thread grid kernels of key widths lx >= 14 with the slot
+// loop unrolled whole (compile-time; 0 = let it choose).  Left to itself the
+// allocator takes 51-52 registers there (4 CTAs of 256 threads); six CTAs
+// keep them at 40 registers without spilling, which is faster.  The other
+// kernels are left free: shorter loops already fit in 40 registers, the
+// partly unrolled loops ran slower under the bound, and the multi-element and
+// persistent kernels would spill.
 #ifndef BC_BATCH_MIN_CTAS
-#define BC_BATCH_MIN_CTAS 0
+#define BC_BATCH_MIN_CTAS 6
 #endif
 
 namespace bc {
@@ -109,7 +115,7 @@ __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor
 }
 
 template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>
-__global__ void __launch_bounds__(kBlock, BC_BATCH_MIN_CTAS)
+__global__ void __launch_bounds__(kBlock, (LX >= 14 && EPT == 1 && UNROLL == 0) ? BC_BATCH_MIN_CTAS : 0)
     relu_batch_grid_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
                            const BatchTile* __restrict__ tiles, uint32_t begin,
                            int* __restrict__ status) {
@@ -181,6 +187,8 @@ cudaError_t launch_tuned(const BatchGroup& g, const BatchTensor* tensors, const 
   switch (L.slot_unroll) {
     case 1:
       return launch_sched<Lane, LX, SHORT, 1>(g, tensors, tiles, counter, status, num_sms, L, s);
+    case 2:
+      return launch_sched<Lane, LX, SHORT, 2>(g, tensors, tiles, counter, status, num_sms, L, s);
     case 3:
       return launch_sched<Lane, LX, SHORT, 3>(g, tensors, tiles, counter, status, num_sms, L, s);
     default:

@@ -21,9 +21,12 @@
 #pragma once
 #include "bc_internal.h"
 
-// Default unroll of the message-slot loop (compile-time).
+// Default unroll of the message-slot loop (compile-time).  0: the whole loop
+// when the key width is a compile-time constant (every slot's block index,
+// shared-memory offsets and counter become immediates, so no loop counter,
+// address increment or 64-bit counter add reaches the multiplier pipe), else 2.
 #ifndef BC_SLOT_UNROLL
-#define BC_SLOT_UNROLL 2
+#define BC_SLOT_UNROLL 0
 #endif
 
 // The slot loop's Z_p sums as three-input adds (1) or in their plain form (0).
@@ -185,7 +188,8 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0,
 // column of the shared-memory shuffle table (stride kBlock words).
 // DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
 // (the RSS protocol finishes differently).  UNROLL: unroll of the loop over
-// the lx + 1 message slots (the key-bit loop).  r2tab (optional): the CTA's
+// the lx + 1 message slots (the key-bit loop); 0 = all of it for a fixed LX,
+// 2 otherwise.  r2tab (optional): the CTA's
 // table of round2_product(tensor_id, b) for b = 0 .. lx, shared by its threads.
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false,
           int UNROLL = kSlotUnroll>
@@ -239,7 +243,8 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
   uint32_t any_zero = 0;
   const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
   uint64_t mb = 0;   // M1 * slot, the round-1 product of the slot's mask block
-#pragma unroll UNROLL
+  constexpr int kUnroll = UNROLL > 0 ? UNROLL : (LX ? LX + 1 : 2);
+#pragma unroll kUnroll
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     uint32_t w0, w1;
     const U32x4 rz =

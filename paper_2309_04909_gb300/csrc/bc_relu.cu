@@ -4,19 +4,28 @@
 // bc_element.cuh; the batched kernels are in bc_batch.cu.
 #include "bc_element.cuh"
 
-// Tuning knob of the single-tensor kernels (compile-time): the minimum resident
-// CTAs per SM requested from the register allocator (0 = let it choose).
+// The minimum resident CTAs per SM requested from the register allocator for
+// the l = 64, lx = 24 single-tensor and fused-step kernels (compile-time; 0 =
+// let it choose).  With the slot loop unrolled whole the allocator takes 48
+// registers (5 CTAs of 256 threads); six CTAs keep those kernels at 40
+// registers without spilling.  Other instantiations (audit buffers, other key
+// widths or rings) would spill under the same bound and are left free.
 #ifndef BC_RELU_MIN_CTAS
-#define BC_RELU_MIN_CTAS 0
+#define BC_RELU_MIN_CTAS 6
 #endif
 
 namespace bc {
 namespace {
 
+template <typename Lane, int LX, bool SHORT, bool AUDIT>
+constexpr int relu_min_ctas() {
+  return (sizeof(Lane) == 8 && LX == 24 && SHORT && !AUDIT) ? BC_RELU_MIN_CTAS : 0;
+}
+
 // One element per thread; the grid covers the tensor once, so the CTA
 // scheduler hands out work as CTAs retire (no static tail).
 template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT>
-__global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
+__global__ void __launch_bounds__(kBlock, (relu_min_ctas<Lane, LX, SHORT, AUDIT>()))
     relu_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
                 uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, const AuditPtrs aud) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
@@ -203,7 +212,7 @@ cudaError_t launch_lx(const ReluConsts& k, const void* sh0, const void* sh1, uin
 // of other warps hides their latency.
 // ---------------------------------------------------------------------------
 template <typename Lane, int LX, bool SHORT>
-__global__ void __launch_bounds__(kBlock, BC_RELU_MIN_CTAS)
+__global__ void __launch_bounds__(kBlock, (relu_min_ctas<Lane, LX, SHORT, false>()))
     linear_relu_kernel(const LinearConsts c, const LinearIo io, uint64_t n) {
   __shared__ uint32_t perm_s[(LX ? LX + 1 : kMaxSlots) * kBlock];
   __shared__ uint64_t r2_s[kMaxSlots + 2];   // the ReLU's table, then the product's (b = 0, 1)

@@ -331,7 +331,8 @@ def test_batch_matches_single_calls(ctx):
     # (tile, schedule, CTAs per SM, elements per thread, key-bit unroll)
     for tile, sched, cps, ept, unroll in ((0, 0, 0, 0, 0), (1000, 0, 2, 0, 3), (4096, 0, 1, 0, 1),
                                           (0, 1, 0, 0, 0), (0, 1, 0, 2, 1), (0, 1, 0, 4, 3),
-                                          (0, 1, 0, 4, 2)):
+                                          (0, 1, 0, 4, 2), (0, 1, 0, 1, 2), (0, 1, 0, 2, 0),
+                                          (512, 0, 0, 0, 2)):
         for it in items:
             it[3].fill_(0)
             it[4].fill_(0)
