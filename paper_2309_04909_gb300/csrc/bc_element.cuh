@@ -42,6 +42,14 @@
 #define BC_ALU_ADDS 1
 #endif
 
+// For a fixed key width, interleave the shuffle with the slot loop (1: each
+// slot's message right after the shuffle step that fixes its window index,
+// so the shared-memory swaps overlap the multiplier work) or shuffle first
+// (0).  The values are unchanged.
+#ifndef BC_INTERLEAVE
+#define BC_INTERLEAVE 1
+#endif
+
 namespace bc {
 
 
@@ -184,26 +192,19 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0,
   return (M::add(w0, w1, p) == 0u) ? 1u : 0u;
 }
 
-// Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
-// column of the shared-memory shuffle table (stride kBlock words).
-// DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
-// (the RSS protocol finishes differently).  UNROLL: unroll of the loop over
-// the lx + 1 message slots (the key-bit loop); 0 = all of it for a fixed LX,
-// 2 otherwise.  r2tab (optional): the CTA's
-// table of round2_product(tensor_id, b) for b = 0 .. lx, shared by its threads.
-template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false,
-          int UNROLL = kSlotUnroll>
-__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
-                                                 uint32_t tensor_id, Lane s0, Lane s1,
-                                                 uint64_t elem, uint32_t* perm, Lane& out0,
-                                                 Lane& out1, const AuditPtrs& aud,
-                                                 uint64_t out_idx,
-                                                 const uint64_t* r2tab = nullptr) {
+// Steps 1-9 of one element, shuffle first: the seed01 stream gives t and
+// the Fisher-Yates shuffle of the lx + 1 slots, then every message slot k
+// runs steps 3-9 on the window index perm[k].  Returns DReLU' (1 if some
+// w_k is zero); t is the flip bit.
+template <typename Lane, int LX, bool SHORT, bool AUDIT, int UNROLL>
+__device__ __forceinline__ uint32_t slots_after_shuffle(const ReluConsts& k, const RoundKeys& rk,
+                                                        const ElemPhilox& ep, Lane s0, Lane s1,
+                                                        uint32_t* perm, const AuditPtrs& aud,
+                                                        uint64_t out_idx, const uint64_t* r2tab,
+                                                        uint32_t& t_out) {
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
   const uint32_t L = lx + 1;
   const Lane mask = (Lane)k.ring_mask;
-  const ElemPhilox ep(elem, tensor_id);
-
   // ---- seed01 stream: t (step 1) and the shuffle words (step 6) ----------
 #pragma unroll
   for (uint32_t s = 0; s < (LX ? (uint32_t)(LX + 1) : (uint32_t)kMaxSlots); ++s) {
@@ -255,6 +256,96 @@ __device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const Roun
       if (aud.w1) aud.w1[out_idx * L + slot] = w1;
     }
   }
+  t_out = t;
+  return any_zero;
+}
+
+// The same steps with the shuffle and the slots interleaved (fixed key width
+// only): Fisher-Yates from the top leaves position j final once step j has
+// run, so slot j's message follows its shuffle step directly, with window
+// index the value just swapped into position j; the slots are taken in the
+// order lx, ..., 1, 0, and their zero tests are OR-ed as before.
+template <typename Lane, int LX, bool SHORT, bool AUDIT>
+__device__ __forceinline__ uint32_t slots_with_shuffle(const ReluConsts& k, const RoundKeys& rk,
+                                                       const ElemPhilox& ep, Lane s0, Lane s1,
+                                                       uint32_t* perm, const AuditPtrs& aud,
+                                                       uint64_t out_idx, const uint64_t* r2tab,
+                                                       uint32_t& t_out) {
+  constexpr uint32_t L = LX + 1;
+  const Lane mask = (Lane)k.ring_mask;
+#pragma unroll
+  for (uint32_t s = 0; s < L; ++s) perm[s * kBlock] = s;
+  const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
+  const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
+  uint32_t t = 0, any_zero = 0;
+  Lane f0 = s0, nf1 = s1;
+#pragma unroll
+  for (uint32_t b = 0; b < (L + 3) / 4; ++b) {
+    const uint64_t mbp = (uint64_t)kPhiloxM1 * b;
+    const U32x4 wb = r2tab ? perm_stream.block_p0(mbp, r2tab[b], rk) : perm_stream.block(mbp, rk);
+    const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const uint32_t widx = 4 * b + q;
+      if (widx == 0) {
+        t = ws[0] & 1u;                                   // steps 1-2
+        f0 = t ? ring_neg(s0, mask) : s0;
+        nf1 = t ? s1 : ring_neg(s1, mask);
+      } else if (widx < L) {
+        const uint32_t j = L - widx;                      // step 6, then slot j
+        const uint32_t partner = __umulhi(ws[q], j + 1);
+        const uint32_t a = perm[j * kBlock];
+        const uint32_t c = perm[partner * kBlock];
+        perm[j * kBlock] = c;
+        perm[partner * kBlock] = a;
+        const uint64_t mb = (uint64_t)kPhiloxM1 * j;
+        const U32x4 rz =
+            r2tab ? mask_stream.block_p0(mb, r2tab[j], rk) : mask_stream.block(mb, rk);
+        uint32_t w0, w1;
+        any_zero |= slot_zero_test<LX, SHORT>(k, f0, nf1, c, rz, w0, w1);
+        if (AUDIT) {
+          if (aud.w0) aud.w0[out_idx * L + j] = w0;
+          if (aud.w1) aud.w1[out_idx * L + j] = w1;
+        }
+      }
+    }
+  }
+  const U32x4 rz = r2tab ? mask_stream.block_p0(0, r2tab[0], rk) : mask_stream.block(0, rk);
+  uint32_t w0, w1;
+  any_zero |= slot_zero_test<LX, SHORT>(k, f0, nf1, perm[0], rz, w0, w1);   // slot 0
+  if (AUDIT) {
+    if (aud.w0) aud.w0[out_idx * L] = w0;
+    if (aud.w1) aud.w1[out_idx * L] = w1;
+  }
+  t_out = t;
+  return any_zero;
+}
+
+// Alg. drelu / Alg. relu for one element.  `perm` points at this thread's
+// column of the shared-memory shuffle table (stride kBlock words).
+// DPONLY: stop after P2's step 9 and return DReLU' in out0 and t in out1
+// (the RSS protocol finishes differently).  UNROLL: unroll of the loop over
+// the lx + 1 message slots (the key-bit loop); 0 = all of it for a fixed LX,
+// 2 otherwise.  r2tab (optional): the CTA's
+// table of round2_product(tensor_id, b) for b = 0 .. lx, shared by its threads.
+template <typename Lane, int LX, bool SHORT, bool RELU, bool AUDIT, bool DPONLY = false,
+          int UNROLL = kSlotUnroll>
+__device__ __forceinline__ void bicoptor_element(const ReluConsts& k, const RoundKeys& rk,
+                                                 uint32_t tensor_id, Lane s0, Lane s1,
+                                                 uint64_t elem, uint32_t* perm, Lane& out0,
+                                                 Lane& out1, const AuditPtrs& aud,
+                                                 uint64_t out_idx,
+                                                 const uint64_t* r2tab = nullptr) {
+  const Lane mask = (Lane)k.ring_mask;
+  const ElemPhilox ep(elem, tensor_id);
+
+  uint32_t t;
+  const uint32_t any_zero =
+      (BC_INTERLEAVE && LX)
+          ? slots_with_shuffle<Lane, (LX ? LX : 1), SHORT, AUDIT>(k, rk, ep, s0, s1, perm, aud,
+                                                                  out_idx, r2tab, t)
+          : slots_after_shuffle<Lane, LX, SHORT, AUDIT, UNROLL>(k, rk, ep, s0, s1, perm, aud,
+                                                                out_idx, r2tab, t);
   const uint32_t dprime = any_zero;
   if (DPONLY) {
     out0 = (Lane)dprime;
