@@ -39,8 +39,8 @@ WORKLOAD = ("ResNet-18 224x224 ReLU set x{images} images, once in Z_2^64 (f=16, 
 BASE_SEED = 0xB1C0_2309_0490_9000
 # DRAM bytes per element of the batched kernel over both rings: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the two launches of one step
-# of a 4-image set (358.2 MB), divided by its 18,464,768 elements
-TRAFFIC_PER_ELEM_BATCH = 19.40
+# of a 4-image set (359.5 MB), divided by its 18,464,768 elements
+TRAFFIC_PER_ELEM_BATCH = 19.47
 # the fused step of a linear layer (reported beside the headline)
 FUSED_WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
                   "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated "
@@ -49,8 +49,8 @@ N_DEFAULT = 1 << 22
 RING, FRAC, K_TRUNC, LX, KEY_OFF = 64, 16, 16, 24, 0
 SEED = 1
 # DRAM bytes per element of the fused step kernel: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one 2^21-element launch (89.92 MB) / its elements
-TRAFFIC_PER_ELEM = 42.88
+# dram__bytes_write.sum of one 2^21-element launch (90.23 MB) / its elements
+TRAFFIC_PER_ELEM = 43.02
 
 
 def parse():
@@ -944,7 +944,8 @@ def chain_only(args, ctx, prm, x0, x1, y0, y1, buf, n, world, dev):
     line = {"metric": METRIC, "value": n * world / (total / 1e3), "unit": "elems/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (four launches)", "n": n},
+            "data": "synthetic",
+            "config": {"workload": FUSED_WORKLOAD + " (four launches)", "n": n},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "T int32 multiply lane-ops/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "relu_kernel<uint64_t,24,SHORT,ReLU>",

@@ -31,7 +31,36 @@ __device__ __forceinline__ uint64_t shr64(uint64_t a, uint32_t s) {
   return s >= 64 ? 0 : a >> s;
 }
 
-template <typename Lane, bool RELU>
+// Steps 3-9 of one message slot whose window offset is pos (= perm[slot]):
+// the recursive sums of both parties, the mask r_k and reshare z_k from the
+// slot's seed01 block, and P2's zero test.  mb = M1 * slot, the round-1
+// product of the slot's mask block.
+template <typename Lane>
+__device__ __forceinline__ uint32_t b1_slot(const ReluConsts& k, const StreamPhilox& mask_stream,
+                                            const uint64_t* r2, uint32_t slot, uint64_t mb,
+                                            uint32_t pos, uint64_t a, uint64_t b, uint64_t top0,
+                                            uint64_t top1, uint64_t mask, Lane* w0, Lane* w1,
+                                            uint64_t wi) {
+  const uint32_t sh = k.c + pos;
+  const uint64_t v0 = (floor_sum(a >> sh) - top0 - 1) & mask;       // S0 - 1 (P0)
+  const uint64_t v1 = (top1 - floor_sum(b >> sh)) & mask;           // S1 = -(sum for b)
+  const U32x4 rz = mask_stream.block_p0(mb, r2[slot], k.rk);
+  const uint64_t r = (((uint64_t)rz.y << 32) | rz.x) | 1u;           // odd: a unit
+  const uint64_t z = ((uint64_t)rz.w << 32) | rz.z;
+  const uint64_t m0 = (v0 * r + z) & mask;                           // P0 -> P2
+  const uint64_t m1 = (v1 * r - z) & mask;                           // P1 -> P2
+  if (w0) {
+    w0[wi + slot] = (Lane)m0;
+    w1[wi + slot] = (Lane)m1;
+  }
+  return ((m0 + m1) & mask) == 0 ? 1u : 0u;                         // step 9
+}
+
+// LX: the key width as a compile-time constant (0 = read from k).  For a
+// fixed width the slots run unrolled and interleaved with the shuffle (slot j
+// right after the Fisher-Yates step that fixes position j), as in the
+// Bicoptor 2.0 kernels, so the two protocols are compared in the same form.
+template <typename Lane, bool RELU, int LX>
 __global__ void __launch_bounds__(kBlock)
     b1_kernel(const ReluConsts k, const Lane* __restrict__ sh0, const Lane* __restrict__ sh1,
               uint64_t n, Lane* __restrict__ o0, Lane* __restrict__ o1, Lane* __restrict__ w0,
@@ -43,60 +72,79 @@ __global__ void __launch_bounds__(kBlock)
   const uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const RoundKeys& rk = k.rk;
-  const uint32_t lx = k.lx, L = lx + 1;
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx, L = lx + 1;
   const uint64_t mask = k.ring_mask;
   const ElemPhilox ep(k.elem_base + i, k.tensor_id);
   uint32_t* perm = perm_s + threadIdx.x;
-
-  // steps 1 and 6: t and the Fisher-Yates shuffle from the seed01 stream
-  for (uint32_t s = 0; s < L; ++s) perm[s * kBlock] = s;
-  uint32_t t = 0;
+  const uint64_t s0 = (uint64_t)sh0[i], s1 = (uint64_t)sh1[i];
+  const uint32_t top = k.c + lx + 1;
   const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
-  for (uint32_t b = 0; b < (L + 3) >> 2; ++b) {
-    const U32x4 wb = perm_stream.block_p0((uint64_t)kPhiloxM1 * b, r2_s[b], rk);
-    const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+  const StreamPhilox mask_stream(ep, kPair01, kPurB1Mask, rk);
+  uint32_t t = 0, any_zero = 0;
+  // steps 1-2: flip; P0 keeps its flipped share a, P1 b = 2^l - its flipped share
+  uint64_t a = 0, b = 0, top0 = 0, top1 = 0;
+  auto flip = [&](uint32_t tt) {
+    a = tt ? (0 - s0) & mask : s0;
+    b = tt ? s1 : (0 - s1) & mask;
+    top0 = floor_sum(shr64(a, top));
+    top1 = floor_sum(shr64(b, top));
+  };
+
+  if (LX) {
 #pragma unroll
-    for (uint32_t q = 0; q < 4; ++q) {
-      const uint32_t widx = 4 * b + q;
-      if (widx == 0) {
-        t = ws[0] & 1u;
-      } else if (widx < L) {
-        const uint32_t j = L - widx;
-        const uint32_t partner = __umulhi(ws[q], j + 1);
-        const uint32_t a = perm[j * kBlock];
-        const uint32_t c = perm[partner * kBlock];
-        perm[j * kBlock] = c;
-        perm[partner * kBlock] = a;
+    for (uint32_t s = 0; s < L; ++s) perm[s * kBlock] = s;
+#pragma unroll
+    for (uint32_t blk = 0; blk < (L + 3) / 4; ++blk) {
+      const U32x4 wb = perm_stream.block_p0((uint64_t)kPhiloxM1 * blk, r2_s[blk], rk);
+      const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t widx = 4 * blk + q;
+        if (widx == 0) {
+          t = ws[0] & 1u;
+          flip(t);
+        } else if (widx < L) {
+          const uint32_t j = L - widx;                       // step 6, then slot j
+          const uint32_t partner = __umulhi(ws[q], j + 1);
+          const uint32_t pa = perm[j * kBlock];
+          const uint32_t pc = perm[partner * kBlock];
+          perm[j * kBlock] = pc;
+          perm[partner * kBlock] = pa;
+          any_zero |= b1_slot<Lane>(k, mask_stream, r2_s, j, (uint64_t)kPhiloxM1 * j, pc, a, b,
+                                    top0, top1, mask, w0, w1, i * L);
+        }
       }
     }
-  }
-
-  // steps 1-2: flip; P0 keeps its flipped share a, P1 b = 2^l - its flipped share
-  const uint64_t s0 = (uint64_t)sh0[i], s1 = (uint64_t)sh1[i];
-  const uint64_t a = t ? (0 - s0) & mask : s0;
-  const uint64_t b = t ? s1 : (0 - s1) & mask;
-  const uint32_t top = k.c + lx + 1;
-  const uint64_t top0 = floor_sum(shr64(a, top)), top1 = floor_sum(shr64(b, top));
-
-  // steps 3-9 per message slot
-  uint32_t any_zero = 0;
-  const StreamPhilox mask_stream(ep, kPair01, kPurB1Mask, rk);
-  uint64_t mb = 0;
-#pragma unroll 2
-  for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
-    const uint32_t sh = k.c + perm[slot * kBlock];
-    const uint64_t v0 = (floor_sum(a >> sh) - top0 - 1) & mask;       // S0 - 1 (P0)
-    const uint64_t v1 = (top1 - floor_sum(b >> sh)) & mask;           // S1 = -(sum for b)
-    const U32x4 rz = mask_stream.block_p0(mb, r2_s[slot], rk);
-    const uint64_t r = (((uint64_t)rz.y << 32) | rz.x) | 1u;           // odd: a unit
-    const uint64_t z = ((uint64_t)rz.w << 32) | rz.z;
-    const uint64_t m0 = (v0 * r + z) & mask;                           // P0 -> P2
-    const uint64_t m1 = (v1 * r - z) & mask;                           // P1 -> P2
-    any_zero |= ((m0 + m1) & mask) == 0 ? 1u : 0u;                     // step 9
-    if (w0) {
-      w0[i * L + slot] = (Lane)m0;
-      w1[i * L + slot] = (Lane)m1;
+    any_zero |= b1_slot<Lane>(k, mask_stream, r2_s, 0, 0, perm[0], a, b, top0, top1, mask, w0,
+                              w1, i * L);
+  } else {
+    // steps 1 and 6: t and the Fisher-Yates shuffle from the seed01 stream
+    for (uint32_t s = 0; s < L; ++s) perm[s * kBlock] = s;
+    for (uint32_t blk = 0; blk < (L + 3) >> 2; ++blk) {
+      const U32x4 wb = perm_stream.block_p0((uint64_t)kPhiloxM1 * blk, r2_s[blk], rk);
+      const uint32_t ws[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t widx = 4 * blk + q;
+        if (widx == 0) {
+          t = ws[0] & 1u;
+        } else if (widx < L) {
+          const uint32_t j = L - widx;
+          const uint32_t partner = __umulhi(ws[q], j + 1);
+          const uint32_t pa = perm[j * kBlock];
+          const uint32_t pc = perm[partner * kBlock];
+          perm[j * kBlock] = pc;
+          perm[partner * kBlock] = pa;
+        }
+      }
     }
+    flip(t);
+    // steps 3-9 per message slot
+    uint64_t mb = 0;
+#pragma unroll 2
+    for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1)
+      any_zero |= b1_slot<Lane>(k, mask_stream, r2_s, slot, mb, perm[slot * kBlock], a, b, top0,
+                                top1, mask, w0, w1, i * L);
   }
   const uint32_t dprime = any_zero;
   const Lane lmask = (Lane)mask;
@@ -128,7 +176,14 @@ cudaError_t launch_b1_t(const ReluConsts& k, const void* sh0, const void* sh1, u
   const uint64_t grid = (n + kBlock - 1) / kBlock;
   if (grid == 0) return cudaSuccess;
   if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
-  b1_kernel<Lane, RELU><<<(unsigned)grid, kBlock, 0, s>>>(
+  // the key widths the comparison runs at l = 64 (lx = 24, and the paper's
+  // lx = 7 with c = 24) have fixed-width kernels, as Bicoptor 2.0's do
+  auto kern = b1_kernel<Lane, RELU, 0>;
+  if constexpr (sizeof(Lane) == 8) {
+    if (k.lx == 24) kern = b1_kernel<Lane, RELU, 24>;
+    if (k.lx == 7) kern = b1_kernel<Lane, RELU, 7>;
+  }
+  kern<<<(unsigned)grid, kBlock, 0, s>>>(
       k, static_cast<const Lane*>(sh0), static_cast<const Lane*>(sh1), n,
       static_cast<Lane*>(o0), static_cast<Lane*>(o1), static_cast<Lane*>(w0),
       static_cast<Lane*>(w1));
