@@ -21,6 +21,7 @@ The pre-shared seeds of Sec. 2.1 are the contexts' common 64-bit seed.
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 from typing import Dict, Optional, Tuple
 
@@ -59,6 +60,115 @@ class Transport:
     def to_device(self, buf: torch.Tensor) -> torch.Tensor:
         return buf if self.direct else buf.to(self.device, non_blocking=False)
 
+    def prepare(self, me: int, nbytes: Dict[int, int]) -> None:
+        """Called by every party before a call's messages, with the same
+        sizes (bytes per message kind); nothing to do for this transport."""
+
+
+class _Deferred:
+    """A request whose work runs when it is waited for."""
+
+    def __init__(self, fn):
+        self.fn = fn
+        self.done = False
+
+    def wait(self):
+        if not self.done:
+            self.fn()
+            self.done = True
+        return True
+
+
+class IpcTransport(Transport):
+    """Messages copied by the GPU straight into the receiver's own device
+    memory (CUDA IPC between the parties' processes on one GPU).
+
+    prepare() allocates this party's receive buffer per (sender, message
+    kind) and maps every other party's through their IPC handles, exchanged
+    once over the process group.  A message then takes a handshake of two
+    one-word tokens through the process group:
+      receiver  irecv(): waits for its own stream (its earlier stages are done
+                with the buffer), tells the sender READY, and later waits for
+                DATA before its stage reads the buffer;
+      sender    isend(), when waited for: waits for READY, copies the message
+                into the receiver's buffer on its stream, waits for the copy,
+                then sends DATA.
+    So no kernel of one party waits on another (each stage launches after its
+    inputs have landed), and a buffer is never overwritten while it is read."""
+
+    def __init__(self, device: torch.device, ranks=(0, 1, 2), group=None):
+        super().__init__(device, direct=True, ranks=ranks)
+        self.group = group
+        self.own: Dict[Tuple[int, int], torch.Tensor] = {}      # (src, tag) -> my buffer
+        self.remote: Dict[Tuple[int, int], torch.Tensor] = {}   # (dst, tag) -> its buffer
+        self.sizes: Dict[int, int] = {}
+        self._keep = collections.deque(maxlen=64)   # tokens of the requests in flight
+
+    def prepare(self, me: int, nbytes: Dict[int, int]) -> None:
+        from torch.multiprocessing.reductions import rebuild_cuda_tensor, reduce_tensor
+        if all(self.sizes.get(t, -1) >= b for t, b in nbytes.items()):
+            return
+        self.own.clear()
+        self.remote.clear()
+        self.sizes = dict(nbytes)
+        mine = {}
+        for src in (P0, P1, P2):
+            if src == me:
+                continue
+            for tag, nb in nbytes.items():
+                buf = torch.empty(max(nb, 16), dtype=torch.uint8, device=self.device)
+                self.own[(src, tag)] = buf
+                mine[(src, me, tag)] = reduce_tensor(buf)[1]
+        torch.cuda.synchronize(self.device)
+        parts = [None, None, None]
+        dist.all_gather_object(parts, mine, group=self.group)
+        for part in parts:
+            for (src, dst, tag), args in part.items():
+                if src == me:
+                    self.remote[(dst, tag)] = rebuild_cuda_tensor(*args)
+
+    def _token(self):
+        t = torch.ones(1, dtype=torch.int32)
+        self._keep.append(t)
+        return t
+
+    def isend(self, t: torch.Tensor, src: int, dst: int, tag: int):
+        nb = t.numel() * t.element_size()
+        self.sent[(src, dst)] = self.sent.get((src, dst), 0) + nb
+        target = self.remote[(dst, tag)]
+        if nb > target.numel():
+            raise ValueError("message larger than the receiver's prepared buffer")
+        flat = t.contiguous().view(-1).view(torch.uint8)
+        ready = self._token()
+        r_ready = dist.irecv(ready, self._rank(dst), tag=2 * tag, group=self.group)
+
+        def go():
+            r_ready.wait()
+            target[:nb].copy_(flat)
+            torch.cuda.current_stream(self.device).synchronize()
+            dist.isend(self._token(), self._rank(dst), tag=2 * tag + 1, group=self.group).wait()
+
+        return _Deferred(go), t
+
+    def irecv(self, like: torch.Tensor, src: int, tag: int):
+        nb = like.numel() * like.element_size()
+        own = self.own[(src, tag)]
+        if nb > own.numel():
+            raise ValueError("message larger than the prepared buffer")
+        buf = own[:nb].view(like.dtype).view(like.shape)
+        torch.cuda.current_stream(self.device).synchronize()
+        r_data = dist.irecv(self._token(), self._rank(src), tag=2 * tag + 1, group=self.group)
+        w_ready = dist.isend(self._token(), self._rank(src), tag=2 * tag, group=self.group)
+
+        def done():
+            w_ready.wait()
+            r_data.wait()
+
+        return _Deferred(done), buf
+
+    def to_device(self, buf: torch.Tensor) -> torch.Tensor:
+        return buf
+
 
 def wait_all(reqs):
     for r in reqs:
@@ -77,6 +187,12 @@ class Stages:
 
 def context_stages(ctx) -> Stages:
     return Stages(ctx.party_local, ctx.party_helper, ctx.party_finish, ctx.party_stage_buffers)
+
+
+def message_sizes(buf: Dict[str, torch.Tensor]) -> Dict[int, int]:
+    """Bytes of each message kind of one call, from a party's stage buffers."""
+    nb = lambda k: buf[k].numel() * buf[k].element_size()
+    return {TAG_W: nb("w"), TAG_OPEN: nb("open"), TAG_REPLY: nb("reply"), TAG_PRE: nb("pre_c1")}
 
 
 class PartyProcess:
@@ -106,6 +222,7 @@ class PartyProcess:
     def run(self, prm, relu: bool, share: Optional[torch.Tensor], n: int,
             tensor_id: int) -> Optional[torch.Tensor]:
         buf = self.s.buffers(prm, n)
+        self.tr.prepare(self.party, message_sizes(buf))
         if self.party == P2:
             return self._helper(prm, relu, n, tensor_id, buf)
         return self._p01(prm, relu, share, n, tensor_id, buf)

@@ -124,15 +124,17 @@ def test_parties_empty_input():
 THREE_SEED = 0x3B0C_E550
 
 
-def _three_worker(rank, port, out_dir, cases):
+def _three_worker(rank, port, out_dir, cases, transport="gloo"):
     import os as _os
     import torch.distributed as dist
     from paper_2309_04909_gb300 import Context, Params, workloads as W
-    from paper_2309_04909_gb300.parties import PartyProcess, Transport, context_stages
+    from paper_2309_04909_gb300.parties import (IpcTransport, PartyProcess, Transport,
+                                                context_stages)
     _os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=3)
     torch.cuda.set_device(0)
     ctx = Context(THREE_SEED)
+    ipc = IpcTransport(torch.device("cuda", 0)) if transport == "ipc" else None
     res = {}
     for ci, (ring, lx, c, mag, n, relu) in enumerate(cases):
         prm = Params(ring, lx, c)
@@ -141,22 +143,36 @@ def _three_worker(rank, port, out_dir, cases):
         x = W.magnitude_bounded_ints(n, mag, seed=ci)
         s0, s1 = ctx.share(ring, torch.from_numpy(x).cuda(), 50 + ci)
         share = (s0, s1, None)[rank]
-        tr = Transport(torch.device("cuda", 0), direct=False)
+        tr = ipc if ipc is not None else Transport(torch.device("cuda", 0), direct=False)
+        tr.sent = {}
         ctx.reset_comm()
-        out = PartyProcess(rank, context_stages(ctx), tr).run(prm, relu, share, n, 60 + ci)
+        pp = PartyProcess(rank, context_stages(ctx), tr)
+        out = pp.run(prm, relu, share, n, 60 + ci)
+        if transport == "ipc":            # the same call again through the same buffers
+            torch.cuda.synchronize()
+            first = None if out is None else out.clone()
+            tr.sent = {}
+            ctx.reset_comm()
+            out = pp.run(prm, relu, share, n, 60 + ci)
+            assert first is None or torch.equal(first, out)
         torch.cuda.synchronize()
         res[ci] = (None if out is None else out.cpu().numpy(), dict(tr.sent), ctx.comm())
     np.save(_os.path.join(out_dir, f"p{rank}.npy"), np.array([res], dtype=object),
             allow_pickle=True)
+    del ipc
+    torch.cuda.synchronize()
     dist.barrier()
     dist.destroy_process_group()
     ctx.close()
 
 
-def test_three_processes_match_fused_and_oracle(tmp_path):
+@pytest.mark.parametrize("transport", ["gloo", "ipc"])
+def test_three_processes_match_fused_and_oracle(tmp_path, transport):
     """Each party in its own process and context: P0 and P1 send their
     packed w messages to P2 (and their openings to each other), P2 replies;
-    every message moves through the transport into the receiver's memory.
+    every message moves through the transport into the receiver's memory:
+    through host memory (gloo), or copied by the GPU into the receiver's own
+    device buffer (CUDA IPC, twice through the same buffers).
     The output shares equal the fused kernel's and the oracle's bit for bit,
     and the three contexts' bit counters add up to the fused call's."""
     import socket
@@ -167,8 +183,8 @@ def test_three_processes_match_fused_and_oracle(tmp_path):
     sock.bind(("127.0.0.1", 0))
     port = sock.getsockname()[1]
     sock.close()
-    mp.start_processes(_three_worker, args=(port, str(tmp_path), cases), nprocs=3, join=True,
-                       start_method="spawn")
+    mp.start_processes(_three_worker, args=(port, str(tmp_path), cases, transport), nprocs=3,
+                       join=True, start_method="spawn")
     r = [np.load(tmp_path / f"p{k}.npy", allow_pickle=True)[0] for k in range(3)]
     ctx = Context(THREE_SEED)
     for ci, (ring, lx, c, mag, n, relu) in enumerate(cases):
