@@ -68,6 +68,10 @@ def parse():
                          "ReLU of --n elements with P0, P1 and P2 as three processes on GPU 0, "
                          "messages through host memory (gloo), per-party compute and transport "
                          "time")
+    ap.add_argument("--party-transport", default="ipc", choices=["ipc", "gloo"],
+                    help="with --workload parties3 -- ipc: each message copied by the GPU into "
+                         "the receiver's own device buffer (CUDA IPC), token handshake over "
+                         "gloo; gloo: messages through host memory")
     ap.add_argument("--images", type=int, default=RESNET_IMAGES,
                     help="images of the ResNet-18 set (32 in the workload; fewer for profiling)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -507,6 +511,61 @@ def headline(args, world, rank, local, dev):
     ctx.close()
 
 
+_LINK = {}
+
+
+def host_link_gbps(nbytes: int = 256 << 20, reps: int = 4) -> dict:
+    """This machine's host link, measured once per process with copy engines:
+    H2D alone, D2H alone and both at once (pinned buffers, CUDA events on
+    two streams).  The e2e rooflines divide by the bidirectional figure; it
+    differs between boxes of the pool (316-340 GB/s on most, about 130 on
+    one), so a fixed constant would misstate the fraction."""
+    import torch
+    if _LINK:
+        return _LINK
+    n = nbytes // 4
+    h_in = torch.ones(n, dtype=torch.int32).pin_memory()
+    h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    d_in = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_out = torch.ones(n, dtype=torch.int32, device="cuda")
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(up: bool, down: bool) -> float:
+        for _ in range(2):
+            if up:
+                with torch.cuda.stream(s_up):
+                    d_in.copy_(h_in, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s_down):
+                    h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        ends = []
+        for st, on in ((s_up, up), (s_down, down)):
+            if not on:
+                continue
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                for _ in range(reps):
+                    if st is s_up:
+                        d_in.copy_(h_in, non_blocking=True)
+                    else:
+                        h_out.copy_(d_out, non_blocking=True)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                ends.append(e)
+        torch.cuda.synchronize()
+        ms = max(start.elapsed_time(e) for e in ends)
+        return (int(up) + int(down)) * reps * nbytes / (ms * 1e-3) / 1e9
+
+    _LINK.update({"h2d_GBps": timed(True, False), "d2h_GBps": timed(False, True),
+                  "both_GBps": timed(True, True),
+                  "how": "copy engines, pinned 256 MB buffers, H2D and D2H on two streams at "
+                         "once for both_GBps; measured on this box before the e2e run"})
+    return _LINK
+
+
 def headline_e2e(ctx, items, cfg, steps, world, dev):
     """The headline step through the host-buffer entry point
     (bc_relu_batch_host): the input shares in page-locked host memory, the
@@ -552,7 +611,8 @@ def headline_e2e(ctx, items, cfg, steps, world, dev):
         run()
     dt = max_over_ranks(time.perf_counter() - t0, device=dev)
     total = sum(it[1].numel() for it in items)
-    link = 333.0   # GB/s both directions at once, measured on this machine's GB300 host link
+    meas = host_link_gbps()
+    link = meas["both_GBps"]
     value = total * steps * world / dt
     return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": h2d * world,
             "d2h_bytes_per_step": d2h * world, "steps": steps, "equal_to_device_run": equal,
@@ -562,7 +622,8 @@ def headline_e2e(ctx, items, cfg, steps, world, dev):
                    "plan + run + synchronise every step",
             "link_roofline": {"bytes_per_step": h2d + d2h, "link_GBps": link,
                               "bound_elems_per_s": world * link * 1e9 * total / (h2d + d2h),
-                              "frac": value / (world * link * 1e9 * total / (h2d + d2h))}}
+                              "frac": value / (world * link * 1e9 * total / (h2d + d2h)),
+                              "link": meas}}
 
 
 def oracle_relu_sample(ctx, items, per_ring, threads):
@@ -827,6 +888,8 @@ def run_extras(args, line, ctx, prm, x0, x1, y0, y1, xi, yi, buf, n, kern_ms, de
     extra("cpu_baseline_batched_configs", lambda: cpu_configs(_threads()))
     extra("drelu_l32_uniform", lambda: uniform_l32_drelu_check(ctx, dev))
     extra("size_sweep_l64", lambda: size_sweep(ctx, dev))
+    if "error" not in line.get("size_sweep_l64", {"error": 1}):
+        extra("network_projection", lambda: network_projection(line["size_sweep_l64"]))
     extra("batched_vs_plain", lambda: vgg16_batched_vs_plain(ctx, dev))
     bvp = line["batched_vs_plain"]
     if "batched_elems_per_s" in bvp:
@@ -1020,14 +1083,15 @@ def e2e_all_ranks(ctx, prm, x0, x1, y0, y1, n, steps, world, dev):
         ctx.linear_relu_host(RING, K_TRUNC, prm, *hx, tensor_id=3, out=out)
     dt = max_over_ranks(time.perf_counter() - t0, device=dev)
     value = n * steps * world / dt
-    link = 333.0   # GB/s both directions at once, measured on this machine's GB300 host link
+    meas = host_link_gbps()
+    link = meas["both_GBps"]
     return {"value": value, "unit": "elems/s", "h2d_bytes_per_step": 4 * 8 * n * world,
             "d2h_bytes_per_step": 4 * 8 * n * world, "steps": steps,
             "api": "bc_linear_relu_host, pinned host buffers, default path (direct: the fused "
                    "kernel loads and stores them across the host link)",
             "link_roofline": {"bytes_per_element": 64, "link_GBps": link,
                               "bound_elems_per_s": world * link * 1e9 / 64,
-                              "frac": value / (world * link * 1e9 / 64)}}
+                              "frac": value / (world * link * 1e9 / 64), "link": meas}}
 
 
 def e2e_paths(ctx, prm, x0, x1, y0, y1, n, steps, buf):
@@ -1257,12 +1321,13 @@ def b1_pair(args, local, dev):
     ctx.close()
 
 
-def _parties3_worker(rank, port, out_dir, n, steps, warmup):
+def _parties3_worker(rank, port, out_dir, n, steps, warmup, transport="ipc"):
     """One party of `--workload parties3` (rank = party)."""
     import torch
     import torch.distributed as dist
     from paper_2309_04909_gb300 import Context, Params, workloads as W
-    from paper_2309_04909_gb300.parties import PartyProcess, Transport, context_stages
+    from paper_2309_04909_gb300.parties import (IpcTransport, PartyProcess, Transport,
+                                                context_stages)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=3)
     torch.cuda.set_device(0)
@@ -1277,7 +1342,7 @@ def _parties3_worker(rank, port, out_dir, n, steps, warmup):
         torch.cuda.synchronize()
         return time.perf_counter()
 
-    tr = Transport(dev, direct=False)
+    tr = IpcTransport(dev) if transport == "ipc" else Transport(dev, direct=False)
     pp = PartyProcess(rank, context_stages(ctx), tr, clock=clock)
     walls, out = [], None
     for i in range(warmup + steps):
@@ -1302,6 +1367,8 @@ def _parties3_worker(rank, port, out_dir, n, steps, warmup):
            "identical_to_fused": same}
     with open(os.path.join(out_dir, f"p{rank}.json"), "w") as fh:
         json.dump(res, fh)
+    del pp, tr
+    torch.cuda.synchronize()
     dist.barrier()
     dist.destroy_process_group()
     ctx.close()
@@ -1310,7 +1377,9 @@ def _parties3_worker(rank, port, out_dir, n, steps, warmup):
 def parties3(args):
     """`--workload parties3`: the ReLU of --n elements (l = 64, lx = 24) with
     P0, P1 and P2 as three processes, each with its own context on GPU 0, every
-    message moved through host memory by gloo into the receiver's memory.  One
+    message moved into the receiver's memory: copied by the GPU into the
+    receiver's device buffer (--party-transport ipc, CUDA IPC, with a token
+    handshake over gloo) or through host memory by gloo.  One
     JSON line: elements/s over the slowest party's step time, each party's
     compute and transport time per step, the bytes each sent, and whether P0's
     and P1's outputs equal the fused kernel's."""
@@ -1322,7 +1391,8 @@ def parties3(args):
     sock.close()
     with tempfile.TemporaryDirectory() as d:
         mp.start_processes(_parties3_worker, nprocs=3, join=True, start_method="spawn",
-                           args=(port, d, args.n, args.steps, args.warmup))
+                           args=(port, d, args.n, args.steps, args.warmup,
+                                 args.party_transport))
         r = [json.load(open(os.path.join(d, f"p{k}.json"))) for k in range(3)]
     step_s = statistics.median(r[0]["step_s"])
     print(json.dumps({
@@ -1330,7 +1400,11 @@ def parties3(args):
         "value": args.n / step_s, "unit": "elems/s", "ms_per_step": step_s * 1e3,
         "steps": args.steps, "warmup": args.warmup,
         "config": {"workload": f"ReLU, l=64 lx=24, n={args.n}, P0/P1/P2 as processes on one "
-                               "GPU, gloo through host memory"},
+                               "GPU, " + ("messages copied by the GPU into the receiver's "
+                                          "device memory (CUDA IPC), tokens over gloo"
+                                          if args.party_transport == "ipc" else
+                                          "gloo through host memory"),
+                   "transport": args.party_transport},
         "parties": {f"P{x['party']}": {k: x[k] for k in ("compute_s", "transport_s",
                                                           "sent_bytes_per_step",
                                                           "identical_to_fused")} for x in r},
@@ -1390,6 +1464,53 @@ def parties_bench(ctx, prm, buf, n, fused_ms):
             "message_bytes_per_element": msg_bytes / n,
             "protocol_bits_per_element_p0_to_p2": (prm.lx + 1) ** 2,
             "identical_to_fused": same, "launches": 3}
+
+
+# The paper's measured throughput (ops/s) of its DReLU and ReLU at lx = 7 on
+# three P100 servers, from its DReLU and ReLU tables (Sec. 7): context beside
+# the projection below, another machine's numbers.
+PAPER_OPS = {
+    "drelu": {"LAN1": {"1e3": 1002646.99, "1e4": 7268181.36, "1e5": 17547892.59,
+                       "1e6": 17062429.72},
+              "LAN2": {"1e3": 713210.80, "1e4": 3898498.69, "1e5": 5863383.17,
+                       "1e6": 4648006.47},
+              "WAN": {"1e3": 23871.19, "1e4": 184700.86, "1e5": 430429.65, "1e6": 526221.62}},
+    "relu": {"LAN1": {"1e3": 621596.76, "1e4": 4395585.07, "1e5": 10041441.03,
+                      "1e6": 11088207.80},
+             "LAN2": {"1e3": 426070.40, "1e4": 2174901.21, "1e5": 3197114.92,
+                      "1e6": 2946653.78},
+             "WAN": {"1e3": 12060.67, "1e4": 114435.72, "1e5": 192806.77, "1e6": 279506.84}},
+}
+
+
+def network_projection(sweep):
+    """A model, not a measurement: the protocol at the paper's key width
+    (lx = 7, l = 64) with each party on a GB300 and the messages on the
+    paper's three networks.  gpu_ms is the measured time of the whole call
+    with all three parties on one GPU (so an upper bound on any one party's
+    work); net_ms is costmodel.network_seconds, the two rounds' latency and
+    bits over the busiest link.  Projected ops/s = n / (gpu + net); the
+    paper's measured figure on P100 servers is beside it."""
+    from paper_2309_04909_gb300 import costmodel as C
+    out = {}
+    for op in ("drelu", "relu"):
+        row = {}
+        for net, (bw, rtt) in C.PAPER_NETWORKS.items():
+            cells = {}
+            for e in range(3, 7):
+                key, n = f"1e{e}", 10 ** e
+                gpu_s = sweep[f"{op}_lx7"][key]["ms"] / 1e3
+                net_s = C.network_seconds(64, 7, n, op == "relu", bw, rtt)
+                cells[key] = {"gpu_ms": gpu_s * 1e3, "net_ms": net_s * 1e3,
+                              "projected_ops_per_s": n / (gpu_s + net_s),
+                              "paper_ops_per_s": PAPER_OPS[op][net][key]}
+            row[net] = cells
+        out[op] = row
+    out["model"] = ("one full-duplex link per server at the network's bandwidth each way; per "
+                    "round half the round-trip time plus the busiest server's bits in or out; "
+                    "w_j of (lx+1)^2 bits per element, openings, e, [c]_1 and the reply of l "
+                    "bits; GPU time measured on one GB300 for all three parties")
+    return out
 
 
 def size_sweep(ctx, dev):

@@ -148,3 +148,46 @@ def int_mul_peak_ops(sm_count: int = SM_COUNT, sm_mhz: float = SM_MAX_MHZ) -> fl
     """Integer-multiplier peak: 4 sub-partitions per SM, each with a 16-lane
     FMA-heavy pipe that executes IMAD-class instructions."""
     return sm_count * 4 * 16 * sm_mhz * 1e6
+
+
+# ---------------------------------------------------------------------------
+# The protocol's messages over the paper's networks (Sec. 6: three servers,
+# LAN1 = 5 Gbps with 0.2 ms round-trip time, LAN2 = 1 Gbps / 0.6 ms, WAN =
+# 100 Mbps / 40 ms).  A model, for comparing the GPU's time per call with the
+# time the messages of Alg. drelu / Alg. relu need on those links; nothing
+# here is measured.
+# ---------------------------------------------------------------------------
+PAPER_NETWORKS = {"LAN1": (5e9, 0.2e-3), "LAN2": (1e9, 0.6e-3), "WAN": (100e6, 40e-3)}
+
+
+def round_bits(ell: int, lx: int, n: int, relu: bool):
+    """Per round, the protocol bits each party sends and receives:
+    [(sent[P0, P1, P2], received[P0, P1, P2]), ...] for the two rounds.
+    Round 1: w_0 and w_1 ((lx + 1)^2 bits per element each, Alg. drelu step
+    8) to P2; for ReLU also the openings [x]_j - [a]_j between P0 and P1 and
+    the preprocessing message [c]_1 from P2 to P1, which depends on no input
+    and so travels while P2's link out is otherwise idle.  Round 2: P2's
+    reply, [DReLU']_1 to P1 (l bits), or for ReLU e = DReLU' - b to both."""
+    w = n * (lx + 1) ** 2
+    lane = n * ell
+    sent1, recv1 = [w, w, 0], [0, 0, 2 * w]
+    if relu:
+        sent1 = [w + lane, w + lane, lane]
+        recv1 = [lane, 2 * lane, 2 * w]
+        sent2, recv2 = [0, 0, 2 * lane], [lane, lane, 0]
+    else:
+        sent2, recv2 = [0, 0, lane], [0, lane, 0]
+    return [(sent1, recv1), (sent2, recv2)]
+
+
+def network_seconds(ell: int, lx: int, n: int, relu: bool, bits_per_s: float,
+                    rtt_s: float) -> float:
+    """Time of the two rounds on links of bits_per_s each way per server
+    (one full-duplex link per server, so a server's messages out share it,
+    and so do its messages in), each round paying half the round-trip time:
+    sum over rounds of rtt/2 + max over servers and directions of bits /
+    bits_per_s."""
+    t = 0.0
+    for sent, recv in round_bits(ell, lx, n, relu):
+        t += rtt_s / 2 + max(max(sent), max(recv)) / bits_per_s
+    return t
