@@ -1628,7 +1628,7 @@ def serving_bench(ctx, dev, capacity, seconds, load_seconds, bvp, budget=40 << 3
     Runs the offered 2,000 req/s and 50 % / 90 % of the measured batched
     capacity, each for `seconds` of arrivals; reports p50/p99 latency."""
     from paper_2309_04909_gb300 import Params, workloads as W
-    from paper_2309_04909_gb300.serve import Engine, ServingSetup
+    from paper_2309_04909_gb300.serve import Engine, ServingSetup, ideal_latencies
     prm = Params(64, 24, 0)
     setup = ServingSetup(ctx, prm, budget, seed=4, pool_images=64)
     mean_elems = 0.5 * 32.5 * (setup.per_image["vgg16"] + setup.per_image["lenet"])
@@ -1643,6 +1643,13 @@ def serving_bench(ctx, dev, capacity, seconds, load_seconds, bvp, budget=40 << 3
         reqs = setup.requests_from_trace(trace)
         st = Engine(setup.executor(schedule=sched), budget, max_iter_elems=1 << 24).run(reqs)
         s = st.summary()
+        # the yardstick: the same arrivals on an ideal first-come server of the
+        # measured capacity (no iteration quantum, no launch cost)
+        ideal = sorted(ideal_latencies([r.arrival_s for r in trace],
+                                       [r.images * setup.per_image[r.net] / capacity
+                                        for r in trace], "fcfs"))
+        s["ideal_fcfs_ms"] = {"p50": 1e3 * ideal[len(ideal) // 2],
+                              "p99": 1e3 * ideal[min(len(ideal) - 1, int(0.99 * len(ideal)))]}
         s["arrival_window_s"] = window
         s["rate_rps"] = rate
         s["offered_elems_per_s"] = rate * mean_elems

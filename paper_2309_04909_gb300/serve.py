@@ -328,6 +328,60 @@ class Engine:
 # Executors
 # ---------------------------------------------------------------------------
 
+def ideal_latencies(arrivals_s: Sequence[float], service_s: Sequence[float],
+                    policy: str = "fcfs") -> List[float]:
+    """Latencies (completion - arrival) of the requests on an ideal single
+    server: no launch cost, instant preemption, work `service_s` seconds each.
+    policy: "fcfs" (first come, first served), "ps" (processor sharing: every
+    unfinished request served at an equal share) or "srpt" (shortest
+    remaining work first).  The yardstick for the engine's tail: the same
+    arrivals and sizes, with none of its iteration quantum or launch costs."""
+    n = len(arrivals_s)
+    order = sorted(range(n), key=lambda i: arrivals_s[i])
+    arr = [float(arrivals_s[i]) for i in order]
+    size = [float(service_s[i]) for i in order]
+    done = [0.0] * n
+    if policy == "fcfs":
+        t = 0.0
+        for i in range(n):
+            t = max(t, arr[i]) + size[i]
+            done[i] = t
+    elif policy in ("ps", "srpt"):
+        t, i, active = 0.0, 0, {}
+        while i < n or active:
+            if not active:
+                t = max(t, arr[i])
+                active[i] = size[i]
+                i += 1
+                continue
+            k = len(active)
+            if policy == "ps":
+                dt_finish = min(active.values()) * k
+            else:
+                j = min(active, key=active.get)
+                dt_finish = active[j]
+            dt_arr = arr[i] - t if i < n else float("inf")
+            dt = min(dt_finish, dt_arr)
+            if policy == "ps":
+                for j in active:
+                    active[j] -= dt / k
+            else:
+                active[j] -= dt
+            t += dt
+            for j in [j for j, v in active.items() if v <= 1e-15]:
+                done[j] = t
+                del active[j]
+            if dt_arr <= dt_finish and i < n:
+                active[i] = size[i]
+                i += 1
+    else:
+        raise ValueError(f"unknown policy {policy!r}")
+    out = [0.0] * n
+    for pos, i in enumerate(order):
+        out[i] = done[pos] - arr[pos]
+    return out
+
+
 class FakeExecutor(Executor):
     """A simulated device for host-logic tests: an iteration of n elements
     takes n / rate seconds of simulated time, iterations run back to back."""

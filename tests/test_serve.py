@@ -2,6 +2,8 @@
 continuous-batching scheduler on a simulated device."""
 import random
 
+import pytest
+
 from paper_2309_04909_gb300.serve import Arena, Engine, FakeExecutor, ServeRequest, ServeStats
 
 
@@ -165,3 +167,22 @@ def test_latency_histogram():
     h = st.summary()["latency_histogram_ms"]
     assert h == {"<=1": 1, "<=2": 1, "<=4": 2, ">1024": 1}
     assert sum(h.values()) == 5
+
+
+def test_ideal_latencies_by_hand():
+    """The ideal-server yardstick on cases worked by hand."""
+    from paper_2309_04909_gb300.serve import ideal_latencies
+    arr, work = [0.0, 1.0, 1.5], [2.0, 1.0, 0.25]
+    # first come: finishes at 2, 3, 3.25
+    assert ideal_latencies(arr, work, "fcfs") == pytest.approx([2.0, 2.0, 1.75])
+    # shortest remaining first: 0 runs to 1 (1 left), 1 arrives (1 left) and
+    # ties go to the lower index, so 0 runs to 1.5 (0.5 left); 2 (0.25) runs
+    # to 1.75, then 0 to 2.25, then 1 to 3.25
+    assert ideal_latencies(arr, work, "srpt") == pytest.approx([2.25, 2.25, 0.25])
+    # processor sharing: two equal jobs arriving together both finish at 2 x work
+    assert ideal_latencies([0.0, 0.0], [1.0, 1.0], "ps") == pytest.approx([2.0, 2.0])
+    # a lone job is served at full rate, and order of the inputs does not matter
+    assert ideal_latencies([5.0], [0.5], "ps") == pytest.approx([0.5])
+    assert ideal_latencies([1.0, 0.0], [1.0, 2.0], "fcfs") == pytest.approx([2.0, 2.0])
+    with pytest.raises(ValueError):
+        ideal_latencies(arr, work, "lifo")
