@@ -27,6 +27,12 @@
 #ifndef BC_BATCH_MIN_CTAS
 #define BC_BATCH_MIN_CTAS 6
 #endif
+// The same for 32-bit lanes (l <= 32): at six CTAs that kernel spills 8 bytes
+// at lx = 14; five CTAs give it 48 registers and no spill, 0.15% faster on
+// the two-ring ResNet-18 set.
+#ifndef BC_BATCH_MIN_CTAS_L32
+#define BC_BATCH_MIN_CTAS_L32 5
+#endif
 
 namespace bc {
 namespace {
@@ -115,7 +121,10 @@ __device__ __forceinline__ void grid_tile(const ReluConsts& k, const BatchTensor
 }
 
 template <typename Lane, int LX, bool SHORT, int UNROLL, int EPT>
-__global__ void __launch_bounds__(kBlock, (LX >= 14 && EPT == 1 && UNROLL == 0) ? BC_BATCH_MIN_CTAS : 0)
+__global__ void __launch_bounds__(kBlock, (LX >= 14 && EPT == 1 && UNROLL == 0)
+                                              ? (sizeof(Lane) == 8 ? BC_BATCH_MIN_CTAS
+                                                                   : BC_BATCH_MIN_CTAS_L32)
+                                              : 0)
     relu_batch_grid_kernel(const ReluConsts k, const BatchTensor* __restrict__ tensors,
                            const BatchTile* __restrict__ tiles, uint32_t begin,
                            int* __restrict__ status) {
