@@ -24,6 +24,14 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 TILE_CANDIDATES = (128, 256, 512, 1024, 2048)
 EPT_CANDIDATES = (1, 2, 4)
 UNROLL_CANDIDATES = (0, 2, 3)   # 0: the whole key-bit loop
+# The launch shape the kernels are tuned and profiled for: grid schedule,
+# 256-element tiles, one element per thread, the key-bit loop unrolled whole.
+DEFAULT_LAUNCH = {"schedule": 1, "tile_elems": 256, "ctas_per_sm": 0, "elems_per_thread": 1,
+                  "slot_unroll": 0}
+# Another candidate replaces the default only when it is faster by more than
+# this fraction, so that timing noise between near-equal shapes does not flip
+# the choice from run to run.
+PREFER_DEFAULT_WITHIN = 0.01
 
 
 class ReluBatch:
@@ -92,7 +100,7 @@ def time_ms(fn, reps: int = 5, warmup: int = 2) -> float:
 def _mix_key(items) -> str:
     rings = sorted({(it[0].ring_bits, it[0].lx) for it in items})
     total = sum(it[1].numel() for it in items)
-    return (f"v3|{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}"
+    return (f"v4|{torch.cuda.get_device_name()}|{rings}|n~2^{max(total, 1).bit_length()}"
             f"|t{len(items)}")
 
 
@@ -102,8 +110,9 @@ def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
     "tile_elems", "ctas_per_sm", "elems_per_thread", "slot_unroll", "ms"}:
     the grid schedule at every (elements per thread, key-bit unroll), then
     the persistent schedule at every (tile, CTAs per SM) with the best
-    unroll.  Outputs of the tensors are written (the protocol is
-    deterministic, so reruns give identical results)."""
+    unroll.  DEFAULT_LAUNCH is kept unless the best candidate beats it by more
+    than PREFER_DEFAULT_WITHIN.  Outputs of the tensors are written (the
+    protocol is deterministic, so reruns give identical results)."""
     key = _mix_key(items)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
@@ -114,12 +123,14 @@ def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
         if key in cache:
             return cache[key]
     best = None
+    timed = {}
 
     def consider(cfg):
         nonlocal best
         b = ReluBatch(ctx, items, cfg["tile_elems"], cfg["ctas_per_sm"], cfg["schedule"],
                       cfg["elems_per_thread"], cfg["slot_unroll"])
         ms = time_ms(b.run, reps=reps, warmup=1)
+        timed[tuple(sorted(cfg.items()))] = ms
         if best is None or ms < best["ms"]:
             best = dict(cfg, ms=ms)
 
@@ -132,6 +143,9 @@ def autotune(ctx: Context, items: Sequence[Tuple], reps: int = 3,
         for cps in (0, 1, 2, 3):
             consider({"schedule": 0, "tile_elems": tile, "ctas_per_sm": cps,
                       "elems_per_thread": 1, "slot_unroll": u})
+    d_ms = timed.get(tuple(sorted(DEFAULT_LAUNCH.items())))
+    if d_ms is not None and d_ms <= best["ms"] * (1.0 + PREFER_DEFAULT_WITHIN):
+        best = dict(DEFAULT_LAUNCH, ms=d_ms)
     cache[key] = best
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
