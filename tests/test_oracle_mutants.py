@@ -2,7 +2,9 @@
 copy of the oracle (a dropped term, a wrong sign or index, a swapped
 operand, a wrong constant) makes the pin suite fail.  Each mutant is a text
 substitution in oracle/bicoptor_oracle.c, built into a temporary directory
-and run against tests/test_oracle_pins.py in a subprocess."""
+and run against tests/test_oracle_pins.py in a subprocess; the mutants'
+subprocesses run side by side."""
+import concurrent.futures as cf
 import os
 import subprocess
 import sys
@@ -64,17 +66,41 @@ MUTANTS = {
 }
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutant(name, workdir):
+    """Build the oracle with mutant `name` planted and run the pin suite on
+    it; returns (pytest exit code, its stdout)."""
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutant {name} no longer matches the oracle source"
-    mutant = tmp_path / "bicoptor_oracle.c"
-    mutant.write_text(src.replace(old, new))
-    env = dict(os.environ, BICOPTOR_ORACLE_SRC=str(mutant), PYTHONPATH=ROOT)
+    if src.count(old) != 1:
+        return None, f"mutant {name} no longer matches the oracle source"
+    mutant = os.path.join(workdir, "bicoptor_oracle.c")
+    with open(mutant, "w") as f:
+        f.write(src.replace(old, new))
+    # the pin suites of the mutants run side by side, two OpenMP threads each
+    env = dict(os.environ, BICOPTOR_ORACLE_SRC=mutant, PYTHONPATH=ROOT, OMP_NUM_THREADS="2")
     proc = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                            os.path.join(HERE, "test_oracle_pins.py")],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    assert proc.returncode != 0, f"no pin caught mutant {name}:\n{proc.stdout[-1500:]}"
-    assert "failed" in proc.stdout or "error" in proc.stdout.lower()
+    return proc.returncode, proc.stdout
+
+
+@pytest.fixture(scope="module")
+def mutant_runs(request, tmp_path_factory):
+    """The pin-suite runs of every mutant selected in this session, made
+    concurrently (each in its own directory and process)."""
+    names = sorted({it.callspec.params["name"] for it in request.session.items
+                    if getattr(it, "originalname", "") == "test_pins_catch_planted_mistake"})
+    dirs = {n: str(tmp_path_factory.mktemp(f"mutant_{n}")) for n in names}
+    workers = max(1, min(len(names), (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(_run_mutant, n, dirs[n]) for n in names}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, mutant_runs):
+    rc, out = mutant_runs[name]
+    assert rc is not None, out
+    assert rc != 0, f"no pin caught mutant {name}:\n{out[-1500:]}"
+    assert "failed" in out or "error" in out.lower()
