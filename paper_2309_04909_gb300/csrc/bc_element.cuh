@@ -138,30 +138,35 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
 
 // Steps 3-9 of one message slot whose window index is i: P0's and P1's
 // windows (Alg. newtrc2), pair sums, Alg. modswitch, the mask r_k and the
-// reshare z_k from the slot's seed01 block rz, and P2's zero test.  Returns 1
-// when w0 + w1 = 0 mod p; w0, w1 are the two messages.
+// reshare z_k from the slot's seed01 block rz, and P2's zero test.  f0c and
+// nf1c are the flipped share and 2^l minus the other flipped share, already
+// shifted right by the key offset c (once per element), so the window of
+// index i starts at bit i.  Returns 1 when w0 + w1 = 0 mod p; w0, w1 are the
+// two messages.
 template <int LX, bool SHORT, typename Lane>
-__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0, Lane nf1,
+__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0c, Lane nf1c,
                                                    uint32_t i, const U32x4& rz, uint32_t& w0,
                                                    uint32_t& w1) {
   constexpr bool kWide = (LX == 0) || (LX > 30);
   using M = SlotMath<LX, kWide>;
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  const uint32_t mx = LX ? (uint32_t)((1ull << (LX ? LX : 1)) - 1u) : k.mx;   // 2^lx - 1
   const uint32_t p = k.mp.p;
-  const uint32_t sh = k.c + i;
-  const uint32_t y0 = window32<SHORT>(f0, sh);
-  const uint32_t y1 = window32<SHORT>(nf1, sh);
-  const uint32_t next_mask = (i < lx) ? k.mx : 0u;   // u_(lx+1) := 0
-  // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1)
-  const uint32_t v0 = ((y0 & k.mx) + ((y0 >> 1) & next_mask) - 1u) & k.mx;
-  const uint32_t v1 = (0u - (y1 & k.mx) - ((y1 >> 1) & next_mask)) & k.mx;
+  const uint32_t y0 = window32<SHORT>(f0c, i);
+  const uint32_t y1 = window32<SHORT>(nf1c, i);
+  const uint32_t next_mask = (i < lx) ? mx : 0u;   // u_(lx+1) := 0
+  // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1);
+  // sums mod 2^lx depend only on the low lx bits of their terms, so u_i's own
+  // mask is left to the final one
+  const uint32_t v0 = (y0 + ((y0 >> 1) & next_mask) - 1u) & mx;
+  const uint32_t v1 = (0u - y1 - ((y1 >> 1) & next_mask)) & mx;
 #if BC_ALU_ADDS
   if (!kWide) {
     // the same steps 5-9 with every sum in three-input form (p < 2^31, so
     // every sum below stays under 2^32; a value in [0, 2p) reduces to the
     // minimum of itself and itself minus p, which wraps above it when < p)
     const uint32_t z1 = k.zero1, z2 = k.zero2, negp = k.neg_p;
-    const uint32_t m0 = v0 ? v0 : k.two_lx;
+    const uint32_t m0 = v0 ? v0 : (LX ? (1u << (LX ? LX : 1)) : k.two_lx);   // 2^lx < p
     const uint32_t m1 = v1 + k.p_minus_2lx + z1;
     const uint32_t rho = mulhi_64x32(rz.x, rz.y, k.mp.pm1) + 1u + z2;
     const uint32_t zk = mulhi_64x32(rz.z, rz.w, p);
@@ -237,8 +242,9 @@ __device__ __forceinline__ uint32_t slots_after_shuffle(const ReluConsts& k, con
   }
 
   // ---- steps 1-2: flip by (-1)^t --------------------------------------------
-  const Lane f0 = t ? ring_neg(s0, mask) : s0;
-  const Lane nf1 = t ? s1 : ring_neg(s1, mask);   // 2^l - [x]_1 of the flipped share
+  // (both shifted right by the key offset c for the windows of step 3)
+  const Lane f0 = (t ? ring_neg(s0, mask) : s0) >> k.c;
+  const Lane nf1 = (t ? s1 : ring_neg(s1, mask)) >> k.c;   // 2^l - [x]_1 of the flipped share
 
   // ---- steps 3-9 over message slots k ----------------------------------------
   uint32_t any_zero = 0;
@@ -289,8 +295,8 @@ __device__ __forceinline__ uint32_t slots_with_shuffle(const ReluConsts& k, cons
       const uint32_t widx = 4 * b + q;
       if (widx == 0) {
         t = ws[0] & 1u;                                   // steps 1-2
-        f0 = t ? ring_neg(s0, mask) : s0;
-        nf1 = t ? s1 : ring_neg(s1, mask);
+        f0 = (t ? ring_neg(s0, mask) : s0) >> k.c;        // shifted by c for step 3
+        nf1 = (t ? s1 : ring_neg(s1, mask)) >> k.c;
       } else if (widx < L) {
         const uint32_t j = L - widx;                      // step 6, then slot j
         const uint32_t partner = __umulhi(ws[q], j + 1);

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(kBlock)
 
   // steps 1-2, then steps 3-9 over this lane's message slots
   const Lane s0 = sh0[i], s1 = sh1[i];
-  const Lane f0 = t ? ring_neg(s0, mask) : s0;
-  const Lane nf1 = t ? s1 : ring_neg(s1, mask);
+  const Lane f0 = (t ? ring_neg(s0, mask) : s0) >> k.c;   // shifted by c for step 3
+  const Lane nf1 = (t ? s1 : ring_neg(s1, mask)) >> k.c;
   uint32_t any_zero = 0;
   const StreamPhilox mask_stream(ep, kPair01, kPurMask, rk);
   for (uint32_t slot = part; slot < L; slot += kSplit) {
