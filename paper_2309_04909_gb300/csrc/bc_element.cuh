@@ -302,7 +302,8 @@ __device__ __forceinline__ uint32_t slots_with_shuffle(const ReluConsts& k, cons
         const uint32_t partner = __umulhi(ws[q], j + 1);
         const uint32_t a = perm[j * kBlock];
         const uint32_t c = perm[partner * kBlock];
-        perm[j * kBlock] = c;
+        // the swap's other half, perm[j] = c, is not stored: position j is
+        // final and later steps (partners <= j - 1) never read it
         perm[partner * kBlock] = a;
         const uint64_t mb = (uint64_t)kPhiloxM1 * j;
         const U32x4 rz =
