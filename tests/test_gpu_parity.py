@@ -142,6 +142,47 @@ def test_protocol_parity_with_audit(ctx, op, ring, lx, c, mag, n):
             assert np.array_equal(to_np(aud[k]).astype(np.uint64), eaud[k])
 
 
+# The kernels compiled for fixed key widths (lx = 24 and 7 at l = 64, 14 and 9
+# at l = 32) at key offsets the configurations above do not reach: at l = 64
+# on both sides of c + lx = 32 (below it the window is one funnel shift of the
+# lane's two words), and l = 32 at c = 0.  The flipped shares are shifted by c
+# once per element, so every window of step 3 depends on it.
+OFFSETS = [(64, 24, 5, 28, 20_011), (64, 24, 9, 32, 20_011), (64, 7, 24, 30, 9_999),
+           (64, 7, 30, 36, 9_999), (32, 14, 0, 13, 9_999), (32, 9, 0, 8, 9_999)]
+
+
+@pytest.mark.parametrize("op", ["drelu", "relu"])
+@pytest.mark.parametrize("ring,lx,c,mag,n", OFFSETS)
+def test_fixed_width_kernels_at_key_offsets(ctx, op, ring, lx, c, mag, n):
+    """Single-tensor kernel with and without the audit, and the batched grid
+    kernel, against the oracle element by element (messages too)."""
+    x = W.magnitude_bounded_ints(n, mag, seed=ring * 5 + lx * 3 + c)
+    tid = 300 + lx + c
+    s0, s1 = _shares(ctx, ring, x, tid)
+    prm, P = Params(ring, lx, c), O.params(ring, lx, c)
+    es0, es1 = O.share(ring, masked(x, ring), SEED, tid)
+    ofn = O.drelu if op == "drelu" else O.relu
+    e0, e1, eaud = ofn(P, es0, es1, SEED, tid + 1, audit=True, threads=8)
+    fn = ctx.drelu if op == "drelu" else ctx.relu
+    o0, o1, aud = fn(prm, s0, s1, tensor_id=tid + 1, audit=True)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+    L = lx + 1
+    assert np.array_equal(to_np(aud["w0"]).reshape(n, L), eaud["w0"])
+    assert np.array_equal(to_np(aud["w1"]).reshape(n, L), eaud["w1"])
+    assert np.array_equal(to_np(aud["dprime"]), eaud["dprime"])
+    o0, o1 = fn(prm, s0, s1, tensor_id=tid + 1)
+    assert np.array_equal(to_np(o0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(o1).astype(np.uint64), e1)
+    b0, b1 = torch.empty_like(s0), torch.empty_like(s1)
+    ctx.relu_batch_plan([(prm, s0, s1, b0, b1, tid + 1, 1 if op == "drelu" else 0)],
+                        schedule=1)
+    ctx.relu_batch_run()
+    assert ctx.batch_status() == 0
+    assert np.array_equal(to_np(b0).astype(np.uint64), e0)
+    assert np.array_equal(to_np(b1).astype(np.uint64), e1)
+
+
 @pytest.mark.parametrize("op", ["drelu", "relu"])
 @pytest.mark.parametrize("ring,lx,c,mag,n", PROTO[:4])
 def test_protocol_parity_no_audit(ctx, op, ring, lx, c, mag, n):
