@@ -138,15 +138,15 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
 
 // Steps 3-9 of one message slot whose window index is i: P0's and P1's
 // windows (Alg. newtrc2), pair sums, Alg. modswitch, the mask r_k and the
-// reshare z_k from the slot's seed01 block rz, and P2's zero test.  f0c and
-// nf1c are the flipped share and 2^l minus the other flipped share, already
-// shifted right by the key offset c (once per element), so the window of
-// index i starts at bit i.  Returns 1 when w0 + w1 = 0 mod p; w0, w1 are the
-// two messages.
+// reshare z_k from the slot's seed01 block rz, and P2's reconstruction.  f0c
+// and nf1c are the flipped share and 2^l minus the other flipped share,
+// already shifted right by the key offset c (once per element), so the window
+// of index i starts at bit i.  Returns P2's w_k = w0 + w1 mod p, which its
+// zero test compares with 0; w0, w1 are the two messages.
 template <int LX, bool SHORT, typename Lane>
-__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0c, Lane nf1c,
-                                                   uint32_t i, const U32x4& rz, uint32_t& w0,
-                                                   uint32_t& w1) {
+__device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f0c, Lane nf1c,
+                                                     uint32_t i, const U32x4& rz, uint32_t& w0,
+                                                     uint32_t& w1) {
   constexpr bool kWide = (LX == 0) || (LX > 30);
   using M = SlotMath<LX, kWide>;
   const uint32_t lx = LX ? (uint32_t)LX : k.lx;
@@ -178,7 +178,7 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0c
     const uint32_t a1 = u1 - zk + z1;                  // P1 subtracts it
     w1 = min(a1, a1 + p + z2);
     const uint32_t s = w0 + w1 + z1;                   // step 9: below 2p
-    return ((s == 0u) | (s == p)) ? 1u : 0u;
+    return min(s, s + negp + z2);                      // s mod p: 0 iff s is 0 or p
   }
 #endif
   // step 5: Alg. modswitch
@@ -193,8 +193,16 @@ __device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0c
   // step 8: reshare (P0 adds z_k, P1 subtracts it) and send to P2
   w0 = M::add(w0, z, p);
   w1 = M::sub(w1, z, p);
-  // step 9: P2 reconstructs w_k and tests it
-  return (M::add(w0, w1, p) == 0u) ? 1u : 0u;
+  // step 9: P2 reconstructs w_k
+  return M::add(w0, w1, p);
+}
+
+// The same slot with P2's zero test: 1 when w_k = 0.
+template <int LX, bool SHORT, typename Lane>
+__device__ __forceinline__ uint32_t slot_zero_test(const ReluConsts& k, Lane f0c, Lane nf1c,
+                                                   uint32_t i, const U32x4& rz, uint32_t& w0,
+                                                   uint32_t& w1) {
+  return slot_reconstruct<LX, SHORT>(k, f0c, nf1c, i, rz, w0, w1) == 0u ? 1u : 0u;
 }
 
 // Steps 1-9 of one element, shuffle first: the seed01 stream gives t and
