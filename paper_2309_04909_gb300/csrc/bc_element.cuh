@@ -166,7 +166,9 @@ __device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f
     // every sum below stays under 2^32; a value in [0, 2p) reduces to the
     // minimum of itself and itself minus p, which wraps above it when < p)
     const uint32_t z1 = k.zero1, z2 = k.zero2, negp = k.neg_p;
-    const uint32_t m0 = v0 ? v0 : (LX ? (1u << (LX ? LX : 1)) : k.two_lx);   // 2^lx < p
+    // step 5: m0 = v0, or 2^lx (< p) when v0 = 0, as ((v0 - 1) mod 2^lx) + 1
+    // with v0 - 1 taken straight from the window sum (no compare and select)
+    const uint32_t m0 = ((y0 + ((y0 >> 1) & next_mask) - 2u) & mx) + 1u + z1;
     const uint32_t m1 = v1 + k.p_minus_2lx + z1;
     const uint32_t rho = mulhi_64x32(rz.x, rz.y, k.mp.pm1) + 1u + z2;
     const uint32_t zk = mulhi_64x32(rz.z, rz.w, p);
