@@ -154,12 +154,15 @@ __device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f
   const uint32_t p = k.mp.p;
   const uint32_t y0 = window32<SHORT>(f0c, i);
   const uint32_t y1 = window32<SHORT>(nf1c, i);
-  const uint32_t next_mask = (i < lx) ? mx : 0u;   // u_(lx+1) := 0
+  // u_(i+1): the window shifted by one, or 0 for i = lx (u_(lx+1) := 0) by a
+  // shift clamped at 32 (a funnel shift of (0, y) by 33 gives 0)
+  const uint32_t sh1 = (i < lx) ? 1u : 33u;
+  const uint32_t n0 = __funnelshift_rc(y0, 0u, sh1), n1 = __funnelshift_rc(y1, 0u, sh1);
   // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1);
-  // sums mod 2^lx depend only on the low lx bits of their terms, so u_i's own
-  // mask is left to the final one
-  const uint32_t v0 = (y0 + ((y0 >> 1) & next_mask) - 1u) & mx;
-  const uint32_t v1 = (0u - y1 - ((y1 >> 1) & next_mask)) & mx;
+  // sums mod 2^lx depend only on the low lx bits of their terms, so neither
+  // u_i nor u_(i+1) needs its own mask, only the sum
+  const uint32_t v0 = (y0 + n0 - 1u) & mx;
+  const uint32_t v1 = (0u - y1 - n1) & mx;
 #if BC_ALU_ADDS
   if (!kWide) {
     // the same steps 5-9 with every sum in three-input form (p < 2^31, so
@@ -168,7 +171,7 @@ __device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f
     const uint32_t z1 = k.zero1, z2 = k.zero2, negp = k.neg_p;
     // step 5: m0 = v0, or 2^lx (< p) when v0 = 0, as ((v0 - 1) mod 2^lx) + 1
     // with v0 - 1 taken straight from the window sum (no compare and select)
-    const uint32_t m0 = ((y0 + ((y0 >> 1) & next_mask) - 2u) & mx) + 1u + z1;
+    const uint32_t m0 = ((y0 + n0 - 2u) & mx) + 1u + z1;
     const uint32_t m1 = v1 + k.p_minus_2lx + z1;
     const uint32_t rho = mulhi_64x32(rz.x, rz.y, k.mp.pm1) + 1u + z2;
     const uint32_t zk = mulhi_64x32(rz.z, rz.w, p);
