@@ -34,16 +34,16 @@ __device__ __forceinline__ uint64_t shr64(uint64_t a, uint32_t s) {
 // Steps 3-9 of one message slot whose window offset is pos (= perm[slot]):
 // the recursive sums of both parties, the mask r_k and reshare z_k from the
 // slot's seed01 block, and P2's zero test.  mb = M1 * slot, the round-1
-// product of the slot's mask block.
+// product of the slot's mask block.  a and b arrive shifted right by the key
+// offset c, so the window of offset pos starts at bit pos.
 template <typename Lane>
 __device__ __forceinline__ uint32_t b1_slot(const ReluConsts& k, const StreamPhilox& mask_stream,
                                             const uint64_t* r2, uint32_t slot, uint64_t mb,
                                             uint32_t pos, uint64_t a, uint64_t b, uint64_t top0,
                                             uint64_t top1, uint64_t mask, Lane* w0, Lane* w1,
                                             uint64_t wi) {
-  const uint32_t sh = k.c + pos;
-  const uint64_t v0 = (floor_sum(a >> sh) - top0 - 1) & mask;       // S0 - 1 (P0)
-  const uint64_t v1 = (top1 - floor_sum(b >> sh)) & mask;           // S1 = -(sum for b)
+  const uint64_t v0 = (floor_sum(a >> pos) - top0 - 1) & mask;      // S0 - 1 (P0)
+  const uint64_t v1 = (top1 - floor_sum(b >> pos)) & mask;          // S1 = -(sum for b)
   const U32x4 rz = mask_stream.block_p0(mb, r2[slot], k.rk);
   const uint64_t r = (((uint64_t)rz.y << 32) | rz.x) | 1u;           // odd: a unit
   const uint64_t z = ((uint64_t)rz.w << 32) | rz.z;
@@ -77,15 +77,16 @@ __global__ void __launch_bounds__(kBlock)
   const ElemPhilox ep(k.elem_base + i, k.tensor_id);
   uint32_t* perm = perm_s + threadIdx.x;
   const uint64_t s0 = (uint64_t)sh0[i], s1 = (uint64_t)sh1[i];
-  const uint32_t top = k.c + lx + 1;
+  const uint32_t top = lx + 1;   // above the windows, counted from bit c
   const StreamPhilox perm_stream(ep, kPair01, kPurPerm, rk);
   const StreamPhilox mask_stream(ep, kPair01, kPurB1Mask, rk);
   uint32_t t = 0, any_zero = 0;
-  // steps 1-2: flip; P0 keeps its flipped share a, P1 b = 2^l - its flipped share
+  // steps 1-2: flip; P0 keeps its flipped share a, P1 b = 2^l - its flipped
+  // share, both shifted right by the key offset c once for the windows
   uint64_t a = 0, b = 0, top0 = 0, top1 = 0;
   auto flip = [&](uint32_t tt) {
-    a = tt ? (0 - s0) & mask : s0;
-    b = tt ? s1 : (0 - s1) & mask;
+    a = (tt ? (0 - s0) & mask : s0) >> k.c;
+    b = (tt ? s1 : (0 - s1) & mask) >> k.c;
     top0 = floor_sum(shr64(a, top));
     top1 = floor_sum(shr64(b, top));
   };
@@ -108,8 +109,7 @@ __global__ void __launch_bounds__(kBlock)
           const uint32_t partner = __umulhi(ws[q], j + 1);
           const uint32_t pa = perm[j * kBlock];
           const uint32_t pc = perm[partner * kBlock];
-          perm[j * kBlock] = pc;
-          perm[partner * kBlock] = pa;
+          perm[partner * kBlock] = pa;   // position j is final; later steps never read it
           any_zero |= b1_slot<Lane>(k, mask_stream, r2_s, j, (uint64_t)kPhiloxM1 * j, pc, a, b,
                                     top0, top1, mask, w0, w1, i * L);
         }

@@ -136,27 +136,22 @@ __device__ __forceinline__ uint32_t window32(uint32_t a, uint32_t sh) {
   return a >> sh;
 }
 
-// Steps 3-9 of one message slot whose window index is i: P0's and P1's
-// windows (Alg. newtrc2), pair sums, Alg. modswitch, the mask r_k and the
-// reshare z_k from the slot's seed01 block rz, and P2's reconstruction.  f0c
-// and nf1c are the flipped share and 2^l minus the other flipped share,
-// already shifted right by the key offset c (once per element), so the window
-// of index i starts at bit i.  Returns P2's w_k = w0 + w1 mod p, which its
-// zero test compares with 0; w0, w1 are the two messages.
-template <int LX, bool SHORT, typename Lane>
-__device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f0c, Lane nf1c,
-                                                     uint32_t i, const U32x4& rz, uint32_t& w0,
-                                                     uint32_t& w1) {
+// Steps 3-9 of one message slot from P0's and P1's windows y0, y1 (32 bits of
+// each flipped share from bit c + i, i the slot's window index): pair sums
+// (Alg. newtrc2), Alg. modswitch, the mask r_k and the reshare z_k from the
+// slot's seed01 block rz, and P2's reconstruction.  sh1 gives u_(i+1): 1 for
+// i < lx, 33 for i = lx (a funnel shift of (0, y) clamped at 32 then gives 0,
+// as u_(lx+1) := 0).  Returns P2's w_k = w0 + w1 mod p, which its zero test
+// compares with 0; w0, w1 are the two messages.
+template <int LX>
+__device__ __forceinline__ uint32_t slot_from_windows(const ReluConsts& k, uint32_t y0,
+                                                      uint32_t y1, uint32_t sh1,
+                                                      const U32x4& rz, uint32_t& w0,
+                                                      uint32_t& w1) {
   constexpr bool kWide = (LX == 0) || (LX > 30);
   using M = SlotMath<LX, kWide>;
-  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
   const uint32_t mx = LX ? (uint32_t)((1ull << (LX ? LX : 1)) - 1u) : k.mx;   // 2^lx - 1
   const uint32_t p = k.mp.p;
-  const uint32_t y0 = window32<SHORT>(f0c, i);
-  const uint32_t y1 = window32<SHORT>(nf1c, i);
-  // u_(i+1): the window shifted by one, or 0 for i = lx (u_(lx+1) := 0) by a
-  // shift clamped at 32 (a funnel shift of (0, y) by 33 gives 0)
-  const uint32_t sh1 = (i < lx) ? 1u : 33u;
   const uint32_t n0 = __funnelshift_rc(y0, 0u, sh1), n1 = __funnelshift_rc(y1, 0u, sh1);
   // steps 3-4: P0 v = u_i + u_(i+1) - 1, P1 v = u_i + u_(i+1) with u = -cut(-x1);
   // sums mod 2^lx depend only on the low lx bits of their terms, so neither
@@ -200,6 +195,18 @@ __device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f
   w1 = M::sub(w1, z, p);
   // step 9: P2 reconstructs w_k
   return M::add(w0, w1, p);
+}
+
+// The same slot from the flipped share and 2^l minus the other flipped share,
+// f0c and nf1c, already shifted right by the key offset c (once per element),
+// so the window of index i starts at bit i.
+template <int LX, bool SHORT, typename Lane>
+__device__ __forceinline__ uint32_t slot_reconstruct(const ReluConsts& k, Lane f0c, Lane nf1c,
+                                                     uint32_t i, const U32x4& rz, uint32_t& w0,
+                                                     uint32_t& w1) {
+  const uint32_t lx = LX ? (uint32_t)LX : k.lx;
+  return slot_from_windows<LX>(k, window32<SHORT>(f0c, i), window32<SHORT>(nf1c, i),
+                               (i < lx) ? 1u : 33u, rz, w0, w1);
 }
 
 // The same slot with P2's zero test: 1 when w_k = 0.

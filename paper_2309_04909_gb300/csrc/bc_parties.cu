@@ -218,21 +218,24 @@ __global__ void __launch_bounds__(kPB)
   const Lane s = valid ? lane_at<Lane>(a.sh[party], i) : (Lane)0;
   // steps 1-2 and the P1 pre-negation: P0 keeps [x]_0 (flipped), P1 keeps
   // 2^l - [x]_1 of its flipped share
-  const Lane f = party == 0 ? (t ? ring_neg(s, mask) : s) : (t ? s : ring_neg(s, mask));
+  // (shifted right by the key offset c once, so window i starts at bit i)
+  const Lane f =
+      (party == 0 ? (t ? ring_neg(s, mask) : s) : (t ? s : ring_neg(s, mask))) >> k.c;
   const StreamPhilox mask_stream(ep, kPair01, kPurMask, k.rk);
   uint64_t mb = 0;
   for (uint32_t slot = 0; slot < L; ++slot, mb += kPhiloxM1) {
     const uint32_t ii = perm[slot * kPB];
-    const uint32_t sh = k.c + ii;
-    const uint32_t y = (uint32_t)((uint64_t)f >> sh);
-    const uint32_t next_mask = (ii < lx) ? k.mx : 0u;
+    const uint32_t y = (uint32_t)((uint64_t)f >> ii);
+    // u_(i+1): y shifted by one, or 0 for i = lx (u_(lx+1) := 0) by a shift
+    // clamped at 32; the sums mod 2^lx need no mask on their terms
+    const uint32_t n = __funnelshift_rc(y, 0u, (ii < lx) ? 1u : 33u);
     uint32_t m;
     if (party == 0) {
-      const uint32_t v = ((y & k.mx) + ((y >> 1) & next_mask) - 1u) & k.mx;   // steps 3-4
-      m = v ? v : k.two_lx;                                                  // step 5
+      // steps 3-5: v = u_i + u_(i+1) - 1, and 2^lx in place of v = 0, as
+      // ((v - 1) mod 2^lx) + 1
+      m = ((y + n - 2u) & k.mx) + 1u;
     } else {
-      const uint32_t v = (0u - (y & k.mx) - ((y >> 1) & next_mask)) & k.mx;
-      m = v + k.p_minus_2lx;
+      m = ((0u - y - n) & k.mx) + k.p_minus_2lx;
     }
     const U32x4 rz = mask_stream.block_p0(mb, r2_s[slot], k.rk);              // step 7
     const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
