@@ -284,19 +284,21 @@ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p) 
   return a >= b ? a - b : a + (p - b);
 }
 
-// floor(w * q / 2^64) for a 64-bit w given as (hi, lo) and a 32-bit q:
-// floor((hi q + floor(lo q / 2^32)) / 2^32) = hi32(hi q) + the carry out of
-// lo32(hi q) + hi32(lo q).  The sum runs as a multiply-add carry chain
-// (mad.lo.cc, then madc.hi), not as a 64-bit multiply-add whose 32-bit addend
-// would first be moved into a register pair.
+// floor(w * q / 2^64) + ADD for a 64-bit w given as (hi, lo), a 32-bit q and
+// a constant ADD (0 or 1; the sum must fit 32 bits): floor((hi q +
+// floor(lo q / 2^32)) / 2^32) = hi32(hi q) + the carry out of lo32(hi q) +
+// hi32(lo q).  The sum runs as a multiply-add carry chain (mad.lo.cc, then
+// madc.hi, whose addend is ADD), not as a 64-bit multiply-add whose 32-bit
+// addend would first be moved into a register pair.
+template <uint32_t ADD = 0>
 __device__ __forceinline__ uint32_t mulhi_64x32(uint32_t lo, uint32_t hi, uint32_t q) {
   const uint32_t a_hi = __umulhi(lo, q);
   uint32_t r;
   asm("{\n\t.reg .u32 t;\n\t"
       "mad.lo.cc.u32 t, %1, %2, %3;\n\t"
-      "madc.hi.u32 %0, %1, %2, 0;\n\t}"
+      "madc.hi.u32 %0, %1, %2, %4;\n\t}"
       : "=r"(r)
-      : "r"(hi), "r"(q), "r"(a_hi));
+      : "r"(hi), "r"(q), "r"(a_hi), "n"(ADD));
   return r;
 }
 

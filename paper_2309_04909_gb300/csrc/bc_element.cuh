@@ -168,7 +168,7 @@ __device__ __forceinline__ uint32_t slot_from_windows(const ReluConsts& k, uint3
     // with v0 - 1 taken straight from the window sum (no compare and select)
     const uint32_t m0 = ((y0 + n0 - 2u) & mx) + 1u + z1;
     const uint32_t m1 = v1 + k.p_minus_2lx + z1;
-    const uint32_t rho = mulhi_64x32(rz.x, rz.y, k.mp.pm1) + 1u + z2;
+    const uint32_t rho = mulhi_64x32<1>(rz.x, rz.y, k.mp.pm1);   // 1 + floor(w (p - 1) / 2^64)
     const uint32_t zk = mulhi_64x32(rz.z, rz.w, p);
     const uint32_t q0 = mont_mul_raw(m0, rho, k.mp), q1 = mont_mul_raw(m1, rho, k.mp);
     const uint32_t u0 = min(q0, q0 + negp + z1);
@@ -186,7 +186,7 @@ __device__ __forceinline__ uint32_t slot_from_windows(const ReluConsts& k, uint3
   const uint32_t m1 = v1 + k.p_minus_2lx;
   // step 7: rho_k, z_k from the slot's seed01 block rz; the mask r_k =
   // rho_k 2^-32 mod p, so one Montgomery product m rho 2^-32 is m r_k
-  const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+  const uint32_t rho = mulhi_64x32<1>(rz.x, rz.y, k.mp.pm1);
   const uint32_t z = mulhi_64x32(rz.z, rz.w, p);
   w0 = mont_mul<kWide>(m0, rho, k.mp);
   w1 = mont_mul<kWide>(m1, rho, k.mp);

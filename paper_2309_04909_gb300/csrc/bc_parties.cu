@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kPB)
       m = ((0u - y - n) & k.mx) + k.p_minus_2lx;
     }
     const U32x4 rz = mask_stream.block_p0(mb, r2_s[slot], k.rk);              // step 7
-    const uint32_t rho = 1u + mulhi_64x32(rz.x, rz.y, k.mp.pm1);
+    const uint32_t rho = mulhi_64x32<1>(rz.x, rz.y, k.mp.pm1);
     const uint32_t z = mulhi_64x32(rz.z, rz.w, k.mp.p);
     uint32_t w = mont_mul(m, rho, k.mp);
     w = party == 0 ? add_mod(w, z, k.mp.p) : sub_mod(w, z, k.mp.p);          // step 8
