@@ -39,8 +39,8 @@ WORKLOAD = ("ResNet-18 224x224 ReLU set x{images} images, once in Z_2^64 (f=16, 
 BASE_SEED = 0xB1C0_2309_0490_9000
 # DRAM bytes per element of the batched kernel over both rings: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the two launches of one step
-# of a 4-image set (358.4 MB), divided by its 18,464,768 elements
-TRAFFIC_PER_ELEM_BATCH = 19.41
+# of a 4-image set (354.5 MB), divided by its 18,464,768 elements
+TRAFFIC_PER_ELEM_BATCH = 19.20
 # the fused step of a linear layer (reported beside the headline)
 FUSED_WORKLOAD = ("Z_2^64 f=16 Beaver product of 2^22 Gaussian(sigma=4) share pairs -> "
                   "trunc k=16 (SecureML prob + det) -> ReLU lx=24 c=0 of the prob-truncated "
