@@ -15,7 +15,8 @@
 //   P0, P1  step 11     unflip (DReLU) / Beaver finish (ReLU)
 // The lx+1 windows are never stored: message slot k recomputes the window of
 // the index i = perm[k] from the two shares, so the l-fold expansion of the
-// paper's step 3 costs two funnel shifts per slot and no memory traffic.
+// paper's step 3 costs two funnel shifts per slot and party (the window u_i
+// and the next one, u_(i+1)) and no memory traffic.
 // Draws shared by P0 and P1 (everything from seed01) are generated once per
 // element and used by both simulated parties.
 #pragma once
