@@ -55,6 +55,20 @@ MUTANTS = {
                                "uint64_t ty0 = smltrc_p0(y0[i], ell, kx), ty1 = smltrc_p1(y1[i], ell, kx);"),
     "aby3_signed_division": ("if (ell < 128 && (v >> (ell - 1)) & 1) v -= ((__int128)1 << ell);",
                              "if (0) v -= ((__int128)1 << ell);"),
+    # the per-element draws of Alg. drelu / Alg. relu from the Philox streams
+    "z_draw_modulus_p_minus_1": ("z[k] = (uint32_t)(((u128)wz * (u128)P->p) >> 64);",
+                                 "z[k] = (uint32_t)(((u128)wz * (u128)(P->p - 1u)) >> 64);"),
+    "mask_without_two_inv32": ("r[k] = (uint32_t)(((uint64_t)rho * inv32) % P->p);",
+                               "r[k] = rho % P->p;"),
+    "mask_words_swapped": ("uint64_t wr = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k) |",
+                           "uint64_t wr = (uint64_t)orc_stream_word(seed, PAIR_01, PUR_MASK, tid, elem, 4 * k + 2) |"),
+    "reply_from_seed12": ("msg1);\n        uint64_t d0 = stream_ring(seed, PAIR_02, PUR_REPLY, tid, elem, 0, ell);",
+                          "msg1);\n        uint64_t d0 = stream_ring(seed, PAIR_12, PUR_REPLY, tid, elem, 0, ell);"),
+    "triple_b0_is_c0": ("T.b0 = stream_ring(seed, PAIR_02, purpose, tid, elem, 1, ell);",
+                        "T.b0 = stream_ring(seed, PAIR_02, purpose, tid, elem, 2, ell);"),
+    "ring_draw_high_word_first": ("return rmod(lo | (hi << 32), ell);",
+                                  "return rmod(hi | (lo << 32), ell);"),
+    "shuffle_words_reversed": ("uint32_t W = fy[lx - j + 1];", "uint32_t W = fy[j];"),
     # the Bicoptor 1.0-style protocol
     "b1_sums_not_recursive": ("acc0 = rmod(acc0 + u0[i], ell);", "acc0 = rmod(u0[i], ell);"),
     "b1_p0_constant_dropped": ("v0[i] = rmod(acc0 - 1, ell);", "v0[i] = acc0;"),

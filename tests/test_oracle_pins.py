@@ -407,6 +407,101 @@ def test_drelu_messages_from_definition(lx, c, p):
         assert dprime == int(any((a + b) % p == 0 for a, b in zip(want0, want1)))
 
 
+@pytest.mark.parametrize("ell,lx,c,p", [(64, 24, 0, None), (32, 14, 4, None), (64, 31, 2, 4294967291),
+                                        (16, 5, 2, None)])
+def test_drelu_relu_draws_from_stream_words(ell, lx, c, p):
+    """Every draw of Alg. drelu / Alg. relu rebuilt with Python integers from
+    the raw Philox stream words (the layout pinned in test_stream_layout):
+    t and the Fisher-Yates words from seed01, rho_k = 1 + floor(W (p-1) /
+    2^64) with r_k = rho_k 2^-32 mod p and z_k = floor(W' p / 2^64) from the
+    slot's mask block (W, W' its two 64-bit halves, low word first), P0's
+    share of DReLU' from seed02, and the ReLU triple from seed02 / seed12
+    (ring elements of one word for l <= 32, two words low first above).  The
+    messages, the reply and the openings of the oracle's audit must follow
+    from them."""
+    P = O.params(ell, lx, c, p=p)
+    p = P.p
+    M, L = 1 << ell, lx + 1
+    seed, tid = 0x0DDB_A11_5EED, 17
+    from paper_2309_04909_gb300 import workloads as W
+    xs = W.magnitude_bounded_ints(24, min(lx + c, ell - 2), seed=lx + c)
+    x = xs.astype(np.uint64) & np.uint64(_mask(ell))
+    s0, s1 = O.share(ell, x, seed=9, tid=3)
+    d0_, d1_, dau = O.drelu(P, s0, s1, seed=seed, tid=tid, audit=True)
+    r0_, r1_, rau = O.relu(P, s0, s1, seed=seed, tid=tid, audit=True)
+    inv32 = pow(2**32, -1, p)
+    word = lambda pair, pur, e, j: O.stream_word(seed, pair, pur, tid, e, j)
+
+    def ring(pair, pur, e, j):
+        if ell <= 32:
+            return word(pair, pur, e, j) % M
+        return (word(pair, pur, e, 2 * j) | (word(pair, pur, e, 2 * j + 1) << 32)) % M
+
+    for e in range(xs.size):
+        t = word(O.PAIR_01, O.PUR_PERM, e, 0) & 1
+        fy = [word(O.PAIR_01, O.PUR_PERM, e, j) for j in range(1, L)]
+        r, z = [], []
+        for k in range(L):
+            wr = word(O.PAIR_01, O.PUR_MASK, e, 4 * k) | (word(O.PAIR_01, O.PUR_MASK, e, 4 * k + 1) << 32)
+            wz = word(O.PAIR_01, O.PUR_MASK, e, 4 * k + 2) | (word(O.PAIR_01, O.PUR_MASK, e, 4 * k + 3) << 32)
+            rho = 1 + ((wr * (p - 1)) >> 64)
+            r.append(rho * inv32 % p)
+            z.append((wz * p) >> 64)
+        assert all(1 <= v < p for v in r) and all(0 <= v < p for v in z)
+        dprime, m0, m1 = O.drelu_core(P, int(s0[e]), int(s1[e]), t, fy, r, z)
+        assert int(dau["t"][e]) == t and int(dau["dprime"][e]) == dprime
+        assert list(dau["w0"][e]) == list(m0) and list(dau["w1"][e]) == list(m1)
+        assert list(rau["w0"][e]) == list(m0) and list(rau["w1"][e]) == list(m1)
+        # step 10: P0's share d0 from seed02, the reply d1 = DReLU' - d0
+        d0 = ring(O.PAIR_02, O.PUR_REPLY, e, 0)
+        assert int(dau["reply"][e]) == (dprime - d0) % M
+        sg = 1 - 2 * t
+        assert int(d0_[e]) == (t + sg * d0) % M and int(d1_[e]) == (sg * (dprime - d0)) % M
+        # Alg. relu: a0, b0, c0 from seed02, a1, b1 from seed12
+        a0, b0, c0 = (ring(O.PAIR_02, O.PUR_RELU_TRIPLE, e, j) for j in range(3))
+        a1, b1 = (ring(O.PAIR_12, O.PUR_RELU_TRIPLE, e, j) for j in range(2))
+        assert int(rau["open0"][e]) == (int(s0[e]) - a0) % M
+        assert int(rau["open1"][e]) == (int(s1[e]) - a1) % M
+        assert int(rau["pre_c1"][e]) == ((a0 + a1) * (b0 + b1) - c0) % M
+        assert int(rau["reply"][e]) == (dprime - b0 - b1) % M
+
+
+def test_drelu_shuffle_from_definition():
+    """Step 6 with explicit Fisher-Yates words: starting from the identity,
+    step j = lx, ..., 1 takes the next word W (words consumed in order) and
+    swaps positions j and floor(W (j + 1) / 2^32); message slot k then
+    carries the masked window of index perm[k].  Recomputed with Python
+    integers and checked against the oracle's messages."""
+    ell, lx, c = 64, 24, 0
+    P = O.params(ell, lx, c)
+    p, M, L = P.p, 1 << ell, lx + 1
+    rng = np.random.default_rng(11)
+    for trial in range(30):
+        x = int(rng.integers(-2**22, 2**22))
+        R = int(rng.integers(0, 2**63)) * 2 + trial % 2
+        s0, s1 = (x + R) % M, (-R) % M
+        t = trial % 2
+        fy = [int(v) for v in rng.integers(0, 2**32, size=lx, dtype=np.uint64)]
+        r = [int(v) for v in rng.integers(1, p, size=L)]
+        z = [int(v) for v in rng.integers(0, p, size=L)]
+        dprime, m0, m1 = O.drelu_core(P, s0, s1, t, fy, r, z)
+        perm = list(range(L))
+        for step, j in enumerate(range(lx, 0, -1)):
+            q = (fy[step] * (j + 1)) >> 32
+            perm[j], perm[q] = perm[q], perm[j]
+        f0, f1 = ((-s0) % M, (-s1) % M) if t else (s0, s1)
+        u0 = [(f0 >> (c + i)) % 2**lx for i in range(L)]
+        u1 = [(-(((-f1) % M) >> (c + i))) % 2**lx for i in range(L)]
+        v0 = [(u0[i] + (u0[i + 1] if i < lx else 0) - 1) % 2**lx for i in range(L)]
+        v1 = [(u1[i] + (u1[i + 1] if i < lx else 0)) % 2**lx for i in range(L)]
+        n0 = [a if a else 2**lx for a in v0]
+        n1 = [(p + a - 2**lx) % p for a in v1]
+        want0 = [(n0[perm[k]] * r[k] + z[k]) % p for k in range(L)]
+        want1 = [(n1[perm[k]] * r[k] - z[k]) % p for k in range(L)]
+        assert list(m0) == want0 and list(m1) == want1
+        assert dprime == int(any((a + b) % p == 0 for a, b in zip(want0, want1)))
+
+
 def test_beaver_mul_exact():
     from paper_2309_04909_gb300 import workloads as W
     for ell in (64, 32, 8):
