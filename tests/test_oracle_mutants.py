@@ -69,6 +69,10 @@ MUTANTS = {
     "ring_draw_high_word_first": ("return rmod(lo | (hi << 32), ell);",
                                   "return rmod(hi | (lo << 32), ell);"),
     "shuffle_words_reversed": ("uint32_t W = fy[lx - j + 1];", "uint32_t W = fy[j];"),
+    "mul_triple_relu_purpose": ("triple_t T = draw_triple(seed, PUR_MUL_TRIPLE, tid, elem_index(idx, i), ell);",
+                                "triple_t T = draw_triple(seed, PUR_RELU_TRIPLE, tid, elem_index(idx, i), ell);"),
+    "dealer_from_seed01": ("uint64_t R = stream_ring(seed, PAIR_DEALER, PUR_SHARE, tid, elem_index(idx, i), 0, ell);",
+                           "uint64_t R = stream_ring(seed, PAIR_01, PUR_SHARE, tid, elem_index(idx, i), 0, ell);"),
     # the Bicoptor 1.0-style protocol
     "b1_sums_not_recursive": ("acc0 = rmod(acc0 + u0[i], ell);", "acc0 = rmod(u0[i], ell);"),
     "b1_p0_constant_dropped": ("v0[i] = rmod(acc0 - 1, ell);", "v0[i] = acc0;"),

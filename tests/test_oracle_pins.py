@@ -531,6 +531,41 @@ def test_share_reconstruct_and_uniformity():
     assert chi2 < 400  # 255 dof; p ~ 1e-8
 
 
+@pytest.mark.parametrize("ell", [64, 32, 13])
+def test_share_and_beaver_shares_from_stream_words(ell):
+    """The dealer's R and the Beaver product's triple rebuilt with Python
+    integers from the raw stream words (ring elements of one word for
+    l <= 32, two words low first above): [x]_0 = x + R, [x]_1 = -R, and the
+    product's output shares [xy]_0 = de + d b0 + e a0 + c0 (de added by P0),
+    [xy]_1 = d b1 + e a1 + c1 with c1 = (a0 + a1)(b0 + b1) - c0, d and e the
+    openings of x - a and y - b."""
+    M = 1 << ell
+    seed = 0xBEA5_E4ED
+    word = lambda pair, pur, tid, e, j: O.stream_word(seed, pair, pur, tid, e, j)
+
+    def ring(pair, pur, tid, e, j):
+        if ell <= 32:
+            return word(pair, pur, tid, e, j) % M
+        return (word(pair, pur, tid, e, 2 * j) | (word(pair, pur, tid, e, 2 * j + 1) << 32)) % M
+
+    rng = np.random.default_rng(ell)
+    x = rng.integers(0, 2**62, size=40, dtype=np.uint64) & np.uint64(_mask(ell))
+    y = rng.integers(0, 2**62, size=40, dtype=np.uint64) & np.uint64(_mask(ell))
+    x0, x1 = O.share(ell, x, seed=seed, tid=5)
+    y0, y1 = O.share(ell, y, seed=seed, tid=6)
+    o0, o1 = O.mul_beaver(ell, x0, x1, y0, y1, seed=seed, tid=9)
+    for e in range(x.size):
+        R = ring(O.PAIR_DEALER, O.PUR_SHARE, 5, e, 0)
+        assert int(x0[e]) == (int(x[e]) + R) % M and int(x1[e]) == (-R) % M
+        a0, b0, c0 = (ring(O.PAIR_02, O.PUR_MUL_TRIPLE, 9, e, j) for j in range(3))
+        a1, b1 = (ring(O.PAIR_12, O.PUR_MUL_TRIPLE, 9, e, j) for j in range(2))
+        c1 = ((a0 + a1) * (b0 + b1) - c0) % M
+        d = (int(x0[e]) - a0 + int(x1[e]) - a1) % M
+        ee = (int(y0[e]) - b0 + int(y1[e]) - b1) % M
+        assert int(o0[e]) == (d * ee + d * b0 + ee * a0 + c0) % M
+        assert int(o1[e]) == (d * b1 + ee * a1 + c1) % M
+
+
 def test_encode_round_half_even():
     f = 4
     x = np.array([0.0, 1.0, -1.0, 0.5 / 16, 1.5 / 16, 2.5 / 16, -0.5 / 16, -1.5 / 16, 3.03125])
