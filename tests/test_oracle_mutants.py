@@ -71,6 +71,10 @@ MUTANTS = {
     "shuffle_words_reversed": ("uint32_t W = fy[lx - j + 1];", "uint32_t W = fy[j];"),
     "mul_triple_relu_purpose": ("triple_t T = draw_triple(seed, PUR_MUL_TRIPLE, tid, elem_index(idx, i), ell);",
                                 "triple_t T = draw_triple(seed, PUR_RELU_TRIPLE, tid, elem_index(idx, i), ell);"),
+    "aby3_rp0_is_r0": ("uint64_t rp0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 1, ell);",
+                       "uint64_t rp0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 0, ell);"),
+    "aby3_r1_from_seed02": ("uint64_t r1 = stream_ring(seed, PAIR_12, PUR_ABY3, tid, elem, 0, ell);",
+                            "uint64_t r1 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 2, ell);"),
     "dealer_from_seed01": ("uint64_t R = stream_ring(seed, PAIR_DEALER, PUR_SHARE, tid, elem_index(idx, i), 0, ell);",
                            "uint64_t R = stream_ring(seed, PAIR_01, PUR_SHARE, tid, elem_index(idx, i), 0, ell);"),
     # the Bicoptor 1.0-style protocol

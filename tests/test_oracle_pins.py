@@ -566,6 +566,36 @@ def test_share_and_beaver_shares_from_stream_words(ell):
         assert int(o1[e]) == (d * b1 + ee * a1 + c1) % M
 
 
+@pytest.mark.parametrize("ell,k,fixed_r", [(64, 16, 0), (64, 26, 1 << 26), (32, 12, 0)])
+def test_aby3_from_stream_words(ell, k, fixed_r):
+    """Alg. aby3trc with its preprocessing rebuilt from the raw stream words
+    ([r]_0 and [r']_0 from seed02, [r]_1 from seed12, or fixed_r - [r]_0) and
+    every step recomputed with Python integers: r' = r / 2^k (signed floor),
+    [r']_1 = r' - [r']_0 from P2, the opened alpha = x + r, P0 keeps
+    alpha / 2^k - [r']_0 and P1 -[r']_1."""
+    M = 1 << ell
+    seed, tid = 0xAB_3AB3, 4
+
+    def ring(pair, e, j):
+        w = lambda jj: O.stream_word(seed, pair, O.PUR_ABY3, tid, e, jj)
+        return w(j) % M if ell <= 32 else (w(2 * j) | (w(2 * j + 1) << 32)) % M
+
+    def sdiv(a):   # floor division of the signed value by 2^k, mod 2^l
+        v = a - M if a >> (ell - 1) else a
+        return (v >> k) % M
+
+    rng = np.random.default_rng(k)
+    x = rng.integers(0, 2**62, size=40, dtype=np.uint64) & np.uint64(_mask(ell))
+    s0, s1 = O.share(ell, x, seed=seed, tid=2)
+    o0, o1 = O.trunc_aby3(ell, k, s0, s1, seed, tid, fixed_r=fixed_r)
+    for e in range(x.size):
+        r0, rp0 = ring(O.PAIR_02, e, 0), ring(O.PAIR_02, e, 1)
+        r1 = (fixed_r - r0) % M if fixed_r else ring(O.PAIR_12, e, 0)
+        rp1 = (sdiv((r0 + r1) % M) - rp0) % M
+        alpha = (int(s0[e]) + r0 + int(s1[e]) + r1) % M
+        assert int(o0[e]) == (sdiv(alpha) - rp0) % M and int(o1[e]) == (-rp1) % M
+
+
 def test_encode_round_half_even():
     f = 4
     x = np.array([0.0, 1.0, -1.0, 0.5 / 16, 1.5 / 16, 2.5 / 16, -0.5 / 16, -1.5 / 16, 3.03125])
