@@ -29,6 +29,7 @@ _lib = None
 PAIR_01, PAIR_02, PAIR_12, PAIR_DEALER, PAIR_012, PAIR_2 = 0x01, 0x02, 0x12, 0xDE, 0x03, 0x20
 PUR_SHARE, PUR_PERM, PUR_MASK, PUR_REPLY, PUR_RELU_TRIPLE, PUR_MUL_TRIPLE, PUR_ABY3 = (
     1, 2, 3, 4, 5, 6, 7)
+PUR_RSS_T, PUR_RSS_S, PUR_RSS_Z, PUR_RSS_ZR = 8, 9, 10, 11
 PUR_B1_MASK = 12
 
 

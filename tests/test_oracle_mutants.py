@@ -71,6 +71,12 @@ MUTANTS = {
     "shuffle_words_reversed": ("uint32_t W = fy[lx - j + 1];", "uint32_t W = fy[j];"),
     "mul_triple_relu_purpose": ("triple_t T = draw_triple(seed, PUR_MUL_TRIPLE, tid, elem_index(idx, i), ell);",
                                 "triple_t T = draw_triple(seed, PUR_RELU_TRIPLE, tid, elem_index(idx, i), ell);"),
+    "rss_alpha_from_seed01": ("for (int j = 0; j < 3; j++) al[j] = stream_ring(seed, PAIR_012, PUR_RSS_T, tid, elem, j, ell);",
+                              "for (int j = 0; j < 3; j++) al[j] = stream_ring(seed, PAIR_01, PUR_RSS_T, tid, elem, j, ell);"),
+    "rss_s_from_seed012": ("uint64_t sbit = orc_stream_word(seed, PAIR_2, PUR_RSS_S, tid, elem, 0) & 1u;",
+                           "uint64_t sbit = orc_stream_word(seed, PAIR_012, PUR_RSS_S, tid, elem, 0) & 1u;"),
+    "rss_relu_reuses_gamma": ("gr[j] = stream_ring(seed, PAIR_012, PUR_RSS_ZR, tid, elem, j, ell);",
+                              "gr[j] = stream_ring(seed, PAIR_012, PUR_RSS_Z, tid, elem, j, ell);"),
     "aby3_rp0_is_r0": ("uint64_t rp0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 1, ell);",
                        "uint64_t rp0 = stream_ring(seed, PAIR_02, PUR_ABY3, tid, elem, 0, ell);"),
     "aby3_r1_from_seed02": ("uint64_t r1 = stream_ring(seed, PAIR_12, PUR_ABY3, tid, elem, 0, ell);",

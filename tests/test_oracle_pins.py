@@ -733,6 +733,56 @@ def test_rss_drelu_bruteforce_l8():
     assert set(np.abs(xs[bad]).tolist()) <= _c0_exceptions(lx)
 
 
+@pytest.mark.parametrize("relu", [False, True])
+def test_rss_components_from_stream_words(relu):
+    """Alg. drelu2 / the RSS ReLU with every preprocessing draw rebuilt from
+    the raw stream words and each step recomputed with Python integers: [t]
+    from alpha_0..2 (seed012) as (a0 - a2, a1 - a0 + t, a2 - a1); s from seed2
+    with [s]_1 from seed012, [s]_2 from seed12 and [s]_0 = s - [s]_1 - [s]_2;
+    the replicated product [s][t] with the zero sharing gamma (seed012);
+    [s xor t] = [s] + [t] - 2[s][t]; the output d'' + [s xor t] - 2 d'' [s xor
+    t] with d'' = s xor DReLU' added to component 0; for ReLU the replicated
+    product with x and its own zero sharing."""
+    ell, lx, c = 64, 24, 0
+    P = O.params(ell, lx, c)
+    M = 1 << ell
+    seed, tid = 0x355_0DD5, 12
+    rng = np.random.default_rng(23)
+    x = rng.integers(-2**22, 2**22, size=30)
+    xu = [int(v) % M for v in x]
+    a = [int(v) for v in rng.integers(0, 2**63, size=30)]
+    b = [int(v) for v in rng.integers(0, 2**63, size=30)]
+    x0 = np.array(a, dtype=np.uint64)
+    x1 = np.array(b, dtype=np.uint64)
+    x2 = np.array([(v - u - w) % M for v, u, w in zip(xu, a, b)], dtype=np.uint64)
+    y0, y1, y2, dp = O.rss_drelu(P, x0, x1, x2, seed, tid, relu=relu)
+
+    def ring(pair, pur, e, j):
+        w = lambda jj: O.stream_word(seed, pair, pur, tid, e, jj)
+        return (w(2 * j) | (w(2 * j + 1) << 32)) % M
+
+    def rmul(u, v, g):   # replicated product: component i from (i, i + 1)
+        return [(u[i] * v[i] + u[i] * v[(i + 1) % 3] + u[(i + 1) % 3] * v[i] + g[i]
+                 - g[(i + 1) % 3]) % M for i in range(3)]
+
+    for e in range(x.size):
+        t = O.stream_word(seed, O.PAIR_01, O.PUR_PERM, tid, e, 0) & 1
+        al = [ring(O.PAIR_012, O.PUR_RSS_T, e, j) for j in range(3)]
+        T = [(al[0] - al[2]) % M, (al[1] - al[0] + t) % M, (al[2] - al[1]) % M]
+        s = O.stream_word(seed, O.PAIR_2, O.PUR_RSS_S, tid, e, 0) & 1
+        S1, S2 = ring(O.PAIR_012, O.PUR_RSS_S, e, 0), ring(O.PAIR_12, O.PUR_RSS_S, e, 0)
+        S = [(s - S1 - S2) % M, S1, S2]
+        g = [ring(O.PAIR_012, O.PUR_RSS_Z, e, j) for j in range(3)]
+        ST = rmul(S, T, g)
+        X = [(S[j] + T[j] - 2 * ST[j]) % M for j in range(3)]
+        dd = s ^ int(dp[e])
+        Y = [(X[j] - 2 * dd * X[j] + (dd if j == 0 else 0)) % M for j in range(3)]
+        if relu:
+            gr = [ring(O.PAIR_012, O.PUR_RSS_ZR, e, j) for j in range(3)]
+            Y = rmul([int(x0[e]), int(x1[e]), int(x2[e])], Y, gr)
+        assert [int(y0[e]), int(y1[e]), int(y2[e])] == Y
+
+
 def test_rss_relu_exact_product():
     from paper_2309_04909_gb300 import workloads as W
     for ell, lx, c, bits in ((64, 24, 0, 23), (32, 14, 4, 17)):
